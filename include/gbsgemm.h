@@ -1,0 +1,218 @@
+/*
+ * gbsgemm.h - C ABI of a GB300 (sm_103a) single-precision GEMM library.
+ *
+ * The operation is the Level-3 BLAS SGEMM (paper Sec. 1: dense product of
+ * A: M x K and B: K x N costing 2MNK flops, exposed through the SGEMM
+ * interface of Level-3 BLAS):
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C
+ *
+ * op(X) = X for trans 'N'/'n' and X^T for 'T'/'t'/'C'/'c' (real data, so
+ * 'C' equals 'T'). op(A) is M x K, op(B) is K x N, C is M x N. All matrices
+ * are column-major: element (r,c) of X lives at X[r + c*ldX].
+ *
+ * Conventions for every entry point below
+ * ---------------------------------------
+ * - Pointers named A, B, C, dC, ... are DEVICE pointers on the handle's GPU;
+ *   pointers to structs and sizes (gb_handle_t*, size_t*, gb_err_report_t*,
+ *   host_problems) are HOST pointers. The caller owns every buffer, the
+ *   workspace and the stream; the library never frees caller memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Compute calls enqueue work on it and return without waiting,
+ *   unless their comment says they synchronise.
+ * - Level-3 BLAS semantics: if beta == 0, C is not read (NaN there does not
+ *   propagate); if alpha == 0 or K == 0, A and B are not read. Quick return
+ *   (nothing enqueued) when M == 0, N == 0, or (alpha == 0 or K == 0) and
+ *   beta == 1.
+ * - Return codes: 0 = success. A negative code -i names the i-th SGEMM
+ *   argument in BLAS order that is invalid (1 transa, 2 transb, 3 M, 4 N,
+ *   5 K, 8 lda, 10 ldb, 13 ldc), as BLAS's xerbla would, but returned
+ *   instead of aborting. Positive codes are the GB_ERR_* values below.
+ *   Nothing is enqueued when a call returns an error before launching.
+ * - Thread safety: a handle may be used from one host thread at a time.
+ */
+#ifndef GBSGEMM_H
+#define GBSGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GB_API __attribute__((visibility("default")))
+#else
+#define GB_API
+#endif
+
+/* Status codes (positive); negative codes are BLAS argument positions. */
+enum {
+    GB_OK = 0,
+    GB_ERR_CUDA = 1,        /* a CUDA runtime/driver call failed */
+    GB_ERR_WORKSPACE = 2,   /* workspace NULL, misaligned or too small */
+    GB_ERR_UNSUPPORTED = 3, /* device is not sm_103, or an unsupported request */
+    GB_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (see gb_get_device_error) */
+    GB_ERR_PLAN = 5,        /* invalid or mismatched grouped plan */
+    GB_ERR_HANDLE = 6,      /* NULL or destroyed handle, or wrong current device */
+    GB_ERR_ARG = 7          /* invalid argument outside the SGEMM list (NULL out-pointer, count < 0, ...) */
+};
+
+/* Algorithms. All compute C in FP32 storage; they differ in how the
+ * products are formed:
+ *  GB_ALGO_SIMT         FP32 fused multiply-add on the CUDA cores.
+ *  GB_ALGO_SPLIT_TF32X3 each operand split as a = hi + lo, both TF32
+ *                       (round to nearest even); hi*hi + hi*lo + lo*hi on
+ *                       the tensor cores (tcgen05 kind::tf32), FP32 accumulation.
+ *  GB_ALGO_SPLIT_BF16X3 hi/lo in BF16; the same three products (kind::f16).
+ *  GB_ALGO_SPLIT_BF16X6 a = b0 + b1 + b2 in BF16 (exact for FP32 inputs);
+ *                       the six products with weight >= 2^-16:
+ *                       b0b0 b0b1 b1b0 b0b2 b1b1 b2b0.
+ *  GB_ALGO_AUTO         the library picks (currently SPLIT_BF16X3 when
+ *                       K >= 1024, else SPLIT_TF32X3 when K >= 16, else SIMT). */
+typedef enum {
+    GB_ALGO_AUTO = -1,
+    GB_ALGO_SIMT = 0,
+    GB_ALGO_SPLIT_TF32X3 = 1,
+    GB_ALGO_SPLIT_BF16X3 = 2,
+    GB_ALGO_SPLIT_BF16X6 = 3
+} gb_algo_t;
+
+typedef struct gb_handle_s *gb_handle_t;
+typedef struct gb_grouped_plan_s *gb_grouped_plan_t;
+
+/* Library version as 10000*major + 100*minor + patch. */
+GB_API int gb_version(void);
+
+/* Human-readable name of a status code (never NULL; static storage). */
+GB_API const char *gb_status_string(int status);
+
+/* Create a handle bound to the CURRENT CUDA device. Allocates a few hundred
+ * bytes of device memory for the device error word and scratch counters.
+ * Returns GB_ERR_UNSUPPORTED if the device is not compute capability 10.3,
+ * GB_ERR_CUDA if no device is usable, GB_ERR_ARG if h is NULL. */
+GB_API int gb_create(gb_handle_t *h);
+
+/* Destroy a handle (synchronises the device first). NULL is a no-op. */
+GB_API int gb_destroy(gb_handle_t h);
+
+/* Bytes of device workspace gb_sgemm needs for this algorithm and problem
+ * (0 for GB_ALGO_SIMT). Writes *bytes; returns a BLAS argument code on bad
+ * arguments. The workspace pointer passed later must be 256-byte aligned. */
+GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char transa, char transb,
+                                   int64_t m, int64_t n, int64_t k, size_t *bytes);
+
+/* C <- alpha*op(A)*op(B) + beta*C (paper Sec. 1; Level-3 BLAS SGEMM).
+ * Requirements: lda >= max(1, rows of stored A) (M if transa is 'N', else K),
+ * ldb >= max(1, rows of stored B) (K if transb is 'N', else N),
+ * ldc >= max(1, M). C must not overlap A or B. The split algorithms need
+ * `workspace` of at least gb_sgemm_workspace_size() bytes, 256-byte aligned
+ * (GB_ERR_WORKSPACE otherwise); SIMT ignores it. Enqueues on `stream` and
+ * returns without waiting. A bounded-wait timeout inside a tensor-core
+ * kernel is reported by gb_get_device_error, not by this call. */
+GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb,
+                    int64_t m, int64_t n, int64_t k,
+                    float alpha, const float *A, int64_t lda,
+                    const float *B, int64_t ldb,
+                    float beta, float *C, int64_t ldc,
+                    void *workspace, size_t ws_bytes, void *stream);
+
+/* Gradients of C = alpha*op(A)*op(B) + beta*C_in with respect to A, B and
+ * C_in, given dC = dL/dC (M x N, lddc). Any of dA, dB, dCin may be NULL to
+ * skip it. dA has the stored shape of A (ldda), dB that of B (lddb), dCin is
+ * M x N (lddcin). Each output is overwritten (not accumulated):
+ *   op(A) = A   : dA = alpha * dC * op(B)^T
+ *   op(A) = A^T : dA = alpha * op(B) * dC^T
+ *   op(B) = B   : dB = alpha * op(A)^T * dC
+ *   op(B) = B^T : dB = alpha * dC^T * op(A)
+ *   dCin = beta * dC
+ * Each gradient product runs through gb_sgemm with the same algorithm;
+ * `workspace` must hold the larger of the two products' requirements
+ * (gb_sgemm_backward_workspace_size). Enqueues on `stream`. */
+GB_API int gb_sgemm_backward(gb_handle_t h, gb_algo_t algo, char transa, char transb,
+                             int64_t m, int64_t n, int64_t k, float alpha,
+                             const float *A, int64_t lda, const float *B, int64_t ldb,
+                             float beta, const float *dC, int64_t lddc,
+                             float *dA, int64_t ldda, float *dB, int64_t lddb,
+                             float *dCin, int64_t lddcin,
+                             void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace bytes for gb_sgemm_backward with the same arguments. */
+GB_API int gb_sgemm_backward_workspace_size(gb_algo_t algo, char transa, char transb,
+                                            int64_t m, int64_t n, int64_t k,
+                                            size_t *bytes);
+
+/* One problem of a grouped call; pointers are device pointers. */
+typedef struct {
+    char transa, transb;
+    int64_t m, n, k;
+    float alpha, beta;
+    const float *A; int64_t lda;
+    const float *B; int64_t ldb;
+    float *C; int64_t ldc;
+} gb_gemm_problem_t;
+
+/* Plan `count` independent SGEMMs (host array `host_problems`) for one
+ * persistent grouped launch. Validates every problem (on error returns
+ * -i for the i-th argument of the first bad problem and writes its index to
+ * *bad_index if not NULL), sorts the work into tiles, uploads the work list
+ * to device memory owned by the plan, and writes the workspace the run needs
+ * to *ws_bytes. Synchronises the device; not capturable. algo may be
+ * GB_ALGO_SIMT or GB_ALGO_AUTO (per-problem choice). */
+GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
+                                 const gb_gemm_problem_t *host_problems,
+                                 gb_grouped_plan_t *plan, size_t *ws_bytes,
+                                 int64_t *bad_index);
+
+/* Run a plan: enqueues a fixed sequence of kernels on `stream`, with no
+ * allocation and no host synchronisation, so it may be captured in a CUDA
+ * graph. `workspace` must be 256-byte aligned and at least the planned size. */
+GB_API int gb_sgemm_grouped_run(gb_grouped_plan_t plan, void *workspace, size_t ws_bytes,
+                                void *stream);
+
+/* Free a plan's device memory (synchronises the device). NULL is a no-op. */
+GB_API int gb_sgemm_grouped_destroy(gb_grouped_plan_t plan);
+
+/* Error report of an FP32 result C (M x N) against an FP64 reference C64
+ * and bound denominator D (both M x N, column-major, device pointers):
+ *   ratio_ij = |C_ij - C64_ij| / (2 * max(K,1) * 2^-24 * D_ij)
+ * with ratio 0 where numerator and bound are both 0 and +inf where only the
+ * bound is 0; two NaNs or equal infinities agree (ratio 0), one non-finite
+ * side alone gives +inf. Reports the maximum ratio, the lower median (rank
+ * floor((MN-1)/2) in ascending order, found exactly by radix selection on the
+ * FP64 bit patterns), sum |C - C64|^2, sum C64^2 (finite entries), the
+ * count of ratios > 1 and the number of elements. This is the only FP64
+ * arithmetic on the GPU. Synchronises `stream` and writes *out.
+ * `workspace` needs gb_err_report_workspace_size(m, n) bytes. */
+typedef struct {
+    double max_ratio;
+    double median_ratio;
+    double sum_sq_diff;
+    double sum_sq_ref;
+    int64_t n_fail;
+    int64_t count;
+} gb_err_report_t;
+
+GB_API size_t gb_err_report_workspace_size(int64_t m, int64_t n);
+GB_API int gb_err_report(gb_handle_t h, int64_t m, int64_t n, int64_t k,
+                         const float *C, int64_t ldc, const double *C64, int64_t ldc64,
+                         const double *D, int64_t ldd, void *workspace, size_t ws_bytes,
+                         gb_err_report_t *out, void *stream);
+
+/* Synchronise `stream`, then read and clear the handle's device error word.
+ * Returns GB_OK if no bounded wait expired since the last call, else
+ * GB_ERR_TIMEOUT and writes the id of the wait site to *site (if not NULL). */
+GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site);
+
+/* Time limit of each bounded mbarrier wait in the tensor-core kernels, in
+ * microseconds of GPU wall clock (default 2,000,000 = 2 s). A wait that
+ * runs out records its site in the device error word and the kernel leaves
+ * cleanly (see gb_get_device_error). Values < 1 are rejected (GB_ERR_ARG). */
+GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSGEMM_H */

@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) single-precision GEMM: C <- alpha*op(A)*op(B) + beta*C.
+
+The computation of Aberdeen & Baxter's Emmerald SGEMM (Level-3 BLAS SGEMM,
+paper Sec. 1), re-designed for the GB300: a plain FP32 SIMT kernel and
+split-precision tensor-core kernels (tcgen05/TMEM/TMA) behind the C ABI in
+include/gbsgemm.h. This package is the thin Python binding: importing it
+does not load the CUDA library; the first call does, and fails loudly if
+the library is missing.
+"""
+from .api import (Handle, backward_raw, colmajor, default_handle, err_report, from_fortran,
+                  sgemm, sgemm_raw, to_fortran, workspace_size)
+
+__all__ = ["Handle", "backward_raw", "colmajor", "default_handle", "err_report", "from_fortran",
+           "sgemm", "sgemm_raw", "to_fortran", "workspace_size"]

@@ -1,0 +1,206 @@
+"""Python binding of the C ABI over torch CUDA tensors (marshalling only).
+
+A column-major matrix is a 2-D float32 CUDA tensor whose first stride is 1
+(element (r, c) at offset r + c*ld, ld = stride(1)); `colmajor(rows, cols)`
+makes one. A row-major torch matrix X (rows x cols, contiguous) is the
+column-major matrix X^T, which is how `linear` maps a dense layer onto the
+BLAS call. Every computation runs in the CUDA library; nothing here falls
+back to torch arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+
+_tls = threading.local()
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def colmajor(rows: int, cols: int, ld: int | None = None, device="cuda", fill=None):
+    """A (rows x cols) column-major float32 tensor with leading dimension ld."""
+    ld = max(rows, 1) if ld is None else ld
+    if ld < max(rows, 1):
+        raise ValueError("ld < rows")
+    store = torch.empty((max(cols, 1), ld), dtype=torch.float32, device=device)
+    if fill is not None:
+        store.fill_(fill)
+    return store.t()[:rows, :cols]
+
+
+def from_fortran(arr, device="cuda", rows=None):
+    """Upload a Fortran-ordered numpy (ld, cols) float32 array; returns the
+    padded storage view (ld x cols) and the logical (rows x cols) view."""
+    import numpy as np
+    a = np.asarray(arr)
+    if a.dtype != np.float32 or not a.flags.f_contiguous:
+        raise TypeError("expected a Fortran-ordered float32 array")
+    ld, cols = a.shape
+    store = torch.from_numpy(np.ascontiguousarray(a.T)).to(device)      # (cols, ld) row-major
+    full = store.t()
+    return full, full[: (ld if rows is None else rows), :]
+
+
+def to_fortran(t):
+    """Download a column-major tensor view into a Fortran numpy array."""
+    return t.detach().t().contiguous().cpu().numpy().T
+
+
+def _mat(t, name):
+    if t is None:
+        return 0, 0, 0, 1
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float32 CUDA tensor")
+    rows, cols = t.shape
+    if rows > 1 and cols > 0 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    ld = t.stride(1) if cols > 1 else max(rows, 1)
+    ld = max(ld, rows, 1)
+    return t.data_ptr(), rows, cols, ld
+
+
+class Handle:
+    """Owns a gb_handle_t bound to one CUDA device and a cached workspace."""
+
+    def __init__(self, device=None):
+        self.lib = _lib.load()
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else
+                           torch.device(device).index or 0)
+        self.device = dev
+        with torch.cuda.device(dev):
+            h = ctypes.c_void_p()
+            _lib.check("gb_create", self.lib.gb_create(ctypes.byref(h)))
+        self.h = h
+        self._ws = None
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self.lib.gb_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, nbytes: int):
+        if nbytes == 0:
+            return None
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def set_wait_limit(self, microseconds: int):
+        _lib.check("gb_set_wait_limit", self.lib.gb_set_wait_limit(self.h, int(microseconds)))
+
+    def device_error(self, stream=None):
+        """Returns (status, site); status GB_ERR_TIMEOUT if a bounded wait expired."""
+        site = ctypes.c_int(0)
+        rc = self.lib.gb_get_device_error(self.h, _stream_ptr(stream), ctypes.byref(site))
+        return rc, site.value
+
+
+def default_handle() -> Handle:
+    dev = torch.cuda.current_device()
+    hs = getattr(_tls, "handles", None)
+    if hs is None:
+        hs = _tls.handles = {}
+    if dev not in hs:
+        hs[dev] = Handle(dev)
+    return hs[dev]
+
+
+def workspace_size(algo, transa, transb, m, n, k) -> int:
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    _lib.check("gb_sgemm_workspace_size",
+               lib.gb_sgemm_workspace_size(_lib.ALGOS[algo], transa.encode(), transb.encode(),
+                                           m, n, k, ctypes.byref(out)))
+    return out.value
+
+
+def sgemm_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc,
+              algo="auto", handle=None, stream=None, workspace=None, check=True) -> int:
+    """Direct call of gb_sgemm on device pointers (ints). Returns the status."""
+    h = handle or default_handle()
+    ws_bytes = workspace_size(algo, transa, transb, m, n, k) if (m >= 0 and n >= 0 and k >= 0
+                                                                   and transa in "NnTtCc"
+                                                                   and transb in "NnTtCc") else 0
+    ws = workspace if workspace is not None else h.workspace(ws_bytes)
+    ws_ptr = ws.data_ptr() if ws is not None else 0
+    ws_len = ws.numel() if ws is not None else 0
+    rc = h.lib.gb_sgemm(h.h, _lib.ALGOS[algo], transa.encode(), transb.encode(), m, n, k,
+                        float(alpha), A_ptr, lda, B_ptr, ldb, float(beta), C_ptr, ldc,
+                        ws_ptr, ws_len, _stream_ptr(stream))
+    if check:
+        _lib.check("gb_sgemm", rc)
+    return rc
+
+
+def sgemm(A, B, C, alpha=1.0, beta=0.0, transa="N", transb="N", algo="auto", handle=None,
+          stream=None):
+    """C <- alpha*op(A)*op(B) + beta*C in place on column-major tensors."""
+    pa, ar, ac, lda = _mat(A, "A")
+    pb, br, bc, ldb = _mat(B, "B")
+    pc, m, n, ldc = _mat(C, "C")
+    k = ac if transa in "Nn" else ar
+    if (ar if transa in "Nn" else ac) != m or (bc if transb in "Nn" else br) != n or \
+            (br if transb in "Nn" else bc) != k:
+        raise ValueError("inconsistent shapes for sgemm")
+    sgemm_raw(transa, transb, m, n, k, alpha, pa, lda, pb, ldb, beta, pc, ldc, algo=algo,
+              handle=handle, stream=stream)
+    return C
+
+
+def backward_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, dC_ptr, lddc,
+                 dA_ptr, ldda, dB_ptr, lddb, dCin_ptr, lddcin, algo="auto", handle=None,
+                 stream=None, check=True) -> int:
+    h = handle or default_handle()
+    out = ctypes.c_size_t(0)
+    rc = h.lib.gb_sgemm_backward_workspace_size(_lib.ALGOS[algo], transa.encode(),
+                                                transb.encode(), m, n, k, ctypes.byref(out))
+    if rc != 0:
+        if check:
+            _lib.check("gb_sgemm_backward_workspace_size", rc)
+        return rc
+    ws = h.workspace(out.value)
+    rc = h.lib.gb_sgemm_backward(h.h, _lib.ALGOS[algo], transa.encode(), transb.encode(), m, n, k,
+                                 float(alpha), A_ptr, lda, B_ptr, ldb, float(beta), dC_ptr, lddc,
+                                 dA_ptr, ldda, dB_ptr, lddb, dCin_ptr, lddcin,
+                                 ws.data_ptr() if ws is not None else 0,
+                                 ws.numel() if ws is not None else 0, _stream_ptr(stream))
+    if check:
+        _lib.check("gb_sgemm_backward", rc)
+    return rc
+
+
+def err_report(C, C64, D, k, handle=None, stream=None) -> dict:
+    """GPU error report of an FP32 result against FP64 (C64, D) (column-major tensors)."""
+    h = handle or default_handle()
+    pc, m, n, ldc = _mat(C, "C")
+    for t, nm in ((C64, "C64"), (D, "D")):
+        if t.dtype != torch.float64 or not t.is_cuda or t.shape != (m, n) or (m > 1 and t.stride(0) != 1):
+            raise TypeError(f"{nm} must be a column-major float64 CUDA tensor of shape {(m, n)}")
+    ld64 = max(C64.stride(1) if n > 1 else m, m, 1)
+    ldd = max(D.stride(1) if n > 1 else m, m, 1)
+    need = h.lib.gb_err_report_workspace_size(m, n)
+    ws = torch.empty(max(int(need), 1), dtype=torch.uint8, device=h.device)
+    rep = _lib.ErrReport()
+    _lib.check("gb_err_report",
+               h.lib.gb_err_report(h.h, m, n, k, pc, ldc, C64.data_ptr(), ld64, D.data_ptr(), ldd,
+                                   ws.data_ptr(), ws.numel(), ctypes.byref(rep),
+                                   _stream_ptr(stream)))
+    num = rep.sum_sq_diff ** 0.5
+    den = rep.sum_sq_ref ** 0.5
+    normwise = 0.0 if num == 0.0 else (num / den if den > 0 else float("inf"))
+    return dict(max_ratio=rep.max_ratio, median_ratio=rep.median_ratio, normwise=normwise,
+                n_fail=rep.n_fail, count=rep.count, sum_sq_diff=rep.sum_sq_diff,
+                sum_sq_ref=rep.sum_sq_ref)

@@ -1,0 +1,310 @@
+// Host side of the C ABI declared in include/gbsgemm.h: argument checks in
+// Level-3 BLAS order, quick returns, workspace layout, algorithm dispatch,
+// the backward formulas and the device error word.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+using namespace gb;
+
+namespace {
+
+bool trans_ok(char t) {
+    return t == 'N' || t == 'n' || t == 'T' || t == 't' || t == 'C' || t == 'c';
+}
+bool is_trans(char t) { return t != 'N' && t != 'n'; }
+int64_t max1(int64_t x) { return x > 1 ? x : 1; }
+
+// BLAS xerbla positions: 1 transa, 2 transb, 3 M, 4 N, 5 K, 8 lda, 10 ldb, 13 ldc.
+int check_sgemm_args(char ta, char tb, int64_t m, int64_t n, int64_t k, int64_t lda,
+                     int64_t ldb, int64_t ldc) {
+    if (!trans_ok(ta)) return -1;
+    if (!trans_ok(tb)) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    if (lda < max1(is_trans(ta) ? k : m)) return -8;
+    if (ldb < max1(is_trans(tb) ? n : k)) return -10;
+    if (ldc < max1(m)) return -13;
+    return 0;
+}
+
+int check_handle(gb_handle_t h) {
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    if (dev != h->device) return GB_ERR_HANDLE;
+    return GB_OK;
+}
+
+int split_mode(gb_algo_t algo) {
+    switch (algo) {
+        case GB_ALGO_SPLIT_TF32X3: return 0;
+        case GB_ALGO_SPLIT_BF16X3: return 1;
+        case GB_ALGO_SPLIT_BF16X6: return 2;
+        default: return -1;
+    }
+}
+
+gb_algo_t resolve_algo(gb_algo_t algo, int64_t k) {
+    if (algo != GB_ALGO_AUTO) return algo;
+    if (k >= 1024) return GB_ALGO_SPLIT_BF16X3;
+    if (k >= 16) return GB_ALGO_SPLIT_TF32X3;
+    return GB_ALGO_SIMT;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace of a split algorithm: [A terms][B terms], each region 1 KiB aligned.
+size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
+    const size_t kpad = (size_t)split_kpad(mode, k);
+    const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
+    return round_up(per * (size_t)m, 1024) + round_up(per * (size_t)n, 1024);
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
+
+int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_t n, int64_t k,
+               float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+               float *C, int64_t ldc, void *ws, size_t ws_bytes, cudaStream_t s) {
+    int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, ldc);
+    if (rc) return rc;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if ((rc = check_handle(h))) return rc;
+    if (m == 0 || n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
+    if (!C) return GB_ERR_ARG;
+    if (alpha == 0.f || k == 0) return cuda_status(launch_scale_c(m, n, beta, C, ldc, s));
+    if (!A || !B) return GB_ERR_ARG;
+
+    algo = resolve_algo(algo, k);
+    if (algo == GB_ALGO_SIMT) {
+        SimtArgs a{is_trans(ta), is_trans(tb), m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+        return cuda_status(launch_simt_sgemm(a, s));
+    }
+    const int mode = split_mode(algo);
+    const size_t need = split_ws_bytes(mode, m, n, k);
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
+    const int64_t kpad = split_kpad(mode, k);
+    const size_t eb = (size_t)split_elem_bytes(mode);
+    char *Ap = static_cast<char *>(ws);
+    char *Bp = Ap + round_up((size_t)split_parts(mode) * kpad * eb * (size_t)m, 1024);
+    // op(A)[i,p]: stored A is K-contiguous iff transposed.
+    cudaError_t e = launch_split_pack(mode, is_trans(ta), m, k, A, lda, Ap, kpad, m * kpad, s);
+    // op(B)^T[j,p] = op(B)[p,j]: stored B is K-contiguous iff NOT transposed.
+    if (e == cudaSuccess)
+        e = launch_split_pack(mode, !is_trans(tb), n, k, B, ldb, Bp, kpad, n * kpad, s);
+    if (e != cudaSuccess) return GB_ERR_CUDA;
+    TcArgs t{};
+    t.mode = mode;
+    t.m = m; t.n = n; t.k = k; t.kpad = kpad;
+    t.alpha = alpha; t.beta = beta;
+    t.Ap = Ap; t.Bp = Bp;
+    t.a_part_stride = m * kpad; t.b_part_stride = n * kpad;
+    t.C = C; t.ldc = ldc;
+    t.dstate = h->dstate;
+    t.wait_limit = h->wait_limit;
+    t.sm_count = h->sm_count;
+    e = launch_tc_sgemm(t, s);
+    return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
+}
+
+// Backward products (see gb_sgemm_backward in the header for the formulas).
+struct BwdCall {
+    char ta, tb;
+    int64_t m, n, k;
+    const float *A; int64_t lda;
+    const float *B; int64_t ldb;
+    float *C; int64_t ldc;
+};
+
+BwdCall grad_a(char ta, char tb, int64_t m, int64_t n, int64_t k, const float *B, int64_t ldb,
+               const float *G, int64_t ldg, float *dA, int64_t ldda) {
+    if (!is_trans(ta))   // dA (M x K) = G (M x N) * op(B)^T (N x K)
+        return BwdCall{'N', is_trans(tb) ? 'N' : 'T', m, k, n, G, ldg, B, ldb, dA, ldda};
+    // dA (K x M) = op(B) (K x N) * G^T (N x M)
+    return BwdCall{is_trans(tb) ? 'T' : 'N', 'T', k, m, n, B, ldb, G, ldg, dA, ldda};
+}
+
+BwdCall grad_b(char ta, char tb, int64_t m, int64_t n, int64_t k, const float *A, int64_t lda,
+               const float *G, int64_t ldg, float *dB, int64_t lddb) {
+    if (!is_trans(tb))   // dB (K x N) = op(A)^T (K x M) * G (M x N)
+        return BwdCall{is_trans(ta) ? 'N' : 'T', 'N', k, n, m, A, lda, G, ldg, dB, lddb};
+    // dB (N x K) = G^T (N x M) * op(A) (M x K)
+    return BwdCall{'T', is_trans(ta) ? 'T' : 'N', n, k, m, G, ldg, A, lda, dB, lddb};
+}
+
+size_t call_ws(gb_algo_t algo, const BwdCall &c) {
+    algo = resolve_algo(algo, c.k);
+    const int mode = split_mode(algo);
+    return mode < 0 ? 0 : split_ws_bytes(mode, c.m, c.n, c.k);
+}
+
+}  // namespace
+
+extern "C" {
+
+GB_API int gb_version(void) { return 10000; }
+
+GB_API const char *gb_status_string(int status) {
+    if (status < 0) return "invalid SGEMM argument (negative code = BLAS argument position)";
+    switch (status) {
+        case GB_OK: return "success";
+        case GB_ERR_CUDA: return "CUDA error";
+        case GB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case GB_ERR_UNSUPPORTED: return "unsupported device or request";
+        case GB_ERR_TIMEOUT: return "bounded device wait expired";
+        case GB_ERR_PLAN: return "invalid grouped plan";
+        case GB_ERR_HANDLE: return "invalid handle or wrong current device";
+        case GB_ERR_ARG: return "invalid argument";
+        default: return "unknown status";
+    }
+}
+
+GB_API int gb_create(gb_handle_t *out) {
+    if (!out) return GB_ERR_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return GB_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return GB_ERR_UNSUPPORTED;
+    gb_handle_s *h = new (std::nothrow) gb_handle_s();
+    if (!h) return GB_ERR_ARG;
+    h->magic = kHandleMagic;
+    h->device = dev;
+    h->sm_count = prop.multiProcessorCount;
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    h->smem_optin = prop.sharedMemPerBlockOptin;
+    h->wait_limit = 2000000;
+    if (cudaMalloc(&h->dstate, sizeof(DeviceState)) != cudaSuccess ||
+        cudaMemset(h->dstate, 0, sizeof(DeviceState)) != cudaSuccess) {
+        delete h;
+        return GB_ERR_CUDA;
+    }
+    *out = h;
+    return GB_OK;
+}
+
+GB_API int gb_destroy(gb_handle_t h) {
+    if (!h) return GB_OK;
+    if (h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    cudaDeviceSynchronize();
+    cudaFree(h->dstate);
+    h->magic = 0;
+    delete h;
+    return GB_OK;
+}
+
+GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char ta, char tb, int64_t m, int64_t n,
+                                   int64_t k, size_t *bytes) {
+    int rc = check_sgemm_args(ta, tb, m, n, k, max1(is_trans(ta) ? k : m),
+                              max1(is_trans(tb) ? n : k), max1(m));
+    if (rc) return rc;
+    if (!bytes) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    const int mode = split_mode(resolve_algo(algo, k));
+    *bytes = (mode < 0 || m == 0 || n == 0 || k == 0) ? 0 : split_ws_bytes(mode, m, n, k);
+    return GB_OK;
+}
+
+GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb, int64_t m, int64_t n,
+                    int64_t k, float alpha, const float *A, int64_t lda, const float *B,
+                    int64_t ldb, float beta, float *C, int64_t ldc, void *workspace,
+                    size_t ws_bytes, void *stream) {
+    return sgemm_impl(h, algo, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+GB_API int gb_sgemm_backward_workspace_size(gb_algo_t algo, char ta, char tb, int64_t m,
+                                            int64_t n, int64_t k, size_t *bytes) {
+    int rc = check_sgemm_args(ta, tb, m, n, k, max1(is_trans(ta) ? k : m),
+                              max1(is_trans(tb) ? n : k), max1(m));
+    if (rc) return rc;
+    if (!bytes) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (m == 0 || n == 0 || k == 0) { *bytes = 0; return GB_OK; }
+    const BwdCall a = grad_a(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
+    const BwdCall b = grad_b(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
+    const size_t wa = call_ws(algo, a), wb = call_ws(algo, b);
+    *bytes = wa > wb ? wa : wb;
+    return GB_OK;
+}
+
+GB_API int gb_sgemm_backward(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m,
+                             int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                             const float *B, int64_t ldb, float beta, const float *dC,
+                             int64_t lddc, float *dA, int64_t ldda, float *dB, int64_t lddb,
+                             float *dCin, int64_t lddcin, void *ws, size_t ws_bytes,
+                             void *stream) {
+    int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, lddc);
+    if (rc) return rc;
+    if ((rc = check_handle(h))) return rc;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (dA && ldda < max1(is_trans(ta) ? k : m)) return GB_ERR_ARG;
+    if (dB && lddb < max1(is_trans(tb) ? n : k)) return GB_ERR_ARG;
+    if (dCin && lddcin < max1(m)) return GB_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dA) {
+        const BwdCall c = grad_a(ta, tb, m, n, k, B, ldb, dC, lddc, dA, ldda);
+        rc = sgemm_impl(h, algo, c.ta, c.tb, c.m, c.n, c.k, alpha, c.A, c.lda, c.B, c.ldb, 0.f,
+                        c.C, c.ldc, ws, ws_bytes, s);
+        if (rc) return rc;
+    }
+    if (dB) {
+        const BwdCall c = grad_b(ta, tb, m, n, k, A, lda, dC, lddc, dB, lddb);
+        rc = sgemm_impl(h, algo, c.ta, c.tb, c.m, c.n, c.k, alpha, c.A, c.lda, c.B, c.ldb, 0.f,
+                        c.C, c.ldc, ws, ws_bytes, s);
+        if (rc) return rc;
+    }
+    if (dCin && m > 0 && n > 0) {
+        if (beta != 0.f && !dC) return GB_ERR_ARG;
+        rc = cuda_status(launch_scaled_copy(m, n, beta, dC, lddc, dCin, lddcin, s));
+        if (rc) return rc;
+    }
+    return GB_OK;
+}
+
+GB_API size_t gb_err_report_workspace_size(int64_t m, int64_t n) {
+    return err_report_ws(m, n);
+}
+
+GB_API int gb_err_report(gb_handle_t h, int64_t m, int64_t n, int64_t k, const float *C,
+                         int64_t ldc, const double *C64, int64_t ldc64, const double *D,
+                         int64_t ldd, void *ws, size_t ws_bytes, gb_err_report_t *out,
+                         void *stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out || m < 0 || n < 0 || k < 0) return GB_ERR_ARG;
+    if (ldc < max1(m) || ldc64 < max1(m) || ldd < max1(m)) return GB_ERR_ARG;
+    if (m > 0 && n > 0 && (!C || !C64 || !D)) return GB_ERR_ARG;
+    if (!ws || ws_bytes < err_report_ws(m, n) || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return GB_ERR_WORKSPACE;
+    return cuda_status(run_err_report(h->sm_count, m, n, k, C, ldc, C64, ldc64, D, ldd, ws, out,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int err[2] = {0, 0};
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GB_ERR_CUDA;
+    if (cudaMemcpy(err, h->dstate->err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GB_ERR_CUDA;
+    if (cudaMemset(h->dstate->err, 0, sizeof(err)) != cudaSuccess) return GB_ERR_CUDA;
+    if (site) *site = (int)err[0];
+    return err[1] ? GB_ERR_TIMEOUT : GB_OK;
+}
+
+GB_API int gb_set_wait_limit(gb_handle_t h, int64_t polls) {
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    if (polls < 1) return GB_ERR_ARG;
+    h->wait_limit = polls;
+    return GB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (see include/gbsgemm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbsgemm.h"
+
+namespace gb {
+
+// Site ids written to the device error word when a bounded wait expires.
+enum WaitSite : int {
+    kSiteProducerEmpty = 1,   // TMA producer waiting for a free smem stage
+    kSiteMmaFull = 2,         // MMA issuer waiting for a filled smem stage
+    kSiteMmaAccEmpty = 3,     // MMA issuer waiting for the epilogue to drain TMEM
+    kSiteEpiAccFull = 4,      // epilogue waiting for a finished accumulator
+    kSiteTmemAlloc = 5,       // TMEM allocation did not complete
+    kSiteDrain = 6            // final drain of in-flight copies
+};
+
+// Device error word layout: err[0] = first failing site (0 = none),
+// err[1] = number of failures since the last read.
+struct DeviceState {
+    unsigned int err[2];
+    unsigned int pad[62];
+};
+
+}  // namespace gb
+
+struct gb_handle_s {
+    int magic;
+    int device;
+    int sm_count;
+    int cc_major, cc_minor;
+    size_t smem_optin;
+    int64_t wait_limit;
+    gb::DeviceState *dstate;   // device memory
+};
+
+namespace gb {
+
+constexpr int kHandleMagic = 0x6b5e3a21;
+
+// ------------------------------------------------------------------ SIMT --
+struct SimtArgs {
+    bool ta, tb;                // true = transposed
+    int64_t m, n, k;
+    float alpha, beta;
+    const float *A; int64_t lda;
+    const float *B; int64_t ldb;
+    float *C; int64_t ldc;
+};
+cudaError_t launch_simt_sgemm(const SimtArgs &a, cudaStream_t s);
+
+// C <- beta*C (beta == 0 writes zeros without reading C).
+cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float *C, int64_t ldc,
+                           cudaStream_t s);
+
+// Y <- beta*X elementwise (M x N; beta == 0 writes zeros without reading X).
+cudaError_t launch_scaled_copy(int64_t m, int64_t n, float beta, const float *X, int64_t ldx,
+                               float *Y, int64_t ldy, cudaStream_t s);
+
+// ------------------------------------------------------ split/pack pass --
+// Splits op(X) (rows x k; rows = M for A, N for B^T) into `parts` terms and
+// writes each term as a row-major [rows][kpad] array (K contiguous).
+// kcontig: the stored matrix is K-contiguous (element (r,p) at X[p + r*ld]),
+// else rows-contiguous (element (r,p) at X[r + p*ld]).
+// mode: 0 = TF32 (4-byte words, 2 parts), 1 = BF16 2 parts, 2 = BF16 3 parts.
+cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k,
+                              const float *X, int64_t ld, void *out, int64_t kpad,
+                              int64_t part_stride_elems, cudaStream_t s);
+
+// -------------------------------------------------- tensor-core kernel ---
+struct TcArgs {
+    int mode;                   // as launch_split_pack
+    int64_t m, n, k, kpad;
+    float alpha, beta;
+    const void *Ap;             // [parts][m][kpad]
+    const void *Bp;             // [parts][n][kpad]
+    int64_t a_part_stride, b_part_stride;   // elements between parts
+    float *C; int64_t ldc;
+    DeviceState *dstate;
+    int64_t wait_limit;
+    int sm_count;
+};
+cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s);
+// Workspace layout helpers shared by the API and the launcher.
+int64_t split_kpad(int mode, int64_t k);
+int split_parts(int mode);
+int split_elem_bytes(int mode);
+
+// --------------------------------------------------------- error report --
+size_t err_report_ws(int64_t m, int64_t n);
+cudaError_t run_err_report(int sm_count, int64_t m, int64_t n, int64_t k, const float *C,
+                           int64_t ldc, const double *C64, int64_t ldc64, const double *D,
+                           int64_t ldd, void *ws, gb_err_report_t *out, cudaStream_t s);
+
+}  // namespace gb

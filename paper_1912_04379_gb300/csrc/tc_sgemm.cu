@@ -1,0 +1,521 @@
+// Split-precision SGEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
+//
+// Input: the split/pack pass has written every FP32 element of op(A) and of
+// op(B)^T as 2 or 3 lower-precision terms (TF32 or BF16), each term as a
+// K-contiguous [rows][kpad] array. This kernel forms
+//     acc = sum over term pairs (s, t) of  A_s * B_t^T      (FP32 in TMEM)
+//     C   = alpha * acc + beta * C                           (fused epilogue)
+// with the pairs ordered smallest weight first:
+//   2 terms (h, l):      l*h, h*l, h*h
+//   3 terms (h, m, l):   h*l, m*m, l*h, h*m, m*h, h*h
+// Dropping l*l (and the 2^-24-weight pairs for 3 terms) keeps the error of
+// every product near FP32 round-off, which is how the split recovers FP32
+// accuracy from BF16/TF32 multipliers.
+//
+// The paper's Emmerald organises SGEMM around keeping operands close to the
+// arithmetic units: a register-resident block of C, a k-block of A and B
+// staged in L1, prefetch of the next block, and L2 blocking (Sec. 2, 3).
+// On sm_103a the same roles are:
+//   * C block in registers  -> a 128 x BN FP32 accumulator in tensor memory
+//     (TMEM), two of them so the epilogue of one tile overlaps the next;
+//   * L1 staging + prefetch -> a ring of shared-memory stages filled by TMA
+//     (cp.async.bulk.tensor, 128-byte swizzle) one step ahead of the MMAs,
+//     handshaken with mbarriers;
+//   * the inner loop        -> tcgen05.mma (M = 128, N = BN, K = 16 BF16 or
+//     8 TF32 per instruction) issued by one thread;
+//   * L2 blocking           -> a persistent grid (one CTA per SM) walking the
+//     output tiles in groups of 16 M-tiles so concurrently running CTAs
+//     share A and B panels in L2.
+// Warp roles in a 192-thread CTA: warp 0 = TMA producer, warp 1 = TMEM owner
+// and MMA issuer, warps 2..5 = epilogue (TMEM -> registers -> global).
+//
+// Every mbarrier wait is bounded by a wall-clock limit (globaltimer). On
+// expiry the thread records the wait site in the handle's device error word,
+// raises a CTA-wide abort flag that every other wait also polls, and all
+// roles leave their loops; the producer then waits (bounded) for its
+// in-flight copies, the MMA issuer for its in-flight MMAs, and TMEM is freed
+// before the CTA exits. No trap, no unbounded spin.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+
+namespace gb {
+namespace {
+
+constexpr int BM = 128;
+constexpr int ROW_BYTES = 128;                 // one swizzle row: 64 BF16 or 32 TF32
+constexpr int NUM_THREADS = 192;
+constexpr int GROUP_M = 16;                    // tile raster: 16 M-tiles per group
+// Limit for the final drains of in-flight copies and MMAs. These always
+// complete in hardware within microseconds; the generous fixed limit keeps
+// the CTA from exiting with asynchronous work outstanding even when the
+// caller set a very short limit for the ordinary waits.
+constexpr uint64_t kDrainLimitNs = 4000000000ull;
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct WaitCtx {
+    volatile int *abort;          // CTA-wide abort flag (shared memory)
+    DeviceState *dstate;          // handle's device error word
+    uint64_t limit_ns;
+};
+
+__device__ __noinline__ void record_timeout(const WaitCtx &w, int site) {
+    atomicCAS(&w.dstate->err[0], 0u, (unsigned)site);
+    atomicAdd(&w.dstate->err[1], 1u);
+    *w.abort = 1;
+}
+
+// Bounded wait for the phase of `bar` with the given parity to complete.
+// Returns false if the limit expired (recorded) or another role aborted.
+__device__ __forceinline__ bool wait_bounded(const WaitCtx &w, uint32_t bar, uint32_t parity,
+                                             int site) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*w.abort) return false;
+        if ((it & 15u) == 15u && global_ns() - t0 > w.limit_ns) {
+            record_timeout(w, site);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms
+// stacked along M/N. Fields: start address >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29; unused for swizzled K-major, set to 1), stride byte
+// offset >> 4 (32-45; 1024 bytes between 8-row groups), descriptor version 1
+// (46-47), base offset 0 (49-51; atoms are 1024-byte aligned), layout type
+// 2 = 128-byte swizzle (61-63).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor (kind::f16 / kind::tf32): D format F32 (bits 4-5 =
+// 1), A and B formats (bits 7-9, 10-12: 1 = BF16, 2 = TF32), both K-major
+// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <bool TF32, int N>
+__device__ __forceinline__ constexpr uint32_t instr_desc() {
+    constexpr uint32_t fmt = TF32 ? 2u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    if (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns: thread t of the warp gets
+// row (lane base + t), columns col..col+15.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ----------------------------------------------------------- the kernel --
+template <int MODE>
+struct Cfg {
+    static constexpr bool TF32 = MODE == 0;
+    static constexpr int PARTS = MODE == 2 ? 3 : 2;
+    static constexpr int NPAIRS = MODE == 2 ? 6 : 3;
+    static constexpr int BN = MODE == 2 ? 128 : 256;
+    static constexpr int ELEM = TF32 ? 4 : 2;
+    static constexpr int BK = ROW_BYTES / ELEM;          // elements per k-block
+    static constexpr int KSTEP_BYTES = 32;               // K per MMA: 16 BF16 / 8 TF32
+    static constexpr int KSTEPS = ROW_BYTES / KSTEP_BYTES;
+    static constexpr int A_TILE = BM * ROW_BYTES;        // bytes of one term's A tile
+    static constexpr int B_TILE = BN * ROW_BYTES;
+    static constexpr int STAGE_BYTES = PARTS * (A_TILE + B_TILE);
+    static constexpr int STAGES = (200 * 1024) / STAGE_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
+    static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
+    static_assert(STAGES >= 2, "need at least two stages");
+    static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
+};
+
+// Term pair (A term, B term) for step q, smallest weight first.
+template <int MODE>
+__device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {
+    if (MODE == 2) {
+        const int a[6] = {0, 1, 2, 0, 1, 0};
+        const int b[6] = {2, 1, 0, 1, 0, 0};
+        sa = a[q]; sb = b[q];
+    } else {
+        const int a[3] = {1, 0, 0};
+        const int b[3] = {0, 1, 0};
+        sa = a[q]; sb = b[q];
+    }
+}
+
+__device__ __forceinline__ void tile_coords(int64_t tile, int64_t tiles_m, int64_t tiles_n,
+                                            int64_t &tm, int64_t &tn) {
+    const int64_t per_group = (int64_t)GROUP_M * tiles_n;
+    const int64_t g = tile / per_group;
+    const int64_t first_m = g * GROUP_M;
+    const int64_t gm = (tiles_m - first_m) < GROUP_M ? (tiles_m - first_m) : GROUP_M;
+    const int64_t r = tile - g * per_group;
+    tm = first_m + r % gm;
+    tn = r / gm;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
+                int64_t ldc, DeviceState *dstate, uint64_t limit_ns) {
+    using CF = Cfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    // [stages][term][A tile] then [stages][term][B tile]
+    const uint32_t a_smem = base;
+    const uint32_t b_smem = base + CF::STAGES * CF::PARTS * CF::A_TILE;
+    const uint32_t bar_base = base + CF::STAGES * CF::STAGE_BYTES;
+    uint8_t *gbar = gbase + CF::STAGES * CF::STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar_base + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (CF::STAGES + s); };
+    auto accf_bar = [&](int b) { return bar_base + 8u * (2 * CF::STAGES + b); };
+    auto acce_bar = [&](int b) { return bar_base + 8u * (2 * CF::STAGES + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * CF::STAGES + 4);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbar + 8 * (2 * CF::STAGES + 5));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbar + 8 * (2 * CF::STAGES + 5) + 4);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    WaitCtx w{abort_flag, dstate, limit_ns};
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 4);       // one arrive per epilogue warp
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_tmap(&mapA);
+        prefetch_tmap(&mapB);
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_holder), CF::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    const int64_t tiles_m = (M + BM - 1) / BM;
+    const int64_t tiles_n = (N + CF::BN - 1) / CF::BN;
+    const int64_t num_tiles = tiles_m * tiles_n;
+    const int nkb = (int)((K + CF::BK - 1) / CF::BK);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, last_parity = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+                int64_t tm, tn;
+                tile_coords(tile, tiles_m, tiles_n, tm, tn);
+                const int y_a = (int)(tm * BM), y_b = (int)(tn * CF::BN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!wait_bounded(w, empty_bar(stage), phase ^ 1u, kSiteProducerEmpty)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(full_bar(stage), CF::STAGE_BYTES);
+                    for (int t = 0; t < CF::PARTS; ++t) {
+                        tma_load_3d(a_smem + (stage * CF::PARTS + t) * CF::A_TILE, &mapA,
+                                    full_bar(stage), kb * CF::BK, y_a, t);
+                        tma_load_3d(b_smem + (stage * CF::PARTS + t) * CF::B_TILE, &mapB,
+                                    full_bar(stage), kb * CF::BK, y_b, t);
+                    }
+                    issued_mask |= 1u << stage;
+                    last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // Wait (bounded, even after an abort) for every copy still in flight.
+            for (int s = 0; s < CF::STAGES; ++s) {
+                if (!(issued_mask & (1u << s))) continue;
+                const uint32_t par = (last_parity >> s) & 1u;
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(full_bar(s), par)) {
+                    if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t idesc = instr_desc<CF::TF32, CF::BN>();
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+                if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
+                uint32_t accumulate = 0;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int q = 0; q < CF::NPAIRS; ++q) {
+                        int sa, sb;
+                        pair_of<MODE>(q, sa, sb);
+                        const uint32_t a0 = a_smem + (stage * CF::PARTS + sa) * CF::A_TILE;
+                        const uint32_t b0 = b_smem + (stage * CF::PARTS + sb) * CF::B_TILE;
+#pragma unroll
+                        for (int ks = 0; ks < CF::KSTEPS; ++ks) {
+                            mma_issue<CF::TF32>(d_tmem, smem_desc_sw128(a0 + ks * CF::KSTEP_BYTES),
+                                                smem_desc_sw128(b0 + ks * CF::KSTEP_BYTES), idesc,
+                                                accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    mma_commit(empty_bar(stage));     // frees the stage once these MMAs finish
+                    if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(accf_bar(acc));            // accumulator ready for the epilogue
+                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+            }
+            // Make sure no MMA is still running before TMEM is released.
+            mma_commit(drain_bar);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(drain_bar, 0)) {
+                if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                       // TMEM lane quarter this warp may read
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+            if (!wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull)) break;
+            tc_fence_after();
+            int64_t tm, tn;
+            tile_coords(tile, tiles_m, tiles_n, tm, tn);
+            const int64_t row = tm * BM + q * 32 + lane;
+            const int64_t col0 = tn * CF::BN;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
+            const bool row_ok = row < M;
+            for (int c = 0; c < CF::BN; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c, v);
+                if (row_ok) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = col0 + c + j;
+                        if (col < N) {
+                            float *p = C + row + col * ldc;
+                            *p = beta != 0.f ? fmaf(alpha, v[j], beta * *p) : alpha * v[j];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(acc));
+            if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, CF::TMEM_COLS);
+}
+
+// ----------------------------------------------------------------- host --
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D map over [terms][rows][kpad] (K innermost), box = BK x box_rows x 1.
+bool make_map(CUtensorMap *map, bool tf32, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
+              int parts, int box_rows, int bk) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    const int eb = tf32 ? 4 : 2;
+    cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)parts};
+    cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(rows * kpad * eb)};
+    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     3, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
+    using CF = Cfg<MODE>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CF::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    // The tensor maps address rows/K with 32-bit coordinates.
+    if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
+        return cudaErrorNotSupported;
+    alignas(64) CUtensorMap ma, mb;
+    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK) ||
+        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK))
+        return cudaErrorInvalidValue;
+    const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN);
+    int grid = a.sm_count > 0 ? a.sm_count : 1;
+    if (tiles < grid) grid = (int)tiles;
+    const uint64_t limit_ns = (uint64_t)a.wait_limit * 1000ull;
+    tc_sgemm_kernel<MODE><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+        ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, a.dstate, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
+    switch (a.mode) {
+        case 0: return launch_mode<0>(a, s);
+        case 1: return launch_mode<1>(a, s);
+        case 2: return launch_mode<2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gb

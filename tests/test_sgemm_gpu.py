@@ -1,0 +1,192 @@
+"""GPU parity: every algorithm against the FP64 CPU oracle, through the C ABI.
+
+Acceptance per element: |C - C64| <= 2 * max(K,1) * 2^-24 * D (D = |alpha||op(A)||op(B)|
++ |beta||C|), and bit-exact equality on integer-valued inputs whose partial sums stay
+below 2^24. Padding rows of C (ld > M) must keep their canary value.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from _gpu import ALGOS, assert_bit_exact, assert_within_bound, check_padding, run, torch_gpu
+
+pytestmark = pytest.mark.gpu
+TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
+SPLIT = ("tf32x3", "bf16x3", "bf16x6")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch_gpu()
+
+
+# --------------------------------------------------------------- 384^3 ----
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_plain_384(algo):
+    p = wl.plain_384()
+    rc, got = run(p, algo)
+    assert rc == 0
+    assert_within_bound(p, got)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_plain_384_integer_bit_exact(algo):
+    p = wl.plain_384(integer=True)
+    rc, got = run(p, algo)
+    assert_bit_exact(p, got)
+
+
+# ------------------------------------------------- padded-stride sweep ----
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("n", (16, 100, 257, 512, 1000, 1023))
+def test_simt_sweep(n, ta, tb):
+    p = wl.sweep_case(n, ta, tb)
+    rc, got = run(p, "simt")
+    assert_within_bound(p, got)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("n", (2048, 4096, 8192))
+def test_simt_sweep_large_sampled(n, ta, tb):
+    p = wl.sweep_case(n, ta, tb)
+    rc, got = run(p, "simt")
+    cols = np.unique(np.r_[0, 1, n // 2, n - 1, np.random.default_rng(n).integers(0, n, 4)])
+    assert_within_bound(p, got, cols=cols)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("algo", SPLIT)
+@pytest.mark.parametrize("n", (100, 257, 1000))
+def test_split_sweep(algo, n, ta, tb):
+    p = wl.sweep_case(n, ta, tb)
+    rc, got = run(p, algo)
+    assert_within_bound(p, got)
+    check_padding(p, got)
+
+
+# ----------------------------------------------------- ragged shapes ----
+
+RAGGED = [(1, 1, 1), (7, 5, 3), (33, 17, 65), (127, 129, 31), (129, 255, 257),
+          (300, 520, 100), (1, 300, 7), (300, 1, 77), (128, 256, 64), (257, 513, 129)]
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("shape", RAGGED, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("algo", ALGOS)
+def test_ragged(algo, shape, ta, tb):
+    m, n, k = shape
+    p = wl.make_problem(ta, tb, m, n, k, -0.75, 1.25, seed=m * 7919 + n * 31 + k, ld_pad=3)
+    rc, got = run(p, algo)
+    assert rc == 0
+    assert_within_bound(p, got)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("algo", ALGOS)
+def test_ragged_integer_bit_exact(algo, ta, tb):
+    p = wl.make_problem(ta, tb, 257, 130, 1029, 1.0, 0.5, seed=21, dist="int", ld_pad=5)
+    rc, got = run(p, algo)
+    assert_bit_exact(p, got)
+    check_padding(p, got)
+
+
+def test_persistent_many_tiles():
+    """More output tiles than SMs: every CTA walks several tiles and both TMEM
+    accumulators are reused."""
+    for algo in SPLIT:
+        p = wl.make_problem("N", "N", 4100, 4100, 64, 1.0, -1.0, seed=22)
+        rc, got = run(p, algo)
+        cols = np.r_[0:3, 255:258, 4097:4100]
+        assert_within_bound(p, got, cols=cols)
+
+
+# ------------------------------------------------ log-uniform magnitudes --
+
+@pytest.mark.parametrize("k", (8, 64, 1000))
+@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x6"))
+def test_log_uniform_small(algo, k):
+    p = wl.make_problem("N", "N", 200, 150, k, 1.0, 0.0, seed=23, dist="logu")
+    rc, got = run(p, algo)
+    assert_within_bound(p, got)
+
+
+def test_bf16x3_log_uniform_large_k():
+    p = wl.make_problem("T", "N", 200, 150, 4096, 1.0, 0.0, seed=24, dist="logu")
+    rc, got = run(p, "bf16x3")
+    assert_within_bound(p, got)
+
+
+# ------------------------------------------------ BLAS special cases ----
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_quick_return_and_alpha_zero(algo):
+    import paper_1912_04379_gb300 as gb
+    torch = torch_gpu()
+    m, n, k = 37, 29, 11
+    A = torch.full((k, m), float("nan"), device="cuda").t()       # column-major m x k
+    B = torch.full((n, k), float("nan"), device="cuda").t()
+    C0 = torch.randn(n, m, device="cuda").t()
+    # alpha = 0, beta = 1: nothing happens (and NaN A/B are never read)
+    C = C0.clone()
+    gb.sgemm(A, B, C, alpha=0.0, beta=1.0, algo=algo)
+    torch.cuda.synchronize()
+    assert torch.equal(C, C0)
+    # alpha = 0, beta = -2: C = beta*C, A and B not read
+    C = C0.clone()
+    gb.sgemm(A, B, C, alpha=0.0, beta=-2.0, algo=algo)
+    torch.cuda.synchronize()
+    assert torch.equal(C, -2.0 * C0)
+    # beta = 0: C not read (NaN in C must not propagate)
+    A2 = torch.randn(k, m, device="cuda").t()
+    B2 = torch.randn(n, k, device="cuda").t()
+    C = torch.full((n, m), float("nan"), device="cuda").t()
+    gb.sgemm(A2, B2, C, alpha=1.0, beta=0.0, algo=algo)
+    torch.cuda.synchronize()
+    assert torch.isfinite(C).all()
+    # K = 0: C = beta*C
+    Ak = torch.empty(0, m, device="cuda").t()
+    Bk = torch.empty(n, 0, device="cuda").t()
+    C = C0.clone()
+    gb.sgemm(Ak, Bk, C, alpha=1.0, beta=0.5, algo=algo)
+    torch.cuda.synchronize()
+    assert torch.equal(C, 0.5 * C0)
+    # M = 0 / N = 0: nothing enqueued
+    gb.sgemm(A2[:0], B2, C[:0], alpha=1.0, beta=0.0, algo=algo)
+    gb.sgemm(A2, B2[:, :0], C[:, :0], alpha=1.0, beta=0.0, algo=algo)
+
+
+def test_workspace_errors():
+    import paper_1912_04379_gb300 as gb
+    from paper_1912_04379_gb300 import _lib
+    torch = torch_gpu()
+    A = torch.randn(64, 64, device="cuda")
+    need = gb.workspace_size("bf16x3", "N", "N", 64, 64, 64)
+    ws = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    small = ws[: need - 1]
+    C = torch.empty_like(A)
+    rc = gb.sgemm_raw("N", "N", 64, 64, 64, 1.0, A.data_ptr(), 64, A.data_ptr(), 64, 0.0,
+                      C.data_ptr(), 64, algo="bf16x3", workspace=small, check=False)
+    assert rc == _lib.GB_ERR_WORKSPACE
+    mis = ws[8: 8 + need]
+    rc = gb.sgemm_raw("N", "N", 64, 64, 64, 1.0, A.data_ptr(), 64, A.data_ptr(), 64, 0.0,
+                      C.data_ptr(), 64, algo="bf16x3", workspace=mis, check=False)
+    assert rc == _lib.GB_ERR_WORKSPACE
+    rc = gb.sgemm_raw("N", "N", 64, 64, 64, 1.0, A.data_ptr(), 64, A.data_ptr(), 64, 0.0,
+                      C.data_ptr(), 64, algo="bf16x3", workspace=ws[:need], check=False)
+    assert rc == 0
+    torch.cuda.synchronize()
+
+
+def test_device_error_word_clean():
+    import paper_1912_04379_gb300 as gb
+    torch_gpu()
+    h = gb.default_handle()
+    p = wl.make_problem("N", "N", 300, 300, 300, 1.0, 0.0, seed=25)
+    for algo in SPLIT:
+        rc, got = run(p, algo, handle=h)
+        assert h.device_error() == (0, 0)
