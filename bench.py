@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""SGEMM throughput on one GB300: split-precision tensor-core SGEMM vs plain
+FP32 SIMT at 8192^3, at equal error bound.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full SGEMM C <- alpha*A*B + beta*C at M = N = K = 8192 (column-
+major, 'N','N', entries random sign x 2^U(-20,20), seed 2, alpha = 1, beta = 0):
+split/pack of A, split/pack of B, then the tcgen05 kernel - exactly the work
+of gb_sgemm, issued as gb_sgemm_pack x 2 + gb_sgemm_compute so that CUDA
+events between the calls time the dominant kernel live. Inputs (256 MiB
+each) are larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). With --gpus N > 1 (launched by torchrun) every
+rank runs an independent replica (the path has no exchange step): value =
+all ranks' flops / the slowest rank's time. --impl reference times the CPU
+oracle (the plain FP64 triple loop) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SGEMM TFLOP/s at 8192^3: split tensor-core vs plain FP32 SIMT at equal error bound"
+M = N = K = 8192
+SEED = 2
+ALGO = "bf16x3"
+# Per-launch DRAM traffic of the tensor-core kernel at 8192^3 bf16x3 from one
+# ncu capture, valid only for the kernel source it was taken on.
+TRAFFIC = {"source_sha": None, "bytes": None}
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--clocks-log", default=None)
+    ap.add_argument("--profile", default=None, metavar="M,N,K[,ALGO]",
+                    help="run one warm-up and one measured SGEMM of this shape (pack A, pack B, "
+                         "compute) and exit; a small case for ncu captures")
+    return ap.parse_args()
+
+
+def run_profile_case(spec):
+    """Two SGEMMs of one shape on device-resident random inputs (ncu target)."""
+    import torch
+    import paper_1912_04379_gb300 as gb
+    parts = spec.split(",")
+    m, n, k = (int(x) for x in parts[:3])
+    algo = parts[3] if len(parts) > 3 else ALGO
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    A = (torch.rand((k, m), device="cuda", generator=g) * 2 - 1).t()
+    B = (torch.rand((n, k), device="cuda", generator=g) * 2 - 1).t()
+    C = gb.colmajor(m, n)
+    if algo == "simt":
+        for _ in range(2):
+            gb.sgemm(A, B, C, algo="simt")
+    else:
+        Ap = torch.empty(gb.pack_size(algo, "A", m, k), dtype=torch.uint8, device="cuda")
+        Bp = torch.empty(gb.pack_size(algo, "B", n, k), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            gb.pack_raw(algo, "A", "N", m, k, A.data_ptr(), m, Ap)
+            gb.pack_raw(algo, "B", "N", n, k, B.data_ptr(), k, Bp)
+            gb.compute_raw(algo, m, n, k, 1.0, Ap, Bp, 0.0, C.data_ptr(), m)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": [m, n, k, algo], "ok": True}), flush=True)
+    return 0
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "sgemm M=N=K=8192, transa=transb='N', lda=ldb=ldc=8192, entries "
+                       "random sign x 2^U(-20,20) (seed 2), alpha=1, beta=0",
+           "m": M, "n": N, "k": K, "algo": ALGO,
+           "l2": "inputs larger than L2 (256 MiB per matrix); no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, log_path=None):
+        self.proc = None
+        self.gpu_index = gpu_index
+        self.log_path = log_path
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        if self.log_path:
+            with open(self.log_path, "w") as f:
+                f.write(out)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = [x.strip() for x in cvd.split(",")]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ------------------------------------------------------- CPU baseline ----
+
+def cpu_oracle_sample(p, target_s, cols_hint=None):
+    """Time the oracle on a sample of whole output columns of the workload."""
+    import numpy as np
+    import oracle
+    threads = oracle.max_threads()
+    if cols_hint is None:
+        t0 = time.perf_counter()
+        oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta, p.C,
+                     p.ldc, cols=np.arange(threads))
+        t1 = time.perf_counter() - t0
+        ncols = int(max(threads, min(p.n, threads * max(1, round(target_s / max(t1, 1e-3))))))
+    else:
+        ncols = cols_hint
+    cols = np.linspace(0, p.n - 1, ncols).round().astype(np.int64)
+    t0 = time.perf_counter()
+    C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta,
+                          p.C, p.ldc, cols=cols)
+    dt = time.perf_counter() - t0
+    return cols, C64, D, dt, threads
+
+
+# --------------------------------------------------------- reference -----
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import workloads as wl
+    import oracle
+    p = wl.split_case(M, N, K, seed=SEED)
+    threads = oracle.max_threads()
+    ncols = threads                                   # one output column per thread and step
+    step_cols = [
+        (i * ncols + j * 611) % N for i in range(args.steps + args.warmup) for j in range(ncols)]
+    import numpy as np
+    times = []
+    for s in range(args.warmup + args.steps):
+        cols = np.array(step_cols[s * ncols:(s + 1) * ncols], dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta, p.C,
+                     p.ldc, cols=cols)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    flops = 2.0 * M * K * ncols * len(times)
+    value = flops / total / 1e12
+    sample = (f"{ncols} whole output columns (of {N}) per step, each M=8192 x K=8192 dot "
+              "products in FP64 plus the bound denominator")
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config({"algo": "cpu-oracle"}),
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- ours ----
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("tc_sgemm.cu", "split_pack.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1912_04379_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import workloads as wl
+    import paper_1912_04379_gb300 as gb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = wl.split_case(M, N, K, seed=SEED)
+    h = gb.Handle(dev)
+    A_full, A = gb.from_fortran(p.A, device=dev)
+    B_full, B = gb.from_fortran(p.B, device=dev)
+    C = gb.colmajor(M, N, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    size_a = gb.pack_size(ALGO, "A", M, K)
+    size_b = gb.pack_size(ALGO, "B", N, K)
+    Ap = torch.empty(size_a, dtype=torch.uint8, device=dev)
+    Bp = torch.empty(size_b, dtype=torch.uint8, device=dev)
+
+    def step():
+        gb.pack_raw(ALGO, "A", "N", M, K, A.data_ptr(), M, Ap, handle=h)
+        gb.pack_raw(ALGO, "B", "N", N, K, B.data_ptr(), K, Bp, handle=h)
+
+    def compute():
+        gb.compute_raw(ALGO, M, N, K, 1.0, Ap, Bp, 0.0, C.data_ptr(), M, handle=h)
+
+    for _ in range(args.warmup):
+        step()
+        compute()
+    barrier()
+    sampler = ClockSampler(gpu_index(local_rank), args.clocks_log) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0.0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i][0].record(stream)
+        compute()
+        ev[i][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = e0.elapsed_time(e1)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    ms_step = max_over_ranks(total_ms / args.steps)
+    kern_ms = max_over_ranks(kern_ms)
+    flops = 2.0 * M * N * K
+    value = world * flops / (ms_step * 1e-3) / 1e12
+    err_rc, site = h.device_error()
+    if err_rc != 0:
+        raise RuntimeError(f"device wait timeout at site {site}")
+
+    # -------- comparison arms on the same inputs (same GPU, same call path)
+    def time_algo(algo, steps, out):
+        ws_n = gb.workspace_size(algo, "N", "N", M, N, K)
+        ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            gb.sgemm_raw("N", "N", M, N, K, 1.0, A.data_ptr(), M, B.data_ptr(), K, 0.0,
+                         out.data_ptr(), M, algo=algo, handle=h, workspace=ws)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(steps):
+            gb.sgemm_raw("N", "N", M, N, K, 1.0, A.data_ptr(), M, B.data_ptr(), K, 0.0,
+                         out.data_ptr(), M, algo=algo, handle=h, workspace=ws)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / steps
+        return {"value": flops / (ms * 1e-3) / 1e12, "ms_per_step": ms, "steps": steps}
+
+    outs = {"simt": gb.colmajor(M, N, device=dev)}
+    arms = {"simt": time_algo("simt", max(3, args.steps // 20), outs["simt"])}
+    for algo in ("tf32x3", "bf16x6"):
+        outs[algo] = gb.colmajor(M, N, device=dev)
+        arms[algo] = time_algo(algo, max(3, args.steps // 5), outs[algo])
+    outs[ALGO] = C
+
+    # -------- end to end: pinned host buffers, copies inside the timed region
+    A_h = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()     # (cols, ld) = storage
+    B_h = torch.from_numpy(np.ascontiguousarray(p.B.T)).pin_memory()
+    C_h = torch.empty((N, M), dtype=torch.float32).pin_memory()
+    A_d = torch.empty_like(A_h, device=dev)
+    B_d = torch.empty_like(B_h, device=dev)
+    C_d = torch.empty((N, M), dtype=torch.float32, device=dev)
+    ws_n = gb.workspace_size(ALGO, "N", "N", M, N, K)
+    ws = torch.empty(ws_n, dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        A_d.copy_(A_h, non_blocking=True)
+        B_d.copy_(B_h, non_blocking=True)
+        gb.sgemm_raw("N", "N", M, N, K, 1.0, A_d.data_ptr(), M, B_d.data_ptr(), K, 0.0,
+                     C_d.data_ptr(), M, algo=ALGO, handle=h, workspace=ws)
+        C_h.copy_(C_d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, args.steps // 10)
+    barrier()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(s0.elapsed_time(s1) / e2e_steps)
+    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4,
+           "d2h_bytes_per_step": C_h.numel() * 4}
+
+    peaks, peak_kind = load_peaks()
+    tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
+    achieved = tensor_flops / (kern_ms * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    sha = source_sha()
+    traffic = TRAFFIC["bytes"] if TRAFFIC["source_sha"] == sha else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "tc_sgemm_kernel<bf16x3>",
+                "kernel_ms": kern_ms, "peak_kind": f"{peak_kind} bf16 dense (burst)",
+                "counted": "3 x 2MNK executed BF16 tensor flops per launch"}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "compute": "3 BF16 products per FP32 product (hi*hi + hi*lo + lo*hi), FP32 accumulate",
+            "data": "synthetic", "config": workload_config(
+                {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+            "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
+            "arms": arms, "clocks": clocks, "source_sha": sha}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cols, C64, D, dt, threads = cpu_oracle_sample(p, args.cpu_seconds)
+        cpu_val = 2.0 * M * K * len(cols) / dt / 1e12
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "TFLOP/s", "cores": threads,
+                                "kind": "oracle", "seconds": dt,
+                                "sample": f"{len(cols)} whole output columns of the 8192^3 "
+                                          "product (FP64 triple loop + bound denominator)"}
+        # accuracy of every arm on the sampled columns (GPU FP64 error report)
+        idx = torch.from_numpy(cols).to(dev)
+        C64_d = torch.from_numpy(np.ascontiguousarray(C64.T)).to(dev).t()
+        D_d = torch.from_numpy(np.ascontiguousarray(D.T)).to(dev).t()
+        acc = {}
+        for algo, out in outs.items():
+            sub = out.index_select(1, idx).t().contiguous().t()      # column-major copy
+            rep = gb.err_report(sub, C64_d, D_d, K, handle=h)
+            acc[algo] = {"max_ratio": rep["max_ratio"], "median_ratio": rep["median_ratio"],
+                         "normwise": rep["normwise"], "n_fail": rep["n_fail"],
+                         "elements": rep["count"]}
+        line["accuracy"] = {"bound": "|C-C64| <= 2*K*2^-24*(|A||B|)_ij (beta=0)",
+                            "sample_columns": len(cols), "by_algo": acc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.gpus != world and world == 1 and args.gpus > 1:
+        print(json.dumps({"error": "use torchrun for --gpus > 1"}), flush=True)
+        return 2
+    if args.profile:
+        return run_profile_case(args.profile)
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

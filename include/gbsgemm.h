@@ -69,8 +69,14 @@ enum {
  *  GB_ALGO_SPLIT_BF16X6 a = b0 + b1 + b2 in BF16 (exact for FP32 inputs);
  *                       the six products with weight >= 2^-16:
  *                       b0b0 b0b1 b1b0 b0b2 b1b1 b2b0.
- *  GB_ALGO_AUTO         the library picks (currently SPLIT_BF16X3 when
- *                       K >= 1024, else SPLIT_TF32X3 when K >= 16, else SIMT). */
+ *  GB_ALGO_AUTO         the library picks: SPLIT_BF16X3 when K >= 1024,
+ *                       SPLIT_BF16X6 when 4 <= K < 1024, else SIMT.
+ * Error per element, D = |alpha||op(A)||op(B)| + |beta||C|, u = 2^-24:
+ *  SIMT       |C - C_exact| <= 2*max(K,1)*u*D
+ *  split x    (2*max(K,1)*u + e_x)*D with e_x the dropped cross terms:
+ *             TF32X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24 (x 1.01),
+ *  so a split meets the plain SIMT bound once K >= 16 (TF32X3), 1024
+ *  (BF16X3) or 4 (BF16X6); AUTO only picks an algorithm above its threshold. */
 typedef enum {
     GB_ALGO_AUTO = -1,
     GB_ALGO_SIMT = 0,
@@ -117,6 +123,31 @@ GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb,
                     const float *B, int64_t ldb,
                     float beta, float *C, int64_t ldc,
                     void *workspace, size_t ws_bytes, void *stream);
+
+/* Pack-once, multiply-many interface of the split algorithms (the paper
+ * re-buffers B' into a contiguous block before the inner loop, Sec. 3;
+ * here a whole operand is split and re-laid out once and can then be reused
+ * across calls, e.g. a weight matrix).
+ *
+ * gb_sgemm_pack_size: bytes of one packed operand. which = 'A' packs op(A)
+ * (mn = M rows, K columns); which = 'B' packs op(B) (mn = N columns, K rows).
+ * Layout (opaque to callers): terms x mn x kpad elements, K contiguous.
+ * gb_sgemm_pack: split and pack op(X) of stored matrix X (trans, ldx as in
+ * gb_sgemm: X is mn x K if trans is 'N' and which is 'A', and so on) into
+ * `packed` (256-byte aligned, >= gb_sgemm_pack_size bytes).
+ * gb_sgemm_compute: C <- alpha*op(A)*op(B) + beta*C from packed operands made
+ * with the same algorithm and K. Together, pack A + pack B + compute do
+ * exactly what gb_sgemm does for a split algorithm.
+ * algo must be a split algorithm or AUTO resolved by K to one
+ * (GB_ERR_UNSUPPORTED for SIMT). Negative codes: -1 which/trans invalid
+ * (pack), -3 mn or M < 0, -4 N < 0, -5 K < 0, -8 ldx too small, -13 ldc. */
+GB_API int gb_sgemm_pack_size(gb_algo_t algo, char which, int64_t mn, int64_t k, size_t *bytes);
+GB_API int gb_sgemm_pack(gb_handle_t h, gb_algo_t algo, char which, char trans, int64_t mn,
+                         int64_t k, const float *X, int64_t ldx, void *packed, size_t bytes,
+                         void *stream);
+GB_API int gb_sgemm_compute(gb_handle_t h, gb_algo_t algo, int64_t m, int64_t n, int64_t k,
+                            float alpha, const void *Apacked, const void *Bpacked, float beta,
+                            float *C, int64_t ldc, void *stream);
 
 /* Gradients of C = alpha*op(A)*op(B) + beta*C_in with respect to A, B and
  * C_in, given dC = dL/dC (M x N, lddc). Any of dA, dB, dCin may be NULL to

@@ -124,16 +124,17 @@ def dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, nthreads=0):
     return out
 
 
-def bound(D, k):
-    """Per-element acceptance bound 2*max(K,1)*u*D, u = 2^-24.
+def bound(D, k, extra=0.0):
+    """Per-element acceptance bound (2*max(K,1)*u + extra)*D, u = 2^-24.
 
     The stated bound is 2*K*u*D; at K = 0 the result is beta*C rounded once
-    to FP32, so max(K, 1) keeps the bound defined there.
+    to FP32, so max(K, 1) keeps the bound defined there. `extra` adds a
+    fixed relative term (the truncation of a split-precision product).
     """
-    return 2.0 * max(int(k), 1) * U32 * np.asarray(D, dtype=np.float64)
+    return (2.0 * max(int(k), 1) * U32 + extra) * np.asarray(D, dtype=np.float64)
 
 
-def err_report(C, C64, D, k):
+def err_report(C, C64, D, k, extra=0.0):
     """Error of an FP32 result C against the double oracle (C64, D).
 
     ratio_ij = |C_ij - C64_ij| / bound_ij, with ratio 0 where both are 0 and
@@ -145,10 +146,11 @@ def err_report(C, C64, D, k):
     """
     c = np.asarray(C, dtype=np.float64).ravel(order="F")
     r = np.asarray(C64, dtype=np.float64).ravel(order="F")
-    b = bound(np.asarray(D).ravel(order="F"), k)
+    b = bound(np.asarray(D).ravel(order="F"), k, extra)
     fin = np.isfinite(c) & np.isfinite(r)
     same_nf = (~fin) & ((np.isnan(c) & np.isnan(r)) | (c == r))
-    diff = np.where(fin, np.abs(c - r), 0.0)
+    with np.errstate(invalid="ignore"):
+        diff = np.where(fin, np.abs(c - r), 0.0)
     with np.errstate(divide="ignore", invalid="ignore"):
         ratio = np.where(diff == 0.0, 0.0, np.where(b > 0.0, diff / b, np.inf))
     ratio = np.where(fin, ratio, np.where(same_nf, 0.0, np.inf))

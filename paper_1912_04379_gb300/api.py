@@ -145,6 +145,38 @@ def sgemm_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, C_pt
     return rc
 
 
+def pack_size(algo, which, mn, k) -> int:
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    _lib.check("gb_sgemm_pack_size",
+               lib.gb_sgemm_pack_size(_lib.ALGOS[algo], which.encode(), mn, k, ctypes.byref(out)))
+    return out.value
+
+
+def pack_raw(algo, which, trans, mn, k, X_ptr, ldx, packed, handle=None, stream=None,
+             check=True) -> int:
+    """Split and pack op(A) (which='A', mn=M) or op(B) (which='B', mn=N) into
+    the uint8 CUDA tensor `packed`."""
+    h = handle or default_handle()
+    rc = h.lib.gb_sgemm_pack(h.h, _lib.ALGOS[algo], which.encode(), trans.encode(), mn, k,
+                             X_ptr, ldx, packed.data_ptr(), packed.numel(), _stream_ptr(stream))
+    if check:
+        _lib.check("gb_sgemm_pack", rc)
+    return rc
+
+
+def compute_raw(algo, m, n, k, alpha, Apacked, Bpacked, beta, C_ptr, ldc, handle=None,
+                stream=None, check=True) -> int:
+    """C <- alpha*op(A)*op(B) + beta*C from packed operands."""
+    h = handle or default_handle()
+    rc = h.lib.gb_sgemm_compute(h.h, _lib.ALGOS[algo], m, n, k, float(alpha),
+                                Apacked.data_ptr(), Bpacked.data_ptr(), float(beta), C_ptr, ldc,
+                                _stream_ptr(stream))
+    if check:
+        _lib.check("gb_sgemm_compute", rc)
+    return rc
+
+
 def sgemm(A, B, C, alpha=1.0, beta=0.0, transa="N", transb="N", algo="auto", handle=None,
           stream=None):
     """C <- alpha*op(A)*op(B) + beta*C in place on column-major tensors."""

@@ -49,10 +49,15 @@ int split_mode(gb_algo_t algo) {
     }
 }
 
+// AUTO picks the fastest algorithm whose worst-case error stays within the
+// FP32 bound 2*K*u*D for this K. Each split drops a fixed relative term per
+// product (BF16 x 2: 3*2^-16, BF16 x 3: 2*2^-24); requiring it to use at
+// most half of 2*K*u gives K >= 1024 for BF16 x 2 and K >= 4 for BF16 x 3
+// (which is also faster than TF32 x 2 at the same accuracy class).
 gb_algo_t resolve_algo(gb_algo_t algo, int64_t k) {
     if (algo != GB_ALGO_AUTO) return algo;
     if (k >= 1024) return GB_ALGO_SPLIT_BF16X3;
-    if (k >= 16) return GB_ALGO_SPLIT_TF32X3;
+    if (k >= 4) return GB_ALGO_SPLIT_BF16X6;
     return GB_ALGO_SIMT;
 }
 
@@ -66,6 +71,41 @@ size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
+
+// Bytes of one packed operand (mn rows of op(A), or mn columns of op(B)).
+size_t packed_bytes(int mode, int64_t mn, int64_t k) {
+    return (size_t)split_parts(mode) * (size_t)split_kpad(mode, k) *
+           (size_t)split_elem_bytes(mode) * (size_t)mn;
+}
+
+// Split + pack one operand. a_side: op(A) (element (i,p) = op(A)[i,p]);
+// else op(B)^T (element (j,p) = op(B)[p,j]).
+cudaError_t pack_operand(int mode, bool a_side, bool trans, int64_t mn, int64_t k,
+                         const float *X, int64_t ldx, void *out, cudaStream_t s) {
+    const int64_t kpad = split_kpad(mode, k);
+    // op(A): stored A is K-contiguous iff transposed; op(B)^T: stored B is
+    // K-contiguous iff NOT transposed.
+    const bool kcontig = a_side ? trans : !trans;
+    return launch_split_pack(mode, kcontig, mn, k, X, ldx, out, kpad, mn * kpad, s);
+}
+
+int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, float alpha,
+                   const void *Ap, const void *Bp, float beta, float *C, int64_t ldc,
+                   cudaStream_t s) {
+    const int64_t kpad = split_kpad(mode, k);
+    TcArgs t{};
+    t.mode = mode;
+    t.m = m; t.n = n; t.k = k; t.kpad = kpad;
+    t.alpha = alpha; t.beta = beta;
+    t.Ap = Ap; t.Bp = Bp;
+    t.a_part_stride = m * kpad; t.b_part_stride = n * kpad;
+    t.C = C; t.ldc = ldc;
+    t.dstate = h->dstate;
+    t.wait_limit = h->wait_limit;
+    t.sm_count = h->sm_count;
+    cudaError_t e = launch_tc_sgemm(t, s);
+    return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
+}
 
 int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_t n, int64_t k,
                float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
@@ -87,28 +127,12 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     const int mode = split_mode(algo);
     const size_t need = split_ws_bytes(mode, m, n, k);
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
-    const int64_t kpad = split_kpad(mode, k);
-    const size_t eb = (size_t)split_elem_bytes(mode);
     char *Ap = static_cast<char *>(ws);
-    char *Bp = Ap + round_up((size_t)split_parts(mode) * kpad * eb * (size_t)m, 1024);
-    // op(A)[i,p]: stored A is K-contiguous iff transposed.
-    cudaError_t e = launch_split_pack(mode, is_trans(ta), m, k, A, lda, Ap, kpad, m * kpad, s);
-    // op(B)^T[j,p] = op(B)[p,j]: stored B is K-contiguous iff NOT transposed.
-    if (e == cudaSuccess)
-        e = launch_split_pack(mode, !is_trans(tb), n, k, B, ldb, Bp, kpad, n * kpad, s);
+    char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
+    cudaError_t e = pack_operand(mode, true, is_trans(ta), m, k, A, lda, Ap, s);
+    if (e == cudaSuccess) e = pack_operand(mode, false, is_trans(tb), n, k, B, ldb, Bp, s);
     if (e != cudaSuccess) return GB_ERR_CUDA;
-    TcArgs t{};
-    t.mode = mode;
-    t.m = m; t.n = n; t.k = k; t.kpad = kpad;
-    t.alpha = alpha; t.beta = beta;
-    t.Ap = Ap; t.Bp = Bp;
-    t.a_part_stride = m * kpad; t.b_part_stride = n * kpad;
-    t.C = C; t.ldc = ldc;
-    t.dstate = h->dstate;
-    t.wait_limit = h->wait_limit;
-    t.sm_count = h->sm_count;
-    e = launch_tc_sgemm(t, s);
-    return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
+    return compute_packed(h, mode, m, n, k, alpha, Ap, Bp, beta, C, ldc, s);
 }
 
 // Backward products (see gb_sgemm_backward in the header for the formulas).
@@ -217,6 +241,65 @@ GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb, int
                     size_t ws_bytes, void *stream) {
     return sgemm_impl(h, algo, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                       workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+GB_API int gb_sgemm_pack_size(gb_algo_t algo, char which, int64_t mn, int64_t k, size_t *bytes) {
+    if (which != 'A' && which != 'a' && which != 'B' && which != 'b') return -1;
+    if (mn < 0) return -3;
+    if (k < 0) return -5;
+    if (!bytes) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    const int mode = split_mode(resolve_algo(algo, k));
+    if (mode < 0) return GB_ERR_UNSUPPORTED;
+    *bytes = packed_bytes(mode, mn, k);
+    return GB_OK;
+}
+
+GB_API int gb_sgemm_pack(gb_handle_t h, gb_algo_t algo, char which, char trans, int64_t mn,
+                         int64_t k, const float *X, int64_t ldx, void *packed, size_t bytes,
+                         void *stream) {
+    const bool a_side = which == 'A' || which == 'a';
+    if (!a_side && which != 'B' && which != 'b') return -1;
+    if (!trans_ok(trans)) return -1;
+    if (mn < 0) return -3;
+    if (k < 0) return -5;
+    // stored rows: op(A) = A is M x K, A^T stored K x M; op(B) = B is K x N, B^T stored N x K
+    const int64_t rows = a_side ? (is_trans(trans) ? k : mn) : (is_trans(trans) ? mn : k);
+    if (ldx < max1(rows)) return -8;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int mode = split_mode(resolve_algo(algo, k));
+    if (mode < 0) return GB_ERR_UNSUPPORTED;
+    if (mn == 0 || k == 0) return GB_OK;
+    if (!X) return GB_ERR_ARG;
+    if (!packed || bytes < packed_bytes(mode, mn, k) ||
+        (reinterpret_cast<uintptr_t>(packed) & 255))
+        return GB_ERR_WORKSPACE;
+    return cuda_status(pack_operand(mode, a_side, is_trans(trans), mn, k, X, ldx, packed,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+GB_API int gb_sgemm_compute(gb_handle_t h, gb_algo_t algo, int64_t m, int64_t n, int64_t k,
+                            float alpha, const void *Apacked, const void *Bpacked, float beta,
+                            float *C, int64_t ldc, void *stream) {
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    if (ldc < max1(m)) return -13;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int mode = split_mode(resolve_algo(algo, k));
+    if (mode < 0) return GB_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (m == 0 || n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
+    if (!C) return GB_ERR_ARG;
+    if (alpha == 0.f || k == 0) return cuda_status(launch_scale_c(m, n, beta, C, ldc, s));
+    if (!Apacked || !Bpacked || (reinterpret_cast<uintptr_t>(Apacked) & 255) ||
+        (reinterpret_cast<uintptr_t>(Bpacked) & 255))
+        return GB_ERR_WORKSPACE;
+    return compute_packed(h, mode, m, n, k, alpha, Apacked, Bpacked, beta, C, ldc, s);
 }
 
 GB_API int gb_sgemm_backward_workspace_size(gb_algo_t algo, char ta, char tb, int64_t m,

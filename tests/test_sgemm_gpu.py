@@ -27,7 +27,7 @@ def test_plain_384(algo):
     p = wl.plain_384()
     rc, got = run(p, algo)
     assert rc == 0
-    assert_within_bound(p, got)
+    assert_within_bound(p, got, algo=algo)
 
 
 @pytest.mark.parametrize("algo", ALGOS)
@@ -64,7 +64,7 @@ def test_simt_sweep_large_sampled(n, ta, tb):
 def test_split_sweep(algo, n, ta, tb):
     p = wl.sweep_case(n, ta, tb)
     rc, got = run(p, algo)
-    assert_within_bound(p, got)
+    assert_within_bound(p, got, algo=algo)
     check_padding(p, got)
 
 
@@ -82,7 +82,7 @@ def test_ragged(algo, shape, ta, tb):
     p = wl.make_problem(ta, tb, m, n, k, -0.75, 1.25, seed=m * 7919 + n * 31 + k, ld_pad=3)
     rc, got = run(p, algo)
     assert rc == 0
-    assert_within_bound(p, got)
+    assert_within_bound(p, got, algo=algo)
     check_padding(p, got)
 
 
@@ -102,7 +102,7 @@ def test_persistent_many_tiles():
         p = wl.make_problem("N", "N", 4100, 4100, 64, 1.0, -1.0, seed=22)
         rc, got = run(p, algo)
         cols = np.r_[0:3, 255:258, 4097:4100]
-        assert_within_bound(p, got, cols=cols)
+        assert_within_bound(p, got, cols=cols, algo=algo)
 
 
 # ------------------------------------------------ log-uniform magnitudes --
@@ -112,13 +112,13 @@ def test_persistent_many_tiles():
 def test_log_uniform_small(algo, k):
     p = wl.make_problem("N", "N", 200, 150, k, 1.0, 0.0, seed=23, dist="logu")
     rc, got = run(p, algo)
-    assert_within_bound(p, got)
+    assert_within_bound(p, got, algo=algo)
 
 
 def test_bf16x3_log_uniform_large_k():
     p = wl.make_problem("T", "N", 200, 150, 4096, 1.0, 0.0, seed=24, dist="logu")
     rc, got = run(p, "bf16x3")
-    assert_within_bound(p, got)
+    assert_within_bound(p, got, algo="bf16x3")
 
 
 # ------------------------------------------------ BLAS special cases ----
