@@ -19,8 +19,9 @@
 //   * C block in registers  -> a 128 x BN FP32 accumulator in tensor memory
 //     (TMEM), two of them so the epilogue of one tile overlaps the next;
 //   * L1 staging + prefetch -> a ring of shared-memory stages filled by TMA
-//     (cp.async.bulk.tensor, 128-byte swizzle) one step ahead of the MMAs,
-//     handshaken with mbarriers;
+//     (cp.async.bulk.tensor) ahead of the MMAs, handshaken with mbarriers:
+//     four 48 KiB stages of 64-byte rows (64-byte swizzle) for long K loops,
+//     two 96 KiB stages of 128-byte rows (128-byte swizzle) for short ones;
 //   * the inner loop        -> tcgen05.mma (M = 128, N = BN, K = 16 BF16 or
 //     8 TF32 per instruction) issued by one thread;
 //   * L2 blocking           -> a persistent grid (one CTA per SM) walking the
@@ -37,6 +38,7 @@
 // before the CTA exits. No trap, no unbounded spin.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <stdlib.h>
 
 #include "internal.h"
 
@@ -44,7 +46,6 @@ namespace gb {
 namespace {
 
 constexpr int BM = 128;
-constexpr int ROW_BYTES = 128;                 // one swizzle row: 64 BF16 or 32 TF32
 constexpr int NUM_THREADS = 192;
 constexpr int GROUP_M = 16;                    // tile raster: 16 M-tiles per group
 // Limit for the final drains of in-flight copies and MMAs. These always
@@ -138,19 +139,21 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms
-// stacked along M/N. Fields: start address >> 4 (bits 0-13), leading byte
-// offset >> 4 (16-29; unused for swizzled K-major, set to 1), stride byte
-// offset >> 4 (32-45; 1024 bytes between 8-row groups), descriptor version 1
-// (46-47), base offset 0 (49-51; atoms are 1024-byte aligned), layout type
-// 2 = 128-byte swizzle (61-63).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+// with an RB-byte swizzle (RB = 128 or 64): rows of RB bytes, 8-row swizzle
+// atoms (8*RB bytes) stacked along M/N. Fields: start address >> 4 (bits
+// 0-13), leading byte offset >> 4 (16-29; unused for swizzled K-major, set to
+// 1), stride byte offset >> 4 (32-45; 8*RB bytes between 8-row groups),
+// descriptor version 1 (46-47), base offset 0 (49-51; atoms are aligned),
+// layout type (61-63): 2 = 128-byte swizzle, 4 = 64-byte swizzle.
+template <int RB>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    static_assert(RB == 128 || RB == 64, "row bytes");
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)((8 * RB) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
     return d;
 }
 
@@ -217,8 +220,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 }
 
 // ----------------------------------------------------------- the kernel --
-template <int MODE>
+template <int MODE, int RB>
 struct Cfg {
+    static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
     static constexpr bool TF32 = MODE == 0;
     static constexpr int PARTS = MODE == 2 ? 3 : 2;
     static constexpr int NPAIRS = MODE == 2 ? 6 : 3;
@@ -262,12 +266,12 @@ __device__ __forceinline__ void tile_coords(int64_t tile, int64_t tiles_m, int64
     tn = r / gm;
 }
 
-template <int MODE>
+template <int MODE, int RB>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
                 int64_t ldc, DeviceState *dstate, uint64_t limit_ns) {
-    using CF = Cfg<MODE>;
+    using CF = Cfg<MODE, RB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -382,8 +386,8 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                         const uint32_t b0 = b_smem + (stage * CF::PARTS + sb) * CF::B_TILE;
 #pragma unroll
                         for (int ks = 0; ks < CF::KSTEPS; ++ks) {
-                            mma_issue<CF::TF32>(d_tmem, smem_desc_sw128(a0 + ks * CF::KSTEP_BYTES),
-                                                smem_desc_sw128(b0 + ks * CF::KSTEP_BYTES), idesc,
+                            mma_issue<CF::TF32>(d_tmem, smem_desc<RB>(a0 + ks * CF::KSTEP_BYTES),
+                                                smem_desc<RB>(b0 + ks * CF::KSTEP_BYTES), idesc,
                                                 accumulate);
                             accumulate = 1;
                         }
@@ -462,7 +466,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 // 3-D map over [terms][rows][kpad] (K innermost), box = BK x box_rows x 1.
 bool make_map(CUtensorMap *map, bool tf32, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
-              int parts, int box_rows, int bk) {
+              int parts, int box_rows, int bk, int row_bytes) {
     auto enc = get_encode();
     if (!enc) return false;
     const int eb = tf32 ? 4 : 2;
@@ -472,20 +476,21 @@ bool make_map(CUtensorMap *map, bool tf32, const void *ptr, int64_t k, int64_t r
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                      3, const_cast<void *>(ptr), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <int MODE>
+template <int MODE, int RB>
 cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
-    using CF = Cfg<MODE>;
+    using CF = Cfg<MODE, RB>;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<MODE>,
+        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<MODE, RB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
@@ -495,14 +500,14 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
         return cudaErrorNotSupported;
     alignas(64) CUtensorMap ma, mb;
-    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK) ||
-        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK))
+    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK, RB) ||
+        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK, RB))
         return cudaErrorInvalidValue;
     const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN);
     int grid = a.sm_count > 0 ? a.sm_count : 1;
     if (tiles < grid) grid = (int)tiles;
     const uint64_t limit_ns = (uint64_t)a.wait_limit * 1000ull;
-    tc_sgemm_kernel<MODE><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+    tc_sgemm_kernel<MODE, RB><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
         ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, a.dstate, limit_ns);
     return cudaGetLastError();
 }
@@ -510,10 +515,21 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
+    // Shared-memory row width of a k-block. 64-byte rows (64-byte swizzle,
+    // 48 KiB stages, 4 in flight) hide the TMA latency on long K loops;
+    // 128-byte rows (96 KiB stages, 2 in flight) measured slightly faster
+    // when the K loop is short (K <= 2048 at M = N = 8192). The environment
+    // variable GB_SGEMM_TC_ROW_BYTES = 64 or 128 forces one of them.
+    static const int forced = [] {
+        const char *e = getenv("GB_SGEMM_TC_ROW_BYTES");
+        const int v = e ? atoi(e) : 0;
+        return (v == 64 || v == 128) ? v : 0;
+    }();
+    const bool rb128 = forced ? forced == 128 : a.k <= 2048;
     switch (a.mode) {
-        case 0: return launch_mode<0>(a, s);
-        case 1: return launch_mode<1>(a, s);
-        case 2: return launch_mode<2>(a, s);
+        case 0: return rb128 ? launch_mode<0, 128>(a, s) : launch_mode<0, 64>(a, s);
+        case 1: return rb128 ? launch_mode<1, 128>(a, s) : launch_mode<1, 64>(a, s);
+        case 2: return rb128 ? launch_mode<2, 128>(a, s) : launch_mode<2, 64>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -190,3 +190,20 @@ def test_device_error_word_clean():
     for algo in SPLIT:
         rc, got = run(p, algo, handle=h)
         assert h.device_error() == (0, 0)
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+def test_long_k_ragged(algo, ta, tb):
+    """K > 2048 selects the four-stage, 64-byte-row pipeline; ragged M, N, K."""
+    p = wl.make_problem(ta, tb, 300, 270, 2500, 1.0, -0.5, seed=26, ld_pad=3)
+    rc, got = run(p, algo)
+    assert_within_bound(p, got, algo=algo)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+def test_long_k_integer_bit_exact(algo):
+    p = wl.make_problem("T", "N", 140, 260, 4100, 1.0, 0.5, seed=27, dist="int", ld_pad=1)
+    rc, got = run(p, algo)
+    assert_bit_exact(p, got)
