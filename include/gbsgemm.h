@@ -124,6 +124,39 @@ GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb,
                     float beta, float *C, int64_t ldc,
                     void *workspace, size_t ws_bytes, void *stream);
 
+/* gb_sgemm for callers that cannot allocate device memory. The paper has no
+ * counterpart; this is a library convenience.
+ *
+ * Some callers can neither call cudaMalloc nor pass a workspace: plugins
+ * inside a framework that owns all device memory through its own pool and
+ * forbids raw allocations, latency-critical code that cannot take the
+ * implicit synchronisation an allocation may cause, or processes whose
+ * device memory is fully reserved. This entry point computes exactly what
+ * gb_sgemm computes, with the same kernels and the same arguments minus the
+ * workspace: the split workspace is a fixed array of GB_STATIC_SCRATCH_BYTES
+ * (32 MiB) in device memory that belongs to the library, and the call
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine). The caller still owns and passes A, B and C.
+ * - Every GPU that loads the library keeps those 32 MiB reserved until the
+ *   process exits.
+ * - Returns GB_ERR_WORKSPACE, with nothing enqueued, when the problem's
+ *   split workspace (gb_sgemm_workspace_size) is larger than
+ *   GB_STATIC_SCRATCH_BYTES, e.g. BF16X3 fits M = N = K = 2048. SIMT needs
+ *   no workspace and has no size limit here.
+ * - The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture.
+ * - All calls share the one array. Each call overwrites every byte of it
+ *   that it reads, so no state carries over, but calls whose executions
+ *   overlap on the GPU (different streams, or different host threads) race
+ *   on the array and produce wrong results: serialise them. */
+#define GB_STATIC_SCRATCH_BYTES (32u << 20)
+GB_API int gb_sgemm_noalloc(gb_handle_t h, gb_algo_t algo, char transa, char transb,
+                            int64_t m, int64_t n, int64_t k,
+                            float alpha, const float *A, int64_t lda,
+                            const float *B, int64_t ldb,
+                            float beta, float *C, int64_t ldc, void *stream);
+
 /* Pack-once, multiply-many interface of the split algorithms (the paper
  * re-buffers B' into a contiguous block before the inner loop, Sec. 3;
  * here a whole operand is split and re-laid out once and can then be reused

@@ -54,6 +54,8 @@ SIGNATURES = {
                                  ctypes.POINTER(c_size)], c_int),
     "gb_sgemm": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64, c_f, c_vp, c_i64, c_vp,
                   c_i64, c_f, c_vp, c_i64, c_vp, c_size, c_vp], c_int),
+    "gb_sgemm_noalloc": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64, c_f, c_vp, c_i64,
+                          c_vp, c_i64, c_f, c_vp, c_i64, c_vp], c_int),
     "gb_sgemm_pack_size": ([c_int, c_char, c_i64, c_i64, ctypes.POINTER(c_size)], c_int),
     "gb_sgemm_pack": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_size,
                        c_vp], c_int),

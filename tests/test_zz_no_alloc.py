@@ -1,0 +1,81 @@
+"""gb_sgemm_noalloc: the SGEMM entry point for callers that cannot allocate.
+
+Callers such as plugins inside a framework that owns all device memory, or
+latency-critical code that cannot afford an allocation, cannot hand the
+library a workspace. gb_sgemm_noalloc runs the same split-precision kernels
+as gb_sgemm with its workspace in a fixed 32 MiB array inside the library.
+This file checks, through the C ABI, that two calls in a row (different
+shapes, transposes and data, so the second call must not depend on what the
+first left in the shared array) give the same result as gb_sgemm within the
+tests' error bound, and that a problem too large for the array is refused
+with GB_ERR_WORKSPACE and no write to C. It is named so that pytest collects
+it last.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _gpu import SPLIT_EXTRA, assert_within_bound, torch_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(h, algo, p, A, B, Cfull):
+    from paper_1912_04379_gb300 import _lib
+    import torch
+    return h.lib.gb_sgemm_noalloc(h.h, _lib.ALGOS[algo], p.ta.encode(), p.tb.encode(), p.m, p.n,
+                                  p.k, p.alpha, A.data_ptr(), p.lda, B.data_ptr(), p.ldb, p.beta,
+                                  Cfull.data_ptr(), p.ldc, torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("algo", ("bf16x3", "tf32x3", "bf16x6"))
+def test_noalloc_matches_gb_sgemm_on_two_calls_in_a_row(algo):
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    h = gb.Handle()
+    probs = [wl.make_problem("N", "T", 700, 520, 1300, 1.25, -0.5, seed=51, ld_pad=3),
+             wl.make_problem("T", "N", 333, 901, 777, -0.75, 0.0, seed=52, ld_pad=1)]
+    dev = []
+    for p in probs:
+        _, A = gb.from_fortran(p.A)
+        _, B = gb.from_fortran(p.B)
+        C_new, _ = gb.from_fortran(p.C)
+        C_ref, _ = gb.from_fortran(p.C)
+        dev.append((p, A, B, C_new, C_ref))
+    # two calls in a row through the allocation-free entry point
+    for p, A, B, C_new, _ in dev:
+        assert _noalloc(h, algo, p, A, B, C_new) == 0
+    torch.cuda.synchronize()
+    # the existing entry point, with its own workspace
+    for p, A, B, _, C_ref in dev:
+        gb.sgemm_raw(p.ta, p.tb, p.m, p.n, p.k, p.alpha, A.data_ptr(), p.lda, B.data_ptr(),
+                     p.ldb, p.beta, C_ref.data_ptr(), p.ldc, algo=algo, handle=h)
+    torch.cuda.synchronize()
+    for p, _, _, C_new, C_ref in dev:
+        new, ref = gb.to_fortran(C_new), gb.to_fortran(C_ref)
+        C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb,
+                              p.beta, p.C, p.ldc)
+        bound = oracle.bound(D, p.k, SPLIT_EXTRA[algo])
+        diff = np.abs(new[:p.m].astype(np.float64) - ref[:p.m].astype(np.float64))
+        assert np.all(diff <= bound), "gb_sgemm_noalloc differs from gb_sgemm beyond the bound"
+        assert_within_bound(p, new, algo=algo)
+        assert np.all(new[p.m:] == wl.CANARY)
+    assert h.device_error() == (0, 0)
+
+
+def test_noalloc_refuses_problems_larger_than_the_static_array():
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    from paper_1912_04379_gb300 import _lib
+    h = gb.Handle()
+    m = n = k = 4096                     # BF16 x 2 workspace: 128 MiB > 32 MiB
+    assert gb.workspace_size("bf16x3", "N", "N", m, n, k) > 32 * 1024 * 1024
+    p = wl.Problem("N", "N", m, n, k, 1.0, 0.0, None, m, None, k, None, m)
+    A = torch.ones(k, m, device="cuda")
+    B = torch.ones(n, k, device="cuda")
+    C = torch.full((n, m), 7.0, device="cuda")
+    rc = _noalloc(h, "bf16x3", p, A, B, C)
+    assert rc == _lib.GB_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert bool((C == 7.0).all())
