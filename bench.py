@@ -37,7 +37,7 @@ SEED = 2
 ALGO = "bf16x3"
 # Per-launch DRAM traffic of the tensor-core kernel at 8192^3 bf16x3 from one
 # ncu capture, valid only for the kernel source it was taken on.
-TRAFFIC = {"source_sha": None, "bytes": None}
+TRAFFIC = {"source_sha": "f39189961ceef909", "bytes": 2526490464}
 
 
 def env_int(name, default):
