@@ -124,6 +124,36 @@ def dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, nthreads=0):
     return out
 
 
+def op(trans, X):
+    """op(X) as a new array: X for 'N', X^T for 'T'/'C'."""
+    return np.array(X if trans in "Nn" else X.T, order="F")
+
+
+def sgemm_backward(ta, tb, alpha, A, B, beta, G):
+    """Reference gradients of L = sum(G * (alpha*op(A)*op(B) + beta*C)).
+
+    A, B, G are dense float64 arrays (A and B in their stored shapes, G is
+    M x N). Differentiating the bilinear map: dL/dop(A) = alpha*G*op(B)^T,
+    dL/dop(B) = alpha*op(A)^T*G, dL/dC = beta*G; the gradient of a stored
+    operand is that of op(X), transposed back when X was transposed. Each
+    product is one call of the double-precision triple loop.
+    Returns (dA, dB, dC) as Fortran float64 arrays.
+    """
+    A = np.asfortranarray(A, dtype=np.float64)
+    B = np.asfortranarray(B, dtype=np.float64)
+    G = np.asfortranarray(G, dtype=np.float64)
+    opA, opB = op(ta, A), op(tb, B)
+    m, k = opA.shape
+    n = opB.shape[1]
+    opBt = np.asfortranarray(opB.T)
+    opAt = np.asfortranarray(opA.T)
+    d_opA = dgemm("N", "N", m, k, n, alpha, G, max(m, 1), opBt, max(n, 1), 0.0, None, 1)
+    d_opB = dgemm("N", "N", k, n, m, alpha, opAt, max(k, 1), G, max(m, 1), 0.0, None, 1)
+    dA = d_opA if ta in "Nn" else np.asfortranarray(d_opA.T)
+    dB = d_opB if tb in "Nn" else np.asfortranarray(d_opB.T)
+    return dA, dB, np.asfortranarray(beta * G)
+
+
 def bound(D, k, extra=0.0):
     """Per-element acceptance bound (2*max(K,1)*u + extra)*D, u = 2^-24.
 
