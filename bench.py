@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true",
+                    help="skip the grouped 2000-problem comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--clocks-log", default=None)
@@ -243,6 +245,76 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
+def bench_grouped(gb, h, dev, stream, reps=10):
+    """2000 uneven problems (M, N, K log-uniform in [8, 1024], seed 4): one
+    graph-captured grouped launch versus 2000 sequential plain SIMT launches
+    (host-issued, and the same launches captured in one graph)."""
+    import torch
+    import workloads as wl
+    probs = wl.grouped_problems(2000, seed=4)
+    flops = float(sum(2 * p.m * p.n * p.k for p in probs))
+    nbytes = float(sum(4 * (p.A.size + p.B.size + 2 * p.C.size) for p in probs))
+    buf, tuples, views = gb.upload_problems(probs, device=dev)
+    out = {"workload": "2000 problems, M,N,K = round(2^U(3,10)), trans N/T p=0.5, "
+                       "alpha,beta ~ U[-2,2], entries U[-1,1] (seed 4)",
+           "gflop": flops / 1e9, "min_bytes": nbytes}
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for algo in ("simt", "auto"):
+        plan = gb.GroupedPlan(tuples, algo=algo, handle=h)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.run(stream=s)
+        torch.cuda.synchronize()
+        ms = timed(g.replay, reps)
+        out[f"grouped_{algo}"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                  "gbs": nbytes / (ms * 1e-3) / 1e9, "launches": plan_launches(plan)}
+        plan.close()
+
+    def one(t, strm=None):
+        ta, tb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc = t
+        gb.sgemm_raw(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, algo="simt",
+                     handle=h, stream=strm)
+
+    def sequential():
+        for t in tuples:
+            one(t)
+    ms = timed(sequential, 2)
+    out["sequential_simt_host_issued"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                          "launches": len(tuples)}
+    g2 = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g2, stream=s):
+            for t in tuples:
+                one(t, s)
+    torch.cuda.synchronize()
+    ms = timed(g2.replay, reps)
+    out["sequential_simt_graph"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                    "launches": len(tuples)}
+    del buf
+    return out
+
+
+def plan_launches(plan):
+    """Kernels one run of the plan enqueues (the work-counter memset excluded)."""
+    return getattr(plan, "kernels_per_run", 1)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -375,6 +447,8 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4,
            "d2h_bytes_per_step": C_h.numel() * 4}
 
+    grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
+
     peaks, peak_kind = load_peaks()
     tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
     achieved = tensor_flops / (kern_ms * 1e-3) / 1e12
@@ -393,7 +467,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
-            "arms": arms, "clocks": clocks, "source_sha": sha}
+            "arms": arms, "grouped": grouped, "clocks": clocks, "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cols, C64, D, dt, threads = cpu_oracle_sample(p, args.cpu_seconds)

@@ -7,10 +7,10 @@ include/gbsgemm.h. This package is the thin Python binding: importing it
 does not load the CUDA library; the first call does, and fails loudly if
 the library is missing.
 """
-from .api import (Handle, backward_raw, colmajor, compute_raw, default_handle, err_report,
-                  from_fortran, pack_raw, pack_size, sgemm, sgemm_raw, to_fortran,
-                  workspace_size)
+from .api import (GroupedPlan, Handle, backward_raw, colmajor, compute_raw, default_handle,
+                  err_report, from_fortran, pack_raw, pack_size, sgemm, sgemm_raw, to_fortran,
+                  upload_problems, workspace_size)
 
-__all__ = ["Handle", "backward_raw", "colmajor", "compute_raw", "default_handle", "err_report",
-           "from_fortran", "pack_raw", "pack_size", "sgemm", "sgemm_raw", "to_fortran",
-           "workspace_size"]
+__all__ = ["GroupedPlan", "Handle", "backward_raw", "colmajor", "compute_raw", "default_handle",
+           "err_report", "from_fortran", "pack_raw", "pack_size", "sgemm", "sgemm_raw",
+           "to_fortran", "upload_problems", "workspace_size"]

@@ -214,6 +214,90 @@ def backward_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, d
     return rc
 
 
+def upload_problems(problems, device="cuda"):
+    """Copy host problems (objects with ta, tb, m, n, k, alpha, beta and
+    Fortran float32 arrays A, B, C with lda, ldb, ldc) into one device buffer.
+
+    Returns (buffer, tuples, c_views): `tuples` are GroupedPlan problem tuples
+    with device pointers; c_views[i] is the (ldc x n) storage view of C_i.
+    Each matrix starts on a 256-byte boundary of the buffer.
+    """
+    import numpy as np
+    sizes, offs, off = [], [], 0
+    for p in problems:
+        for X in (p.A, p.B, p.C):
+            offs.append(off)
+            sizes.append(X.size)
+            off += (X.size + 63) // 64 * 64
+    host = np.zeros(max(off, 1), dtype=np.float32)
+    i = 0
+    for p in problems:
+        for X in (p.A, p.B, p.C):
+            host[offs[i]:offs[i] + X.size] = X.ravel(order="F")
+            i += 1
+    buf = torch.from_numpy(host).to(device)
+    base = buf.data_ptr()
+    tuples, views = [], []
+    for j, p in enumerate(problems):
+        oa, ob, oc = offs[3 * j:3 * j + 3]
+        tuples.append((p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.beta, base + 4 * oa, p.lda,
+                       base + 4 * ob, p.ldb, base + 4 * oc, p.ldc))
+        ldc, cols = p.C.shape
+        views.append(buf[oc:oc + ldc * cols].view(cols, ldc).t())
+    return buf, tuples, views
+
+
+class GroupedPlan:
+    """A planned batch of independent SGEMMs for one persistent launch.
+
+    `problems` is a sequence of (transa, transb, m, n, k, alpha, beta, A_ptr,
+    lda, B_ptr, ldb, C_ptr, ldc) with device pointers as ints. `run()` only
+    enqueues work (graph-capturable); the plan owns its device tables until
+    `close()`.
+    """
+
+    def __init__(self, problems, algo="auto", handle=None):
+        self.h = handle or default_handle()
+        lib = self.h.lib
+        n = len(problems)
+        arr = (_lib.GemmProblem * max(n, 1))()
+        for i, (ta, tb, m, nn, k, alpha, beta, A, lda, B, ldb, C, ldc) in enumerate(problems):
+            arr[i] = _lib.GemmProblem(ta.encode(), tb.encode(), m, nn, k, float(alpha),
+                                      float(beta), A, lda, B, ldb, C, ldc)
+        plan = ctypes.c_void_p()
+        ws = ctypes.c_size_t(0)
+        bad = ctypes.c_int64(-1)
+        rc = lib.gb_sgemm_grouped_plan(self.h.h, _lib.ALGOS[algo], n, arr, ctypes.byref(plan),
+                                       ctypes.byref(ws), ctypes.byref(bad))
+        self.bad_index = bad.value
+        if rc != 0:
+            err = _lib.GBError("gb_sgemm_grouped_plan", rc)
+            err.bad_index = bad.value
+            raise err
+        self.plan = plan
+        self.ws_bytes = ws.value
+        self.workspace = torch.empty(max(int(ws.value), 256), dtype=torch.uint8,
+                                     device=self.h.device)
+
+    def run(self, stream=None, check=True) -> int:
+        rc = self.h.lib.gb_sgemm_grouped_run(self.plan, self.workspace.data_ptr(),
+                                             self.workspace.numel(), _stream_ptr(stream))
+        if check:
+            _lib.check("gb_sgemm_grouped_run", rc)
+        return rc
+
+    def close(self):
+        if getattr(self, "plan", None) is not None and self.plan.value:
+            self.h.lib.gb_sgemm_grouped_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def err_report(C, C64, D, k, handle=None, stream=None) -> dict:
     """GPU error report of an FP32 result against FP64 (C64, D) (column-major tensors)."""
     h = handle or default_handle()

@@ -1,0 +1,117 @@
+"""Grouped SGEMM: 2000 uneven problems in one persistent launch, checked per
+problem against the oracle; CUDA-graph replay gives the eager bits."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _gpu import torch_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_problem(p, got_storage, cols=None, algo="simt"):
+    from _gpu import SPLIT_EXTRA, STANDARD_BOUND_MIN_K
+    C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta,
+                          p.C, p.ldc, cols=cols)
+    sub = got_storage[:p.m, :] if cols is None else got_storage[:p.m, cols]
+    rep = oracle.err_report(sub, C64, D, p.k, extra=SPLIT_EXTRA[algo])
+    assert rep["max_ratio"] <= 1.0, (p.ta, p.tb, p.m, p.n, p.k, rep)
+    if p.k >= STANDARD_BOUND_MIN_K[algo]:
+        assert oracle.err_report(sub, C64, D, p.k)["max_ratio"] <= 1.0
+
+
+@pytest.fixture(scope="module")
+def group2000():
+    torch_gpu()
+    return wl.grouped_problems(2000, seed=4)
+
+
+@pytest.mark.parametrize("algo", ("simt", "auto"))
+def test_grouped_2000_against_oracle(group2000, algo):
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    probs = group2000
+    buf, tuples, views = gb.upload_problems(probs)
+    plan = gb.GroupedPlan(tuples, algo=algo)
+    plan.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(8)
+    full = set(rng.choice(len(probs), size=60, replace=False).tolist())
+    for i, p in enumerate(probs):
+        got = views[i].cpu().numpy()
+        if i in full:
+            _check_problem(p, got, algo="simt")
+        else:
+            cols = np.unique(rng.integers(0, p.n, size=min(p.n, 3)))
+            _check_problem(p, got, cols=cols, algo="simt")
+    plan.close()
+
+
+def test_grouped_graph_replay_is_bit_identical(group2000):
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    probs = group2000[:400]
+    buf, tuples, views = gb.upload_problems(probs)
+    saved = buf.clone()
+    plan = gb.GroupedPlan(tuples)
+    plan.run()
+    torch.cuda.synchronize()
+    eager = buf.clone()
+    buf.copy_(saved)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run(stream=s)
+    torch.cuda.synchronize()
+    buf.copy_(saved)                      # capture did not run the kernels; start clean
+    for _ in range(2):
+        buf.copy_(saved)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(buf, eager)
+    plan.close()
+
+
+def test_grouped_edge_cases():
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    from paper_1912_04379_gb300 import _lib
+    rng = np.random.default_rng(9)
+    probs = [
+        wl.make_problem("N", "N", 0, 5, 5, 1.0, 0.0, rng=rng),       # M = 0: nothing
+        wl.make_problem("T", "N", 7, 9, 11, 0.0, 1.0, rng=rng),      # alpha 0, beta 1: untouched
+        wl.make_problem("N", "T", 7, 9, 11, 0.0, -2.0, rng=rng),     # alpha 0: beta*C
+        wl.make_problem("T", "T", 13, 1, 0, 1.0, 0.5, rng=rng),      # K = 0: beta*C
+        wl.make_problem("N", "N", 1, 1, 1, 1.5, 0.0, rng=rng),
+        wl.make_problem("N", "N", 300, 200, 150, -1.0, 0.25, rng=rng),
+    ]
+    probs[1].A[:] = np.nan
+    probs[2].A[:] = np.nan
+    probs[2].B[:] = np.nan
+    buf, tuples, views = gb.upload_problems(probs)
+    before = [v.cpu().numpy().copy() for v in views]
+    plan = gb.GroupedPlan(tuples)
+    plan.run()
+    torch.cuda.synchronize()
+    after = [v.cpu().numpy() for v in views]
+    assert np.array_equal(after[1], before[1])
+    assert np.array_equal(after[2], np.float32(-2.0) * before[2])
+    assert np.array_equal(after[3], np.float32(0.5) * before[3])
+    for i in (4, 5):
+        _check_problem(probs[i], after[i])
+    plan.close()
+    # a bad problem is reported with its index and BLAS argument position
+    bad = list(tuples)
+    t = list(bad[4])
+    t[8] = 0                              # lda = 0 < 1
+    bad[4] = tuple(t)
+    with pytest.raises(_lib.GBError) as ei:
+        gb.GroupedPlan(bad)
+    assert ei.value.code == -8 and ei.value.bad_index == 4
+    # an empty group is valid and runs nothing
+    empty = gb.GroupedPlan([])
+    assert empty.run() == 0
+    empty.close()
