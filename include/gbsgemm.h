@@ -170,7 +170,9 @@ GB_API int gb_sgemm_noalloc(gb_handle_t h, gb_algo_t algo, char transa, char tra
  * `packed` (256-byte aligned, >= gb_sgemm_pack_size bytes).
  * gb_sgemm_compute: C <- alpha*op(A)*op(B) + beta*C from packed operands made
  * with the same algorithm and K. Together, pack A + pack B + compute do
- * exactly what gb_sgemm does for a split algorithm.
+ * what gb_sgemm does for a split algorithm, bit for bit, except that
+ * gb_sgemm may also split K across CTAs (few output tiles, K >= 1024; the
+ * partial sums then go through its workspace), which compute never does.
  * algo must be a split algorithm or AUTO resolved by K to one
  * (GB_ERR_UNSUPPORTED for SIMT). Negative codes: -1 which/trans invalid
  * (pack), -3 mn or M < 0, -4 N < 0, -5 K < 0, -8 ldx too small, -13 ldc. */

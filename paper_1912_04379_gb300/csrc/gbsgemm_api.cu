@@ -63,14 +63,37 @@ gb_algo_t resolve_algo(gb_algo_t algo, int64_t k) {
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace of a split algorithm: [A terms][B terms], each region 1 KiB aligned.
+// Workspace of a split algorithm: [A terms][B terms][split-K partials],
+// each region 1 KiB aligned; the partials exist only when K is split.
 size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
     const size_t kpad = (size_t)split_kpad(mode, k);
     const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
-    return round_up(per * (size_t)m, 1024) + round_up(per * (size_t)n, 1024);
+    const int s = split_k_factor(mode, m, n, k);
+    const size_t partials = s > 1 ? (size_t)s * (size_t)m * (size_t)n * sizeof(float) : 0;
+    return round_up(per * (size_t)m, 1024) + round_up(per * (size_t)n, 1024) +
+           round_up(partials, 1024);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
+
+}  // namespace
+
+// Split-K: when a problem has too few output tiles to occupy the GPU (at most
+// 37 tiles of 128 x BN) and a long K (>= 1024), each tile's K range is cut
+// into S slices so that about 148 work units run at once (S <= K/256, so a
+// slice always holds several k-blocks, and S <= 16). Depends on the shape
+// only: workspace sizes do not depend on the device.
+int gb::split_k_factor(int mode, int64_t m, int64_t n, int64_t k) {
+    const int64_t bn = mode == 2 ? 128 : 256;
+    const int64_t tiles = ((m + 127) / 128) * ((n + bn - 1) / bn);
+    if (tiles < 1 || tiles * 4 > 148 || k < 1024) return 1;
+    int64_t s = 148 / tiles;
+    if (s > k / 256) s = k / 256;
+    if (s > 16) s = 16;
+    return s > 1 ? (int)s : 1;
+}
+
+namespace {
 
 // Bytes of one packed operand (mn rows of op(A), or mn columns of op(B)).
 size_t packed_bytes(int mode, int64_t mn, int64_t k) {
@@ -91,7 +114,7 @@ cudaError_t pack_operand(int mode, bool a_side, bool trans, int64_t mn, int64_t 
 
 int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, float alpha,
                    const void *Ap, const void *Bp, float beta, float *C, int64_t ldc,
-                   cudaStream_t s) {
+                   cudaStream_t s, float *part = nullptr, int splits = 1) {
     const int64_t kpad = split_kpad(mode, k);
     TcArgs t{};
     t.mode = mode;
@@ -100,6 +123,8 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     t.Ap = Ap; t.Bp = Bp;
     t.a_part_stride = m * kpad; t.b_part_stride = n * kpad;
     t.C = C; t.ldc = ldc;
+    t.part = part;
+    t.splits = part ? splits : 1;
     t.dstate = h->dstate;
     t.wait_limit = h->wait_limit;
     t.sm_count = h->sm_count;
@@ -129,10 +154,13 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
     char *Ap = static_cast<char *>(ws);
     char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
+    char *Pp = Bp + round_up(packed_bytes(mode, n, k), 1024);
+    const int splits = split_k_factor(mode, m, n, k);
     cudaError_t e = pack_operand(mode, true, is_trans(ta), m, k, A, lda, Ap, s);
     if (e == cudaSuccess) e = pack_operand(mode, false, is_trans(tb), n, k, B, ldb, Bp, s);
     if (e != cudaSuccess) return GB_ERR_CUDA;
-    return compute_packed(h, mode, m, n, k, alpha, Ap, Bp, beta, C, ldc, s);
+    return compute_packed(h, mode, m, n, k, alpha, Ap, Bp, beta, C, ldc, s,
+                          splits > 1 ? reinterpret_cast<float *>(Pp) : nullptr, splits);
 }
 
 // Backward products (see gb_sgemm_backward in the header for the formulas).

@@ -80,11 +80,16 @@ struct TcArgs {
     const void *Bp;             // [parts][n][kpad]
     int64_t a_part_stride, b_part_stride;   // elements between parts
     float *C; int64_t ldc;
+    float *part;                // split-K partial sums (splits x m x n floats) or null
+    int splits;                 // K slices per output tile (1 = no split)
     DeviceState *dstate;
     int64_t wait_limit;
     int sm_count;
 };
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s);
+// Number of K slices gb_sgemm uses for a split-precision problem (depends on
+// the shape only, so workspace sizes do not depend on the device).
+int split_k_factor(int mode, int64_t m, int64_t n, int64_t k);
 // Workspace layout helpers shared by the API and the launcher.
 int64_t split_kpad(int mode, int64_t k);
 int split_parts(int mode);

@@ -270,7 +270,8 @@ template <int MODE, int RB>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
-                int64_t ldc, DeviceState *dstate, uint64_t limit_ns) {
+                int64_t ldc, float *__restrict__ part, int splits, DeviceState *dstate,
+                uint64_t limit_ns) {
     using CF = Cfg<MODE, RB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -318,6 +319,16 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int64_t tiles_n = (N + CF::BN - 1) / CF::BN;
     const int64_t num_tiles = tiles_m * tiles_n;
     const int nkb = (int)((K + CF::BK - 1) / CF::BK);
+    // Work unit u = (tile u / splits, K slice u % splits). Slice s covers
+    // k-blocks [s*nkb/splits, (s+1)*nkb/splits); with splits == 1 a unit is a
+    // whole tile. Split units write raw partial sums to `part` (slice s at
+    // part + s*M*N, column-major, ld = M); a separate pass reduces them.
+    const int64_t num_units = num_tiles * splits;
+    auto kb_range = [&](int64_t u, int &kb0, int &kb1) {
+        const int64_t sl = u % splits;
+        kb0 = (int)(sl * nkb / splits);
+        kb1 = (int)((sl + 1) * nkb / splits);
+    };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -326,11 +337,13 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             uint32_t phase = 0;
             uint32_t issued_mask = 0, last_parity = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+            for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 int64_t tm, tn;
-                tile_coords(tile, tiles_m, tiles_n, tm, tn);
+                tile_coords(u / splits, tiles_m, tiles_n, tm, tn);
                 const int y_a = (int)(tm * BM), y_b = (int)(tn * CF::BN);
-                for (int kb = 0; kb < nkb; ++kb) {
+                int kb0, kb1;
+                kb_range(u, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!wait_bounded(w, empty_bar(stage), phase ^ 1u, kSiteProducerEmpty)) {
                         ok = false;
                         break;
@@ -367,12 +380,14 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+            for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
                 uint32_t accumulate = 0;
-                for (int kb = 0; kb < nkb; ++kb) {
+                int kb0, kb1;
+                kb_range(u, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) {
                         ok = false;
                         break;
@@ -412,11 +427,16 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int q = warp & 3;                       // TMEM lane quarter this warp may read
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        for (int64_t u = blockIdx.x; u < num_units; u += gridDim.x) {
             if (!wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull)) break;
             tc_fence_after();
             int64_t tm, tn;
-            tile_coords(tile, tiles_m, tiles_n, tm, tn);
+            tile_coords(u / splits, tiles_m, tiles_n, tm, tn);
+            float *dst = part ? part + (u % splits) * M * N : C;
+            const int64_t ldd = part ? M : ldc;
+            int kb0, kb1;
+            kb_range(u, kb0, kb1);
+            const float keep = kb0 < kb1 ? 1.f : 0.f;   // an empty K range contributes 0
             const int64_t row = tm * BM + q * 32 + lane;
             const int64_t col0 = tn * CF::BN;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
@@ -429,8 +449,10 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                     for (int j = 0; j < 16; ++j) {
                         const int64_t col = col0 + c + j;
                         if (col < N) {
-                            float *p = C + row + col * ldc;
-                            *p = beta != 0.f ? fmaf(alpha, v[j], beta * *p) : alpha * v[j];
+                            float *p = dst + row + col * ldd;
+                            const float x = keep * v[j];
+                            if (part) *p = x;
+                            else *p = beta != 0.f ? fmaf(alpha, x, beta * *p) : alpha * x;
                         }
                     }
                 }
@@ -446,6 +468,31 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem_base, CF::TMEM_COLS);
+}
+
+// C = alpha * (sum over slices s = 0..S-1, in that order, of part_s) + beta*C
+// (C not read when beta == 0). part_s is column-major M x N with ld = M.
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const float *__restrict__ part,
+                                     float alpha, float beta, float *__restrict__ C, int64_t ldc) {
+    const int64_t total = M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float acc = part[e];
+        for (int s = 1; s < S; ++s) acc += part[(int64_t)s * total + e];
+        const int64_t i = e % M, j = e / M;
+        float *p = C + i + j * ldc;
+        *p = beta != 0.f ? fmaf(alpha, acc, beta * *p) : alpha * acc;
+    }
+}
+
+cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part, float alpha,
+                                 float beta, float *C, int64_t ldc, cudaStream_t s) {
+    const int64_t total = m * n;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, n, S, part, alpha, beta, C, ldc);
+    return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------- host --
@@ -503,13 +550,17 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK, RB) ||
         !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK, RB))
         return cudaErrorInvalidValue;
-    const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN);
+    const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
+    const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
     int grid = a.sm_count > 0 ? a.sm_count : 1;
-    if (tiles < grid) grid = (int)tiles;
+    if (units < grid) grid = (int)units;
     const uint64_t limit_ns = (uint64_t)a.wait_limit * 1000ull;
     tc_sgemm_kernel<MODE, RB><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
-        ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, a.dstate, limit_ns);
-    return cudaGetLastError();
+        ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, splits > 1 ? a.part : nullptr, splits,
+        a.dstate, limit_ns);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
 }
 
 }  // namespace

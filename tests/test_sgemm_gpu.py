@@ -207,3 +207,53 @@ def test_long_k_integer_bit_exact(algo):
     p = wl.make_problem("T", "N", 140, 260, 4100, 1.0, 0.5, seed=27, dist="int", ld_pad=1)
     rc, got = run(p, algo)
     assert_bit_exact(p, got)
+
+
+# ------------------------------------------------------------- split-K ----
+
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+def test_split_k_small_full_check(algo):
+    """Few output tiles and a long K: the K range is cut into slices whose
+    partial sums are reduced in a fixed order (beta != 0 goes through the reduce)."""
+    p = wl.make_problem("N", "T", 200, 300, 3000, 0.5, 0.5, seed=28, ld_pad=2)
+    rc, got = run(p, algo)
+    assert_within_bound(p, got, algo=algo)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+def test_split_k_integer_bit_exact(algo):
+    p = wl.make_problem("T", "T", 100, 100, 5000, 1.0, 0.5, seed=29, dist="int", ld_pad=1)
+    rc, got = run(p, algo)
+    assert_bit_exact(p, got)
+
+
+def test_split_k_factor_is_used_in_workspace():
+    import paper_1912_04379_gb300 as gb
+    base = 2 * 2 * 8192 * (64 + 8192)             # packed A + B, BF16 x 2 terms, K = 8192
+    ws = gb.workspace_size("bf16x3", "N", "N", 64, 8192, 8192)
+    assert ws == base + 4 * 64 * 8192 * 4         # 4 slices of FP32 partials
+    assert gb.workspace_size("bf16x3", "N", "N", 8192, 8192, 8192) == 2 * 2 * 8192 * 16384
+
+
+# ----------------------------------------- full-size split shapes (sampled) --
+
+_SPLIT_CACHE = {}
+
+
+def _split_problem(shape):
+    if shape not in _SPLIT_CACHE:
+        _SPLIT_CACHE.clear()
+        _SPLIT_CACHE[shape] = wl.split_case(*shape)
+    return _SPLIT_CACHE[shape]
+
+
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("shape", wl.SPLIT_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_split_shapes_full_size_sampled(shape, algo):
+    p = _split_problem(shape)
+    rc, got = run(p, algo)
+    assert rc == 0
+    n = p.n
+    cols = np.unique(np.r_[0, n - 1, np.random.default_rng(n + p.k).integers(0, n, 6)])
+    assert_within_bound(p, got, cols=cols, algo=algo)
