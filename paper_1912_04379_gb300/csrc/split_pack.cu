@@ -25,8 +25,6 @@
 namespace gb {
 namespace {
 
-constexpr int TILE = 32;
-
 __device__ __forceinline__ float tf32_rne(float a) {
     // Round to 10 explicit mantissa bits, nearest-even, by integer arithmetic
     // on the encoding: add half an ulp of the target precision (minus one,
@@ -46,68 +44,133 @@ __device__ __forceinline__ __nv_bfloat16 bf16_rne(float a) {
     return h;
 }
 
+// Splits four consecutive k of one row and stores each term as one vector:
+// 4 TF32 words (16 bytes) or 4 BF16 values (8 bytes). idx is a multiple of 4
+// and rows start on 16-byte boundaries, so the stores are aligned.
 template <int MODE>
-__device__ __forceinline__ void split_store(float a, void *out, int64_t part_stride, int64_t idx) {
+__device__ __forceinline__ void split_store4(const float v[4], void *out, int64_t ps, int64_t idx) {
     if (MODE == 0) {
-        float *o = static_cast<float *>(out);
-        float h = tf32_rne(a);
-        float l = isfinite(a) ? tf32_rne(a - h) : 0.f;
-        o[idx] = h;
-        o[idx + part_stride] = l;
-    } else {
-        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out);
-        const __nv_bfloat16 h = bf16_rne(a);
-        const float hf = __bfloat162float(h);
-        const bool fin = isfinite(a);
-        const float r1 = fin ? a - hf : 0.f;
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        o[idx] = h;
-        o[idx + part_stride] = m;
-        if (MODE == 2) {
-            const float r2 = fin ? r1 - __bfloat162float(m) : 0.f;
-            o[idx + 2 * part_stride] = __float2bfloat16_rn(r2);
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            h[i] = tf32_rne(v[i]);
+            l[i] = isfinite(v[i]) ? tf32_rne(v[i] - h[i]) : 0.f;
         }
+        float *o = static_cast<float *>(out) + idx;
+        *reinterpret_cast<float4 *>(o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(o + ps) = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+        __nv_bfloat16 t0[4], t1[4], t2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float a = v[i];
+            const bool fin = isfinite(a);
+            t0[i] = bf16_rne(a);
+            const float r1 = fin ? a - __bfloat162float(t0[i]) : 0.f;
+            t1[i] = __float2bfloat16_rn(r1);
+            const float r2 = fin ? r1 - __bfloat162float(t1[i]) : 0.f;
+            t2[i] = __float2bfloat16_rn(r2);
+        }
+        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + idx;
+        auto pack = [](const __nv_bfloat16 t[4]) {
+            uint2 u;
+            u.x = (uint32_t)__bfloat16_as_ushort(t[0]) | ((uint32_t)__bfloat16_as_ushort(t[1]) << 16);
+            u.y = (uint32_t)__bfloat16_as_ushort(t[2]) | ((uint32_t)__bfloat16_as_ushort(t[3]) << 16);
+            return u;
+        };
+        *reinterpret_cast<uint2 *>(o) = pack(t0);
+        *reinterpret_cast<uint2 *>(o + ps) = pack(t1);
+        if (MODE == 2) *reinterpret_cast<uint2 *>(o + 2 * ps) = pack(t2);
     }
 }
 
-// One 32 x 32 (rows x k) tile per CTA of 256 threads. Reads are coalesced
-// along whichever dimension is contiguous in the source; writes are
-// coalesced along k.
-template <int MODE, bool KC>
+// Source contiguous along K (element (r,p) at X[p + r*ld]): no transpose.
+// Each thread splits 4 consecutive k of one row: 16-byte loads when the
+// source is 16-byte aligned, vector stores of every term. blockIdx.y walks
+// rows, blockIdx.x the k-quads of a row.
+template <int MODE, bool VEC>
 __global__ void __launch_bounds__(256)
-split_pack_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                  void *__restrict__ out, int64_t kpad, int64_t part_stride) {
-    __shared__ float T[TILE][TILE + 1];
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    const int64_t p0 = (int64_t)blockIdx.x * TILE;
-    const int64_t r0 = (int64_t)blockIdx.y * TILE;
+split_pack_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
+                     void *__restrict__ out, int64_t kpad, int64_t ps) {
+    const int64_t p = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
+    if (p >= kpad) return;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const float *src = X + r * ld + p;
+        float v[4];
+        if (VEC && p + 3 < K) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(src));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        int r, p;
-        if (KC) { p = lx; r = ly + 8 * e; }
-        else    { r = lx; p = ly + 8 * e; }
-        const int64_t rr = r0 + r, pp = p0 + p;
-        float v = 0.f;
-        if (rr < rows && pp < K) v = KC ? __ldg(X + pp + rr * ld) : __ldg(X + rr + pp * ld);
-        T[r][p] = v;
+            for (int i = 0; i < 4; ++i) v[i] = p + i < K ? __ldg(src + i) : 0.f;
+        }
+        split_store4<MODE>(v, out, ps, r * kpad + p);
+    }
+}
+
+// Source contiguous along the rows (element (r,p) at X[r + p*ld]): 64 x 64
+// tiles transposed through shared memory. Loads: 16 threads cover 64 rows
+// of one k column (16-byte loads when aligned). Stores: 16 threads cover 64
+// consecutive k of one row, 4 per thread.
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(256)
+split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
+                     void *__restrict__ out, int64_t kpad, int64_t ps) {
+    __shared__ float T[64][65];                       // [k][row]
+    const int t = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * 64, p0 = (int64_t)blockIdx.x * 64;
+    {
+        const int lr = (t & 15) * 4, lp = t >> 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int pl = lp + 16 * e;
+            const int64_t pp = p0 + pl, rr = r0 + lr;
+            float v[4];
+            if (VEC && pp < K && rr + 3 < rows) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(X + rr + pp * ld));
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v[i] = (pp < K && rr + i < rows) ? __ldg(X + rr + i + pp * ld) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) T[pl][lr + i] = v[i];
+        }
     }
     __syncthreads();
+    const int pq = (t & 15) * 4;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int r = ly + 8 * e, p = lx;
-        const int64_t rr = r0 + r, pp = p0 + p;
-        if (rr < rows && pp < kpad) split_store<MODE>(T[r][p], out, part_stride, rr * kpad + pp);
+        const int rl = (t >> 4) + 16 * e;
+        const int64_t rr = r0 + rl, pp = p0 + pq;
+        if (rr < rows && pp < kpad) {
+            float v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = T[pq + i][rl];
+            split_store4<MODE>(v, out, ps, rr * kpad + pp);
+        }
     }
 }
 
 template <int MODE>
 cudaError_t launch_mode(bool kc, int64_t rows, int64_t k, const float *X, int64_t ld, void *out,
                         int64_t kpad, int64_t ps, cudaStream_t s) {
-    const int64_t gx = (kpad + TILE - 1) / TILE, gy = (rows + TILE - 1) / TILE;
-    if (gx > 2147483647LL || gy > 65535LL) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    if (kc) split_pack_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
-    else    split_pack_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+    const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && ld % 4 == 0;
+    if (kc) {
+        const int64_t gx = (kpad / 4 + 255) / 256;
+        const int64_t gy = rows < 65535 ? rows : 65535;
+        if (gx > 2147483647LL) return cudaErrorInvalidConfiguration;
+        dim3 grid((unsigned)gx, (unsigned)gy);
+        if (vec) split_pack_kc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+        else     split_pack_kc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+    } else {
+        const int64_t gx = (kpad + 63) / 64, gy = (rows + 63) / 64;
+        if (gx > 2147483647LL || gy > 65535LL) return cudaErrorInvalidConfiguration;
+        dim3 grid((unsigned)gx, (unsigned)gy);
+        if (vec) split_pack_rc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+        else     split_pack_rc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+    }
     return cudaGetLastError();
 }
 

@@ -204,9 +204,9 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 
 // 32 lanes x 32 bits, 16 consecutive columns: thread t of the warp gets
-// row (lane base + t), columns col..col+15.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
+// row (lane base + t), columns col..col+15. The load is asynchronous: the
+// registers are valid only after tmem_wait().
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -214,10 +214,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// Waits for this thread's outstanding TMEM loads. The 16 registers of the
+// load are in/out operands, so the compiler cannot move any use of them
+// above the wait (the load writes them asynchronously).
+__device__ __forceinline__ void tmem_wait16(uint32_t r[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+
 
 // ----------------------------------------------------------- the kernel --
 template <int MODE, int RB>
@@ -441,19 +452,24 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             const int64_t col0 = tn * CF::BN;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
             const bool row_ok = row < M;
+            // Chunks of 16 columns: load from TMEM, wait, store; a warp writes
+            // 128 contiguous bytes of one column per store instruction. (Keeping
+            // more TMEM loads in flight, pipelining them against the stores, or
+            // staging whole 512-byte columns through shared memory all measured
+            // slower on the store-bound K = 64 shapes.)
             for (int c = 0; c < CF::BN; c += 16) {
-                float v[16];
-                tmem_ld16(taddr + (uint32_t)c, v);
-                if (row_ok) {
+                uint32_t r[16];
+                tmem_ld16(taddr + (uint32_t)c, r);
+                tmem_wait16(r);
+                if (!row_ok) continue;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = col0 + c + j;
-                        if (col < N) {
-                            float *p = dst + row + col * ldd;
-                            const float x = keep * v[j];
-                            if (part) *p = x;
-                            else *p = beta != 0.f ? fmaf(alpha, x, beta * *p) : alpha * x;
-                        }
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = col0 + c + j;
+                    if (col < N) {
+                        float *p = dst + row + col * ldd;
+                        const float x = keep * __uint_as_float(r[j]);
+                        if (part) *p = x;
+                        else *p = beta != 0.f ? fmaf(alpha, x, beta * *p) : alpha * x;
                     }
                 }
             }
