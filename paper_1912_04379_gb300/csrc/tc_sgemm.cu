@@ -456,11 +456,34 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             // 128 contiguous bytes of one column per store instruction. (Keeping
             // more TMEM loads in flight, pipelining them against the stores, or
             // staging whole 512-byte columns through shared memory all measured
-            // slower on the store-bound K = 64 shapes.)
+            // slower on the store-bound K = 64 shapes.) Interior tiles take a
+            // path with no per-element checks and a pointer bump per column:
+            // on store-bound shapes the epilogue's instruction count is the limit.
+            const bool interior = (tm * BM + BM <= M) && (col0 + CF::BN <= N);
+            float *colp = dst + row + col0 * ldd;
             for (int c = 0; c < CF::BN; c += 16) {
                 uint32_t r[16];
                 tmem_ld16(taddr + (uint32_t)c, r);
                 tmem_wait16(r);
+                if (interior) {
+                    float *p = colp + c * ldd;
+                    if (part) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { *p = keep * __uint_as_float(r[j]); p += ldd; }
+                    } else if (beta == 0.f) {
+                        const float a = keep * alpha;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { *p = a * __uint_as_float(r[j]); p += ldd; }
+                    } else {
+                        const float a = keep * alpha;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            *p = fmaf(a, __uint_as_float(r[j]), beta * *p);
+                            p += ldd;
+                        }
+                    }
+                    continue;
+                }
                 if (!row_ok) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
