@@ -56,9 +56,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grouped", action="store_true",
                     help="skip the grouped 2000-problem comparison")
+    ap.add_argument("--no-shapes", action="store_true",
+                    help="skip the per-shape table (K = 1024, 16384 and the skinny shapes)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--clocks-log", default=None)
+    ap.add_argument("--profile-grouped", default=None, metavar="ALGO",
+                    help="run the 2000-problem grouped workload twice with ALGO and exit")
     ap.add_argument("--profile", default=None, metavar="M,N,K[,ALGO]",
                     help="run one warm-up and one measured SGEMM of this shape (pack A, pack B, "
                          "compute) and exit; a small case for ncu captures")
@@ -89,6 +93,22 @@ def run_profile_case(spec):
             gb.compute_raw(algo, m, n, k, 1.0, Ap, Bp, 0.0, C.data_ptr(), m)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": [m, n, k, algo], "ok": True}), flush=True)
+    return 0
+
+
+def run_profile_grouped(algo):
+    """Two runs of the 2000-problem grouped workload with one algorithm (ncu target)."""
+    import torch
+    import workloads as wl
+    import paper_1912_04379_gb300 as gb
+    torch.cuda.set_device(0)
+    probs = wl.grouped_problems(2000, seed=4)
+    buf, tuples, views = gb.upload_problems(probs)
+    plan = gb.GroupedPlan(tuples, algo=algo)
+    for _ in range(2):
+        plan.run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_grouped": algo, "ok": True}), flush=True)
     return 0
 
 
@@ -270,7 +290,7 @@ def bench_grouped(gb, h, dev, stream, reps=10):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
-    for algo in ("simt", "auto"):
+    for algo in ("simt", "bf16x6", "auto"):
         plan = gb.GroupedPlan(tuples, algo=algo, handle=h)
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream(device=dev)
@@ -307,6 +327,46 @@ def bench_grouped(gb, h, dev, stream, reps=10):
     out["sequential_simt_graph"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
                                     "launches": len(tuples)}
     del buf
+    return out
+
+
+def bench_shapes(gb, h, dev, stream, reps=10):
+    """gb_sgemm on the split-precision shapes (M=N=8192 with K = 1024, 16384;
+    skinny 8192x8192x64 and 64x8192x8192) per algorithm: TFLOP/s and, for the
+    memory-bound skinny shapes, HBM GB/s of the minimum traffic
+    4(MK + KN + MN) bytes against the measured HBM peak."""
+    import torch
+    peaks, _ = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    for (m, n, k) in ((8192, 8192, 1024), (8192, 8192, 16384), (8192, 8192, 64), (64, 8192, 8192)):
+        g = torch.Generator(device=dev).manual_seed(SEED)
+        A = (torch.rand((k, m), device=dev, generator=g) * 2 - 1).t()
+        B = (torch.rand((n, k), device=dev, generator=g) * 2 - 1).t()
+        C = gb.colmajor(m, n, device=dev)
+        rows = {}
+        for algo in ("bf16x3", "tf32x3", "bf16x6", "simt"):
+            ws_n = gb.workspace_size(algo, "N", "N", m, n, k)
+            ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+
+            def f():
+                gb.sgemm_raw("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0,
+                             C.data_ptr(), m, algo=algo, handle=h, workspace=ws)
+            f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 4.0 * (m * k + k * n + m * n) / (ms * 1e-3) / 1e9
+            rows[algo] = {"ms": ms, "tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12,
+                          "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+            del ws
+        out[f"{m}x{n}x{k}"] = rows
+        del A, B, C
     return out
 
 
@@ -448,6 +508,7 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": C_h.numel() * 4}
 
     grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
+    shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
 
     peaks, peak_kind = load_peaks()
     tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
@@ -467,7 +528,8 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
-            "arms": arms, "grouped": grouped, "clocks": clocks, "source_sha": sha}
+            "arms": arms, "grouped": grouped, "shapes": shapes, "clocks": clocks,
+            "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cols, C64, D, dt, threads = cpu_oracle_sample(p, args.cpu_seconds)
@@ -506,6 +568,8 @@ def main():
         return 2
     if args.profile:
         return run_profile_case(args.profile)
+    if args.profile_grouped:
+        return run_profile_grouped(args.profile_grouped)
     if args.impl == "reference":
         return run_reference(args, rank)
     return run_ours(args, rank, world, local_rank)

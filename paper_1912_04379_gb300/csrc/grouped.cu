@@ -16,6 +16,7 @@
 // computes it with the shared-memory staged FMA scheme of the plain SIMT
 // kernel, transposes and leading dimensions read from the problem's
 // descriptor.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -149,6 +150,27 @@ __device__ __forceinline__ void simt_tile(const GProblem &P, int tm, int tn, flo
         __syncthreads();
         cur ^= 1;
     }
+    // beta != 0: read every C value of this thread before the first store (a
+    // store may alias a later load, so interleaving them would serialise the
+    // loads' latencies), folding beta*C into the accumulators.
+    if (P.beta != 0.f) {
+#pragma unroll
+        for (int j = 0; j < T::TN; ++j) {
+            const int col = n0 + (j / 4) * (BN / T::RN) + ty * 4 + (j % 4);
+            const float *cc = P.C + (int64_t)col * P.ldc;
+#pragma unroll
+            for (int i = 0; i < T::TM; ++i) {
+                const int row = m0 + (i / 4) * (BM / RM) + tx * 4 + (i % 4);
+                const float c = (row < P.m && col < P.n) ? cc[row] : 0.f;
+                acc[i][j] = fmaf(P.alpha, acc[i][j], P.beta * c);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < T::TM; ++i)
+#pragma unroll
+            for (int j = 0; j < T::TN; ++j) acc[i][j] *= P.alpha;
+    }
 #pragma unroll
     for (int j = 0; j < T::TN; ++j) {
         const int col = n0 + (j / 4) * (BN / T::RN) + ty * 4 + (j % 4);
@@ -157,9 +179,7 @@ __device__ __forceinline__ void simt_tile(const GProblem &P, int tm, int tn, flo
 #pragma unroll
         for (int i = 0; i < T::TM; ++i) {
             const int row = m0 + (i / 4) * (BM / RM) + tx * 4 + (i % 4);
-            if (row < P.m)
-                cc[row] = P.beta != 0.f ? fmaf(P.alpha, acc[i][j], P.beta * cc[row])
-                                        : P.alpha * acc[i][j];
+            if (row < P.m) cc[row] = acc[i][j];
         }
     }
     __syncthreads();    // shared memory is reused by the next tile
@@ -217,48 +237,82 @@ struct gb_grouped_plan_s {
     gb_handle_t h;
     int device;
     int64_t count;
-    int nitems;
     int grid;
+    // SIMT part
+    int nitems;
     gb::GProblem *d_probs;
     gb::GItem *d_items;
+    // tensor-core part (BF16 x 3 split): packed operands, tensor maps,
+    // problems, tiles and pack tiles, all in device memory owned by the plan
+    int64_t tc_nitems, tc_npack;
+    void *tc_packed;
+    CUtensorMap *tc_maps;
+    gb::TcProblem *tc_probs;
+    gb::TcItem *tc_items;
+    gb::PackItem *tc_pack;
 };
 
 namespace {
+
 constexpr int kPlanMagic = 0x47525031;
+constexpr int kTcMode = 2;          // BF16 x 3 terms: FP32 bound for every K >= 4
+constexpr bool kTcRb128 = true;     // short K loops (K <= 1024 in typical groups)
+constexpr int kClasses = 8;
+
+// Size class of a problem: floor(log2 of the geometric mean of M, N, K),
+// clamped to [3, 10] and shifted to 0..7.
+int size_class(int64_t m, int64_t n, int64_t k) {
+    const double g = cbrt((double)m * (double)n * (double)(k > 0 ? k : 1));
+    int c = (int)floor(log2(g > 1.0 ? g : 1.0)) - 3;
+    return c < 0 ? 0 : (c >= kClasses ? kClasses - 1 : c);
 }
 
-extern "C" {
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
-                                 const gb_gemm_problem_t *hp, gb_grouped_plan_t *plan,
-                                 size_t *ws_bytes, int64_t *bad_index) {
+void free_plan_memory(gb_grouped_plan_s *pl) {
+    cudaFree(pl->d_probs);
+    cudaFree(pl->d_items);
+    cudaFree(pl->tc_packed);
+    cudaFree(pl->tc_maps);
+    cudaFree(pl->tc_probs);
+    cudaFree(pl->tc_items);
+    cudaFree(pl->tc_pack);
+}
+
+template <class T>
+bool upload(T **dptr, const std::vector<T> &v) {
+    *dptr = nullptr;
+    if (v.empty()) return true;
+    return cudaMalloc(dptr, v.size() * sizeof(T)) == cudaSuccess &&
+           cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Builds a plan for validated problems; choice[c] routes size class c.
+// Returns a GB status; on error frees everything it allocated.
+int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
+               const int choice[kClasses], gb_grouped_plan_s **out) {
     using namespace gb;
-    if (plan) *plan = nullptr;
-    if (bad_index) *bad_index = -1;
-    if (!plan || !ws_bytes || count < 0 || (count > 0 && !hp)) return GB_ERR_ARG;
-    if (algo != GB_ALGO_AUTO && algo != GB_ALGO_SIMT) return GB_ERR_UNSUPPORTED;
-    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
-    if (dev != h->device) return GB_ERR_HANDLE;
-    if (count > (int64_t)1 << 30) return GB_ERR_UNSUPPORTED;
-
     std::vector<GProblem> probs;
     std::vector<GItem> items;
     std::vector<double> work;
-    probs.reserve((size_t)count);
-    for (int64_t i = 0; i < count; ++i) {
-        const gb_gemm_problem_t &p = hp[i];
-        int rc = check_problem(p);
-        if (rc) {
-            if (bad_index) *bad_index = i;
-            return rc;
-        }
+    struct TcPending { size_t prob; size_t off_a, off_b; };
+    std::vector<TcPending> tcs;
+    size_t packed_bytes = 0;
+    for (size_t i = 0; i < ps.size(); ++i) {
+        const gb_gemm_problem_t &p = ps[i];
         const bool scale_only = p.alpha == 0.f || p.k == 0;
         if (p.m == 0 || p.n == 0 || (scale_only && p.beta == 1.f)) continue;
-        if (!p.C || (!scale_only && (!p.A || !p.B))) {
-            if (bad_index) *bad_index = i;
-            return GB_ERR_ARG;
+        const int ch = (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
+                                               : choice[size_class(p.m, p.n, p.k)];
+        if (ch == 2) {
+            const size_t kpad = (size_t)split_kpad(kTcMode, p.k);
+            const size_t per = (size_t)split_parts(kTcMode) * kpad * (size_t)split_elem_bytes(kTcMode);
+            TcPending t{i, packed_bytes, 0};
+            packed_bytes += round_up(per * (size_t)p.m, 1024);
+            t.off_b = packed_bytes;
+            packed_bytes += round_up(per * (size_t)p.n, 1024);
+            tcs.push_back(t);
+            continue;
         }
         GProblem g;
         g.A = p.A; g.B = p.B; g.C = p.C;
@@ -268,9 +322,7 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
         g.ta = is_trans(p.transa); g.tb = is_trans(p.transb);
         const int pi = (int)probs.size();
         probs.push_back(g);
-        // Tile class: 64 x 64 when either output side is below 96 (a 128-wide
-        // tile would be mostly empty), else 128 x 128.
-        const int cls = (p.m < 96 || p.n < 96) ? 1 : 0;
+        const int cls = ch == 1 ? 0 : 1;                 // GItem class 0: 128 x 128, 1: 64 x 64
         const int bm = cls ? 64 : 128, bn = cls ? 64 : 128;
         const int tiles_m = (int)((p.m + bm - 1) / bm), tiles_n = (int)((p.n + bn - 1) / bn);
         for (int tm = 0; tm < tiles_m; ++tm)
@@ -292,31 +344,232 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
     pl->magic = kPlanMagic;
     pl->h = h;
     pl->device = dev;
-    pl->count = count;
+    pl->count = (int64_t)ps.size();
     pl->nitems = (int)sorted.size();
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_simt_kernel, NT, 0) !=
             cudaSuccess || per_sm < 1)
         per_sm = 1;
-    pl->grid = std::max(1, std::min(h->sm_count * per_sm, pl->nitems));
-    pl->d_probs = nullptr;
-    pl->d_items = nullptr;
-    bool ok = true;
-    if (!probs.empty())
-        ok = cudaMalloc(&pl->d_probs, probs.size() * sizeof(GProblem)) == cudaSuccess &&
-             cudaMemcpy(pl->d_probs, probs.data(), probs.size() * sizeof(GProblem),
-                        cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok && !sorted.empty())
-        ok = cudaMalloc(&pl->d_items, sorted.size() * sizeof(GItem)) == cudaSuccess &&
-             cudaMemcpy(pl->d_items, sorted.data(), sorted.size() * sizeof(GItem),
-                        cudaMemcpyHostToDevice) == cudaSuccess;
+    pl->grid = std::max(1, std::min(h->sm_count * per_sm, std::max(pl->nitems, 1)));
+    bool ok = upload(&pl->d_probs, probs) && upload(&pl->d_items, sorted);
+
+    // ---- tensor-core problems: packed buffers, tensor maps, tiles, pack tiles
+    if (ok && !tcs.empty()) {
+        ok = cudaMalloc(&pl->tc_packed, packed_bytes) == cudaSuccess &&
+             cudaMalloc(&pl->tc_maps, 2 * tcs.size() * sizeof(CUtensorMap)) == cudaSuccess;
+        std::vector<CUtensorMap> maps(2 * tcs.size());
+        std::vector<TcProblem> tprobs(tcs.size());
+        std::vector<TcItem> titems;
+        std::vector<double> twork;
+        std::vector<PackItem> pack;
+        const int bn = tc_tile_n(kTcMode);
+        char *base = static_cast<char *>(pl->tc_packed);
+        for (size_t j = 0; ok && j < tcs.size(); ++j) {
+            const gb_gemm_problem_t &p = ps[tcs[j].prob];
+            const int64_t kpad = split_kpad(kTcMode, p.k);
+            char *pa = base + tcs[j].off_a, *pb = base + tcs[j].off_b;
+            ok = tc_make_operand_map(&maps[2 * j], kTcMode, kTcRb128, pa, p.k, p.m, true) &&
+                 tc_make_operand_map(&maps[2 * j + 1], kTcMode, kTcRb128, pb, p.k, p.n, false);
+            TcProblem &t = tprobs[j];
+            t.mapA = pl->tc_maps + 2 * j;
+            t.mapB = pl->tc_maps + 2 * j + 1;
+            t.C = p.C; t.ldc = p.ldc;
+            t.m = p.m; t.n = p.n; t.k = p.k;
+            t.alpha = p.alpha; t.beta = p.beta;
+            const int tiles_m = (int)((p.m + 127) / 128), tiles_n = (int)((p.n + bn - 1) / bn);
+            for (int tm = 0; tm < tiles_m; ++tm)
+                for (int tn = 0; tn < tiles_n; ++tn) {
+                    titems.push_back(TcItem{(int)j, tm, tn, 0});
+                    twork.push_back((double)p.k);
+                }
+            // pack tiles of op(A) (M x K, K-contiguous iff A is transposed) and
+            // op(B)^T (N x K, K-contiguous iff B is not transposed)
+            for (int side = 0; side < 2; ++side) {
+                PackItem it{};
+                it.X = side ? p.B : p.A;
+                it.ld = side ? p.ldb : p.lda;
+                it.out = side ? pb : pa;
+                it.kpad = kpad;
+                it.rows = side ? p.n : p.m;
+                it.ps = it.rows * kpad;
+                it.k = p.k;
+                it.kc = side ? !is_trans(p.transb) : is_trans(p.transa);
+                it.vec = ((reinterpret_cast<uintptr_t>(it.X) & 15) == 0) && (it.ld % 4 == 0);
+                for (int64_t r0 = 0; r0 < it.rows; r0 += 64)
+                    for (int64_t p0 = 0; p0 < kpad; p0 += 64) {
+                        it.r0 = r0;
+                        it.p0 = p0;
+                        pack.push_back(it);
+                    }
+            }
+        }
+        std::vector<int> tord(titems.size());
+        for (size_t i = 0; i < tord.size(); ++i) tord[i] = (int)i;
+        std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) { return twork[a] > twork[b]; });
+        std::vector<TcItem> tsorted(titems.size());
+        for (size_t i = 0; i < tord.size(); ++i) tsorted[i] = titems[tord[i]];
+        ok = ok &&
+             cudaMemcpy(pl->tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             upload(&pl->tc_probs, tprobs) && upload(&pl->tc_items, tsorted) &&
+             upload(&pl->tc_pack, pack);
+        pl->tc_nitems = (int64_t)tsorted.size();
+        pl->tc_npack = (int64_t)pack.size();
+    }
     if (!ok) {
-        cudaFree(pl->d_probs);
-        cudaFree(pl->d_items);
+        free_plan_memory(pl);
         delete pl;
         return GB_ERR_CUDA;
     }
-    *ws_bytes = 256;         // the work counter
+    *out = pl;
+    return GB_OK;
+}
+
+int run_plan(gb_grouped_plan_s *plan, void *workspace, cudaStream_t s) {
+    using namespace gb;
+    if (plan->tc_nitems > 0) {
+        if (launch_split_pack_grouped(kTcMode, plan->tc_pack, plan->tc_npack, s) != cudaSuccess)
+            return GB_ERR_CUDA;
+        if (launch_tc_grouped(kTcMode, kTcRb128, plan->tc_probs, plan->tc_items, plan->tc_nitems,
+                              plan->h->sm_count, plan->h->dstate, plan->h->wait_limit, s) !=
+            cudaSuccess)
+            return GB_ERR_CUDA;
+    }
+    if (plan->nitems > 0) {
+        int *counter = static_cast<int *>(workspace);
+        if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return GB_ERR_CUDA;
+        grouped_simt_kernel<<<plan->grid, NT, 0, s>>>(plan->d_probs, plan->d_items, plan->nitems,
+                                                      counter);
+        if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
+    }
+    return GB_OK;
+}
+
+void destroy_plan(gb_grouped_plan_s *plan) {
+    cudaDeviceSynchronize();
+    free_plan_memory(plan);
+    plan->magic = 0;
+    delete plan;
+}
+
+// Autotuner: for each size class, time a synthetic group of square problems
+// of the class's middle size (geometric mean 2^(c+3.5)) under each candidate
+// (SIMT 64x64 tiles, SIMT 128x128 tiles, tensor cores) and keep the fastest.
+// Runs once per handle, on a private stream, with scratch memory freed
+// afterwards; the result is stored in the handle.
+int autotune(gb_handle_t h, int dev) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GB_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = GB_OK;
+    void *ws = nullptr;
+    if (cudaMalloc(&ws, 256) != cudaSuccess) rc = GB_ERR_CUDA;
+    for (int c = 0; c < kClasses && rc == GB_OK; ++c) {
+        const int64_t d = (int64_t)llround(pow(2.0, c + 3.5));
+        // enough problems for about two waves of 128 x 128 tiles, bounded in memory
+        const int64_t tiles = ((d + 127) / 128) * ((d + 127) / 128);
+        int64_t g = std::max<int64_t>(16, (2 * (int64_t)h->sm_count + tiles - 1) / tiles);
+        g = std::min<int64_t>(g, std::max<int64_t>(4, (int64_t)(256ll << 20) / (12 * d * d)));
+        float *buf = nullptr;
+        const size_t per = (size_t)(3 * d * d);
+        if (cudaMalloc(&buf, per * g * sizeof(float)) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
+        cudaMemsetAsync(buf, 0x3e, per * g * sizeof(float), s);   // values near 0.19
+        std::vector<gb_gemm_problem_t> ps((size_t)g);
+        for (int64_t i = 0; i < g; ++i) {
+            gb_gemm_problem_t &p = ps[(size_t)i];
+            p.transa = (i & 1) ? 'T' : 'N';
+            p.transb = (i & 2) ? 'T' : 'N';
+            p.m = p.n = p.k = d;
+            p.alpha = 1.f; p.beta = 0.f;
+            p.A = buf + per * i; p.lda = d;
+            p.B = buf + per * i + d * d; p.ldb = d;
+            p.C = buf + per * i + 2 * d * d; p.ldc = d;
+        }
+        float best = 1e30f;
+        int best_ch = 1;
+        for (int ch = 0; ch < 3 && rc == GB_OK; ++ch) {
+            int choice[kClasses];
+            for (int q = 0; q < kClasses; ++q) choice[q] = ch;
+            gb_grouped_plan_s *pl = nullptr;
+            if (build_plan(h, dev, ps, choice, &pl) != GB_OK) { rc = GB_ERR_CUDA; break; }
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {          // the first run is a warm-up
+                cudaEventRecord(e0, s);
+                if (run_plan(pl, ws, s) != GB_OK) { rc = GB_ERR_CUDA; break; }
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);
+            }
+            destroy_plan(pl);
+            if (ms < best) { best = ms; best_ch = ch; }
+        }
+        cudaFree(buf);
+        h->grouped_choice[c] = best_ch;
+    }
+    cudaFree(ws);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (rc == GB_OK) h->grouped_tuned = true;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
+                                 const gb_gemm_problem_t *hp, gb_grouped_plan_t *plan,
+                                 size_t *ws_bytes, int64_t *bad_index) {
+    using namespace gb;
+    if (plan) *plan = nullptr;
+    if (bad_index) *bad_index = -1;
+    if (!plan || !ws_bytes || count < 0 || (count > 0 && !hp)) return GB_ERR_ARG;
+    if (algo != GB_ALGO_AUTO && algo != GB_ALGO_SIMT && algo != GB_ALGO_SPLIT_BF16X6)
+        return GB_ERR_UNSUPPORTED;
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    if (dev != h->device) return GB_ERR_HANDLE;
+    if (count > (int64_t)1 << 30) return GB_ERR_UNSUPPORTED;
+    std::vector<gb_gemm_problem_t> ps;
+    ps.reserve((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const gb_gemm_problem_t &p = hp[i];
+        int rc = check_problem(p);
+        if (rc) {
+            if (bad_index) *bad_index = i;
+            return rc;
+        }
+        const bool scale_only = p.alpha == 0.f || p.k == 0;
+        const bool quick = p.m == 0 || p.n == 0 || (scale_only && p.beta == 1.f);
+        if (!quick && (!p.C || (!scale_only && (!p.A || !p.B)))) {
+            if (bad_index) *bad_index = i;
+            return GB_ERR_ARG;
+        }
+        ps.push_back(p);
+    }
+    int choice[kClasses];
+    if (algo == GB_ALGO_AUTO) {
+        if (!h->grouped_tuned) {
+            int rc = autotune(h, dev);
+            if (rc) return rc;
+        }
+        for (int c = 0; c < kClasses; ++c) choice[c] = h->grouped_choice[c];
+    } else {
+        // SIMT: 64x64 tiles for the three smallest classes, else 128x128;
+        // SPLIT_BF16X6: every problem with K >= 4 on the tensor cores
+        for (int c = 0; c < kClasses; ++c)
+            choice[c] = algo == GB_ALGO_SIMT ? (c < 3 ? 0 : 1) : 2;
+    }
+    gb_grouped_plan_s *pl = nullptr;
+    int rc = build_plan(h, dev, ps, choice, &pl);
+    if (rc) return rc;
+    *ws_bytes = 256;         // the SIMT work counter
     *plan = pl;
     return GB_OK;
 }
@@ -328,25 +581,16 @@ GB_API int gb_sgemm_grouped_run(gb_grouped_plan_t plan, void *workspace, size_t 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
     if (dev != plan->device) return GB_ERR_HANDLE;
-    if (plan->nitems == 0) return GB_OK;
+    if (plan->nitems == 0 && plan->tc_nitems == 0) return GB_OK;
     if (!workspace || ws_bytes < 256 || (reinterpret_cast<uintptr_t>(workspace) & 255))
         return GB_ERR_WORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int *counter = static_cast<int *>(workspace);
-    if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return GB_ERR_CUDA;
-    grouped_simt_kernel<<<plan->grid, NT, 0, s>>>(plan->d_probs, plan->d_items, plan->nitems,
-                                                  counter);
-    return cudaGetLastError() == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+    return run_plan(plan, workspace, static_cast<cudaStream_t>(stream));
 }
 
 GB_API int gb_sgemm_grouped_destroy(gb_grouped_plan_t plan) {
     if (!plan) return GB_OK;
     if (plan->magic != kPlanMagic) return GB_ERR_PLAN;
-    cudaDeviceSynchronize();
-    cudaFree(plan->d_probs);
-    cudaFree(plan->d_items);
-    plan->magic = 0;
-    delete plan;
+    destroy_plan(plan);
     return GB_OK;
 }
 

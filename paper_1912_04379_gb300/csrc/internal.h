@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (see include/gbsgemm.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,6 +37,10 @@ struct gb_handle_s {
     size_t smem_optin;
     int64_t wait_limit;
     gb::DeviceState *dstate;   // device memory
+    // Grouped autotuner result, per size class of a problem (see grouped.cu):
+    // 0 = SIMT 64x64 tiles, 1 = SIMT 128x128 tiles, 2 = tensor cores (BF16 x 3).
+    bool grouped_tuned;
+    int grouped_choice[8];
 };
 
 namespace gb {
@@ -94,6 +99,46 @@ int split_k_factor(int mode, int64_t m, int64_t n, int64_t k);
 int64_t split_kpad(int mode, int64_t k);
 int split_parts(int mode);
 int split_elem_bytes(int mode);
+
+// ------------------------------------------------ grouped tensor-core path --
+// One problem of a grouped tensor-core launch (device memory). Its operands
+// were split and packed by launch_split_pack_grouped into buffers owned by
+// the plan; mapA / mapB are their tensor maps, also in device memory.
+struct TcProblem {
+    const CUtensorMap *mapA;
+    const CUtensorMap *mapB;
+    float *C;
+    int64_t ldc;
+    int64_t m, n, k;
+    float alpha, beta;
+};
+struct TcItem {
+    int prob;
+    int tm, tn;                 // output tile (128 x tile_n)
+    int pad;
+};
+int tc_tile_n(int mode);
+// Tensor map of one packed operand ([terms][rows][kpad], K innermost) for the
+// kernel variant (mode, 128-byte rows or not); a_side selects the box height.
+bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
+                         int64_t rows, bool a_side);
+cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, const TcItem *items,
+                              int64_t nitems, int sm_count, DeviceState *dstate,
+                              int64_t wait_limit, cudaStream_t s);
+
+// One 64 x 64 (rows x k) tile of the grouped split/pack pass.
+struct PackItem {
+    const float *X;
+    int64_t ld;
+    void *out;                  // terms at out + t*ps, row r at r*kpad
+    int64_t kpad, ps;
+    int64_t rows, k;
+    int64_t r0, p0;
+    int kc;                     // source contiguous along K
+    int vec;                    // 16-byte loads allowed
+};
+cudaError_t launch_split_pack_grouped(int mode, const PackItem *items, int64_t nitems,
+                                      cudaStream_t s);
 
 // --------------------------------------------------------- error report --
 size_t err_report_ws(int64_t m, int64_t n);

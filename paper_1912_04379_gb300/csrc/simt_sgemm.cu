@@ -176,7 +176,37 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
 
     // Epilogue: thread rows {tx*4 + 0..3, 64 + tx*4 + 0..3}, columns
     // {ty*4 + 0..3, 64 + ty*4 + 0..3}; a warp writes 64 consecutive floats of
-    // a column per store instruction.
+    // a column per store instruction. With beta != 0 every C value of the
+    // thread is read before the first store (a store may alias a later load,
+    // so interleaving them would serialise the loads' latencies).
+    if (beta != 0.f) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t col = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+            const float *cc = C + col * ldc;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = m0 + h * 64 + tx * 4;
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                if (col < N) {
+                    if (VC && row + 3 < M) {
+                        const float4 q = *reinterpret_cast<const float4 *>(cc + row);
+                        c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) c[e] = row + e < M ? cc[row + e] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[h * 4 + e][j] = fmaf(alpha, acc[h * 4 + e][j], beta * c[e]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] *= alpha;
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int64_t col = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
@@ -186,28 +216,12 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         for (int h = 0; h < 2; ++h) {
             const int64_t row = m0 + h * 64 + tx * 4;
             if (VC && row + 3 < M) {
-                float4 o;
-                if (beta != 0.f) {
-                    const float4 c = *reinterpret_cast<const float4 *>(cc + row);
-                    o.x = fmaf(alpha, acc[h * 4 + 0][j], beta * c.x);
-                    o.y = fmaf(alpha, acc[h * 4 + 1][j], beta * c.y);
-                    o.z = fmaf(alpha, acc[h * 4 + 2][j], beta * c.z);
-                    o.w = fmaf(alpha, acc[h * 4 + 3][j], beta * c.w);
-                } else {
-                    o.x = alpha * acc[h * 4 + 0][j];
-                    o.y = alpha * acc[h * 4 + 1][j];
-                    o.z = alpha * acc[h * 4 + 2][j];
-                    o.w = alpha * acc[h * 4 + 3][j];
-                }
-                *reinterpret_cast<float4 *>(cc + row) = o;
+                *reinterpret_cast<float4 *>(cc + row) =
+                    make_float4(acc[h * 4 + 0][j], acc[h * 4 + 1][j], acc[h * 4 + 2][j], acc[h * 4 + 3][j]);
             } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (row + e < M) {
-                        const float r = acc[h * 4 + e][j];
-                        cc[row + e] = beta != 0.f ? fmaf(alpha, r, beta * cc[row + e]) : alpha * r;
-                    }
-                }
+                for (int e = 0; e < 4; ++e)
+                    if (row + e < M) cc[row + e] = acc[h * 4 + e][j];
             }
         }
     }

@@ -108,25 +108,25 @@ split_pack_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
     }
 }
 
-// Source contiguous along the rows (element (r,p) at X[r + p*ld]): 64 x 64
-// tiles transposed through shared memory. Loads: 16 threads cover 64 rows
-// of one k column (16-byte loads when aligned). Stores: 16 threads cover 64
-// consecutive k of one row, 4 per thread.
-template <int MODE, bool VEC>
-__global__ void __launch_bounds__(256)
-split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                     void *__restrict__ out, int64_t kpad, int64_t ps) {
-    __shared__ float T[64][65];                       // [k][row]
+// One 64 x 64 (rows x k) tile through shared memory. Loads are coalesced
+// along whichever dimension the source is contiguous in (16 threads cover 64
+// consecutive floats, 16-byte loads when vec); stores are coalesced along k
+// (16 threads cover 64 consecutive k of one row, 4 per thread, one vector per
+// term). kc: element (r,p) at X[p + r*ld]; otherwise at X[r + p*ld].
+template <int MODE>
+__device__ __forceinline__ void pack_tile64(const float *__restrict__ X, int64_t ld, bool kc,
+                                            bool vec, int64_t rows, int64_t K,
+                                            void *__restrict__ out, int64_t kpad, int64_t ps,
+                                            int64_t r0, int64_t p0, float (*T)[65]) {
     const int t = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.y * 64, p0 = (int64_t)blockIdx.x * 64;
-    {
-        const int lr = (t & 15) * 4, lp = t >> 4;
+    const int l4 = (t & 15) * 4, l16 = t >> 4;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int pl = lp + 16 * e;
-            const int64_t pp = p0 + pl, rr = r0 + lr;
-            float v[4];
-            if (VEC && pp < K && rr + 3 < rows) {
+    for (int e = 0; e < 4; ++e) {
+        float v[4];
+        if (!kc) {
+            const int pl = l16 + 16 * e;                 // T[pl][l4 .. l4+3]
+            const int64_t pp = p0 + pl, rr = r0 + l4;
+            if (vec && pp < K && rr + 3 < rows) {
                 const float4 q = __ldg(reinterpret_cast<const float4 *>(X + rr + pp * ld));
                 v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
             } else {
@@ -135,21 +135,57 @@ split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
                     v[i] = (pp < K && rr + i < rows) ? __ldg(X + rr + i + pp * ld) : 0.f;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) T[pl][lr + i] = v[i];
+            for (int i = 0; i < 4; ++i) T[pl][l4 + i] = v[i];
+        } else {
+            const int rl = l16 + 16 * e;                 // T[l4 .. l4+3][rl]
+            const int64_t rr = r0 + rl, pp = p0 + l4;
+            if (vec && rr < rows && pp + 3 < K) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(X + pp + rr * ld));
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v[i] = (rr < rows && pp + i < K) ? __ldg(X + pp + i + rr * ld) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) T[l4 + i][rl] = v[i];
         }
     }
     __syncthreads();
-    const int pq = (t & 15) * 4;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int rl = (t >> 4) + 16 * e;
-        const int64_t rr = r0 + rl, pp = p0 + pq;
+        const int rl = l16 + 16 * e;
+        const int64_t rr = r0 + rl, pp = p0 + l4;
         if (rr < rows && pp < kpad) {
             float v[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = T[pq + i][rl];
+            for (int i = 0; i < 4; ++i) v[i] = T[l4 + i][rl];
             split_store4<MODE>(v, out, ps, rr * kpad + pp);
         }
+    }
+    __syncthreads();                                     // T is reused by the next tile
+}
+
+// Source contiguous along the rows (element (r,p) at X[r + p*ld]): one
+// 64 x 64 tile per CTA, transposed through shared memory.
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(256)
+split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
+                     void *__restrict__ out, int64_t kpad, int64_t ps) {
+    __shared__ float T[64][65];
+    pack_tile64<MODE>(X, ld, false, VEC, rows, K, out, kpad, ps, (int64_t)blockIdx.y * 64,
+                      (int64_t)blockIdx.x * 64, T);
+}
+
+// Grouped pass: each CTA walks a list of 64 x 64 tiles of many operands.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+split_pack_grouped_kernel(const PackItem *__restrict__ items, int64_t nitems) {
+    __shared__ float T[64][65];
+    for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const PackItem it = items[i];
+        pack_tile64<MODE>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
+                          it.ps, it.r0, it.p0, T);
     }
 }
 
@@ -175,6 +211,19 @@ cudaError_t launch_mode(bool kc, int64_t rows, int64_t k, const float *X, int64_
 }
 
 }  // namespace
+
+cudaError_t launch_split_pack_grouped(int mode, const PackItem *items, int64_t nitems,
+                                      cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = (int)(nitems < 65536 ? nitems : 65536);
+    switch (mode) {
+        case 0: split_pack_grouped_kernel<0><<<grid, 256, 0, s>>>(items, nitems); break;
+        case 1: split_pack_grouped_kernel<1><<<grid, 256, 0, s>>>(items, nitems); break;
+        case 2: split_pack_grouped_kernel<2><<<grid, 256, 0, s>>>(items, nitems); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 int split_parts(int mode) { return mode == 2 ? 3 : 2; }
 int split_elem_bytes(int mode) { return mode == 0 ? 4 : 2; }

@@ -36,7 +36,6 @@
 // roles leave their loops; the producer then waits (bounded) for its
 // in-flight copies, the MMA issuer for its in-flight MMAs, and TMEM is freed
 // before the CTA exits. No trap, no unbounded spin.
-#include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdlib.h>
 
@@ -266,23 +265,88 @@ __device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {
     }
 }
 
-__device__ __forceinline__ void tile_coords(int64_t tile, int64_t tiles_m, int64_t tiles_n,
-                                            int64_t &tm, int64_t &tn) {
-    const int64_t per_group = (int64_t)GROUP_M * tiles_n;
-    const int64_t g = tile / per_group;
-    const int64_t first_m = g * GROUP_M;
-    const int64_t gm = (tiles_m - first_m) < GROUP_M ? (tiles_m - first_m) : GROUP_M;
-    const int64_t r = tile - g * per_group;
+// Tile raster in groups of GROUP_M tile rows (32-bit: the host guarantees
+// that the number of work units fits in an int).
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int64_t &tm,
+                                            int64_t &tn) {
+    const int per_group = GROUP_M * tiles_n;
+    const int g = tile / per_group;
+    const int first_m = g * GROUP_M;
+    const int gm = (tiles_m - first_m) < GROUP_M ? (tiles_m - first_m) : GROUP_M;
+    const int r = tile - g * per_group;
     tm = first_m + r % gm;
     tn = r / gm;
 }
 
-template <int MODE, int RB>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
-                int64_t ldc, float *__restrict__ part, int splits, DeviceState *dstate,
-                uint64_t limit_ns) {
+// What one work unit is: the operands' tensor maps, the output tile, the
+// range of k-blocks, and where and how the result is written.
+struct UnitInfo {
+    const CUtensorMap *ma, *mb;
+    int64_t M, N;                 // the problem's output size
+    int64_t tm, tn;               // tile coordinates
+    int kb0, kb1;                 // k-blocks [kb0, kb1)
+    float alpha, beta;
+    float *dst;                   // C, or this slice's partial-sum buffer
+    int64_t ldd;
+    bool raw;                     // write raw sums (split-K partial), no alpha/beta
+};
+
+// One GEMM: units are (tile, K slice) pairs in the grouped raster order.
+// Split units write raw partial sums to `part` (slice s at part + s*M*N,
+// column-major, ld = M); a separate pass reduces them.
+template <int BN, int BK>
+struct SingleSource {
+    const CUtensorMap *ma, *mb;
+    int64_t M, N, K;
+    float alpha, beta;
+    float *C;
+    int64_t ldc;
+    float *part;
+    int splits;
+    int tiles_m, tiles_n;
+    int nkb;
+    __device__ __forceinline__ int64_t num_units() const {
+        return (int64_t)tiles_m * tiles_n * splits;
+    }
+    __device__ __forceinline__ void unit(int64_t u64, UnitInfo &ui) const {
+        const int u = (int)u64;
+        tile_coords(u / splits, tiles_m, tiles_n, ui.tm, ui.tn);
+        const int sl = u % splits;
+        ui.kb0 = (int)((int64_t)sl * nkb / splits);
+        ui.kb1 = (int)((int64_t)(sl + 1) * nkb / splits);
+        ui.ma = ma; ui.mb = mb;
+        ui.M = M; ui.N = N;
+        ui.alpha = alpha; ui.beta = beta;
+        ui.raw = part != nullptr;
+        ui.dst = part ? part + sl * M * N : C;
+        ui.ldd = part ? M : ldc;
+    }
+};
+
+// Many GEMMs: units are the planned (problem, tile) items; each problem has
+// its own tensor maps (in device global memory) and output.
+template <int BN, int BK>
+struct GroupSource {
+    const TcProblem *probs;
+    const TcItem *items;
+    int64_t nitems;
+    __device__ __forceinline__ int64_t num_units() const { return nitems; }
+    __device__ __forceinline__ void unit(int64_t u, UnitInfo &ui) const {
+        const TcItem it = items[u];
+        const TcProblem &P = probs[it.prob];
+        ui.ma = P.mapA; ui.mb = P.mapB;
+        ui.M = P.m; ui.N = P.n;
+        ui.tm = it.tm; ui.tn = it.tn;
+        ui.kb0 = 0;
+        ui.kb1 = (int)((P.k + BK - 1) / BK);
+        ui.alpha = P.alpha; ui.beta = P.beta;
+        ui.dst = P.C; ui.ldd = P.ldc;
+        ui.raw = false;
+    }
+};
+
+template <int MODE, int RB, class Src>
+__device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uint64_t limit_ns) {
     using CF = Cfg<MODE, RB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -317,29 +381,13 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        prefetch_tmap(&mapA);
-        prefetch_tmap(&mapB);
     }
     if (warp == 1) tmem_alloc(smem_u32(tmem_holder), CF::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
-
-    const int64_t tiles_m = (M + BM - 1) / BM;
-    const int64_t tiles_n = (N + CF::BN - 1) / CF::BN;
-    const int64_t num_tiles = tiles_m * tiles_n;
-    const int nkb = (int)((K + CF::BK - 1) / CF::BK);
-    // Work unit u = (tile u / splits, K slice u % splits). Slice s covers
-    // k-blocks [s*nkb/splits, (s+1)*nkb/splits); with splits == 1 a unit is a
-    // whole tile. Split units write raw partial sums to `part` (slice s at
-    // part + s*M*N, column-major, ld = M); a separate pass reduces them.
-    const int64_t num_units = num_tiles * splits;
-    auto kb_range = [&](int64_t u, int &kb0, int &kb1) {
-        const int64_t sl = u % splits;
-        kb0 = (int)(sl * nkb / splits);
-        kb1 = (int)((sl + 1) * nkb / splits);
-    };
+    const int64_t num_units = src.num_units();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -349,21 +397,19 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             uint32_t issued_mask = 0, last_parity = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-                int64_t tm, tn;
-                tile_coords(u / splits, tiles_m, tiles_n, tm, tn);
-                const int y_a = (int)(tm * BM), y_b = (int)(tn * CF::BN);
-                int kb0, kb1;
-                kb_range(u, kb0, kb1);
-                for (int kb = kb0; kb < kb1; ++kb) {
+                UnitInfo ui;
+                src.unit(u, ui);
+                const int y_a = (int)(ui.tm * BM), y_b = (int)(ui.tn * CF::BN);
+                for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
                     if (!wait_bounded(w, empty_bar(stage), phase ^ 1u, kSiteProducerEmpty)) {
                         ok = false;
                         break;
                     }
                     mbar_arrive_expect_tx(full_bar(stage), CF::STAGE_BYTES);
                     for (int t = 0; t < CF::PARTS; ++t) {
-                        tma_load_3d(a_smem + (stage * CF::PARTS + t) * CF::A_TILE, &mapA,
+                        tma_load_3d(a_smem + (stage * CF::PARTS + t) * CF::A_TILE, ui.ma,
                                     full_bar(stage), kb * CF::BK, y_a, t);
-                        tma_load_3d(b_smem + (stage * CF::PARTS + t) * CF::B_TILE, &mapB,
+                        tma_load_3d(b_smem + (stage * CF::PARTS + t) * CF::B_TILE, ui.mb,
                                     full_bar(stage), kb * CF::BK, y_b, t);
                     }
                     issued_mask |= 1u << stage;
@@ -396,9 +442,9 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
                 uint32_t accumulate = 0;
-                int kb0, kb1;
-                kb_range(u, kb0, kb1);
-                for (int kb = kb0; kb < kb1; ++kb) {
+                UnitInfo ui;
+                src.unit(u, ui);
+                for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
                     if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) {
                         ok = false;
                         break;
@@ -441,15 +487,15 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         for (int64_t u = blockIdx.x; u < num_units; u += gridDim.x) {
             if (!wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull)) break;
             tc_fence_after();
-            int64_t tm, tn;
-            tile_coords(u / splits, tiles_m, tiles_n, tm, tn);
-            float *dst = part ? part + (u % splits) * M * N : C;
-            const int64_t ldd = part ? M : ldc;
-            int kb0, kb1;
-            kb_range(u, kb0, kb1);
-            const float keep = kb0 < kb1 ? 1.f : 0.f;   // an empty K range contributes 0
-            const int64_t row = tm * BM + q * 32 + lane;
-            const int64_t col0 = tn * CF::BN;
+            UnitInfo ui;
+            src.unit(u, ui);
+            const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
+            float *dst = ui.dst;
+            const float alpha = ui.alpha, beta = ui.beta;
+            const bool part = ui.raw;
+            const float keep = ui.kb0 < ui.kb1 ? 1.f : 0.f;   // an empty K range contributes 0
+            const int64_t row = ui.tm * BM + q * 32 + lane;
+            const int64_t col0 = ui.tn * CF::BN;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
             const bool row_ok = row < M;
             // Chunks of 16 columns: load from TMEM, wait, store; a warp writes
@@ -459,8 +505,9 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             // slower on the store-bound K = 64 shapes.) Interior tiles take a
             // path with no per-element checks and a pointer bump per column:
             // on store-bound shapes the epilogue's instruction count is the limit.
-            const bool interior = (tm * BM + BM <= M) && (col0 + CF::BN <= N);
+            const bool interior = (ui.tm * BM + BM <= M) && (col0 + CF::BN <= N);
             float *colp = dst + row + col0 * ldd;
+#pragma unroll 1
             for (int c = 0; c < CF::BN; c += 16) {
                 uint32_t r[16];
                 tmem_ld16(taddr + (uint32_t)c, r);
@@ -475,24 +522,34 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
                         for (int j = 0; j < 16; ++j) { *p = a * __uint_as_float(r[j]); p += ldd; }
                     } else {
+                        // read all 16 C values before the first store: a store
+                        // may alias a later load, so interleaving them would
+                        // serialise 16 memory latencies
                         const float a = keep * alpha;
+                        float cv[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            *p = fmaf(a, __uint_as_float(r[j]), beta * *p);
-                            p += ldd;
-                        }
+                        for (int j = 0; j < 16; ++j) cv[j] = p[j * ldd];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) p[j * ldd] = fmaf(a, __uint_as_float(r[j]), beta * cv[j]);
                     }
                     continue;
                 }
                 if (!row_ok) continue;
+                {
+                    float cv[16];
+                    const bool rd = !part && beta != 0.f;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t col = col0 + c + j;
-                    if (col < N) {
-                        float *p = dst + row + col * ldd;
-                        const float x = keep * __uint_as_float(r[j]);
-                        if (part) *p = x;
-                        else *p = beta != 0.f ? fmaf(alpha, x, beta * *p) : alpha * x;
+                    for (int j = 0; j < 16; ++j)
+                        cv[j] = (rd && col0 + c + j < N) ? dst[row + (col0 + c + j) * ldd] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = col0 + c + j;
+                        if (col < N) {
+                            float *p = dst + row + col * ldd;
+                            const float x = keep * __uint_as_float(r[j]);
+                            if (part) *p = x;
+                            else *p = rd ? fmaf(alpha, x, beta * cv[j]) : alpha * x;
+                        }
                     }
                 }
             }
@@ -507,6 +564,38 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem_base, CF::TMEM_COLS);
+}
+
+template <int MODE, int RB>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
+                int64_t ldc, float *__restrict__ part, int splits, DeviceState *dstate,
+                uint64_t limit_ns) {
+    using CF = Cfg<MODE, RB>;
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&mapA);
+        prefetch_tmap(&mapB);
+    }
+    SingleSource<CF::BN, CF::BK> src;
+    src.ma = &mapA; src.mb = &mapB;
+    src.M = M; src.N = N; src.K = K;
+    src.alpha = alpha; src.beta = beta;
+    src.C = C; src.ldc = ldc;
+    src.part = part; src.splits = splits;
+    src.tiles_m = (int)((M + BM - 1) / BM);
+    src.tiles_n = (int)((N + CF::BN - 1) / CF::BN);
+    src.nkb = (int)((K + CF::BK - 1) / CF::BK);
+    tc_body<MODE, RB>(src, dstate, limit_ns);
+}
+
+template <int MODE, int RB>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_grouped_kernel(const TcProblem *__restrict__ probs, const TcItem *__restrict__ items,
+                  int64_t nitems, DeviceState *dstate, uint64_t limit_ns) {
+    using CF = Cfg<MODE, RB>;
+    GroupSource<CF::BN, CF::BK> src{probs, items, nitems};
+    tc_body<MODE, RB>(src, dstate, limit_ns);
 }
 
 // C = alpha * (sum over slices s = 0..S-1, in that order, of part_s) + beta*C
@@ -591,6 +680,7 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
     const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
+    if (units > 2147483647LL) return cudaErrorNotSupported;   // device raster is 32-bit
     int grid = a.sm_count > 0 ? a.sm_count : 1;
     if (units < grid) grid = (int)units;
     const uint64_t limit_ns = (uint64_t)a.wait_limit * 1000ull;
@@ -602,7 +692,56 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
 }
 
+template <int MODE, int RB>
+cudaError_t launch_grouped_mode(const TcProblem *probs, const TcItem *items, int64_t nitems,
+                                int sm_count, DeviceState *dstate, int64_t wait_limit,
+                                cudaStream_t s) {
+    using CF = Cfg<MODE, RB>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MODE, RB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CF::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    int grid = sm_count > 0 ? sm_count : 1;
+    if (nitems < grid) grid = (int)nitems;
+    tc_grouped_kernel<MODE, RB><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+        probs, items, nitems, dstate, (uint64_t)wait_limit * 1000ull);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int tc_tile_n(int mode) { return mode == 2 ? 128 : 256; }
+
+bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
+                         int64_t rows, bool a_side) {
+    const int rb = rb128 ? 128 : 64;
+    const bool tf32 = mode == 0;
+    const int bk = rb / (tf32 ? 4 : 2);
+    return make_map(map, tf32, packed, k, rows, split_kpad(mode, k), split_parts(mode),
+                    a_side ? BM : tc_tile_n(mode), bk, rb);
+}
+
+cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, const TcItem *items,
+                              int64_t nitems, int sm_count, DeviceState *dstate,
+                              int64_t wait_limit, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    switch (mode) {
+        case 0: return rb128 ? launch_grouped_mode<0, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
+                             : launch_grouped_mode<0, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 1: return rb128 ? launch_grouped_mode<1, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
+                             : launch_grouped_mode<1, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 2: return rb128 ? launch_grouped_mode<2, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
+                             : launch_grouped_mode<2, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
     // Shared-memory row width of a k-block. 64-byte rows (64-byte swizzle,

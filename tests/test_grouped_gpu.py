@@ -27,7 +27,7 @@ def group2000():
     return wl.grouped_problems(2000, seed=4)
 
 
-@pytest.mark.parametrize("algo", ("simt", "auto"))
+@pytest.mark.parametrize("algo", ("simt", "auto", "bf16x6"))
 def test_grouped_2000_against_oracle(group2000, algo):
     torch = torch_gpu()
     import paper_1912_04379_gb300 as gb
