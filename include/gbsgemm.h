@@ -277,6 +277,18 @@ GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site);
  * cleanly (see gb_get_device_error). Values < 1 are rejected (GB_ERR_ARG). */
 GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
 
+/* Whether gb_sgemm (and gb_sgemm_backward) may split the operands inside the
+ * tensor-core kernel instead of in a separate split/pack pass (default: 0).
+ * The fused form applies to SPLIT_BF16X3 and SPLIT_BF16X6 when A and B are
+ * 16-byte aligned with leading dimensions that are multiples of 4; it reads
+ * the FP32 operands once and needs no operand workspace (the workspace is
+ * still required for split-K partials). It consumes K in 32-element stages,
+ * so for K > 2048 its results are bit-identical to the two-pass form's. It
+ * is off by default because it is slower on this build: its in-place
+ * conversion moves each operand stage through shared memory three times
+ * (9.2 ms against 1.9 ms at M = N = K = 8192). */
+GB_API int gb_set_fused_split(gb_handle_t h, int enable);
+
 #ifdef __cplusplus
 }
 #endif

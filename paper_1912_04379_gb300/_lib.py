@@ -76,6 +76,7 @@ SIGNATURES = {
                        c_size, ctypes.POINTER(ErrReport), c_vp], c_int),
     "gb_get_device_error": ([c_vp, c_vp, ctypes.POINTER(c_int)], c_int),
     "gb_set_wait_limit": ([c_vp, c_i64], c_int),
+    "gb_set_fused_split": ([c_vp, c_int], c_int),
 }
 
 

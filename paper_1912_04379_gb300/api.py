@@ -98,6 +98,10 @@ class Handle:
             self._ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
         return self._ws
 
+    def set_fused_split(self, enable: bool):
+        """Allow (default) or forbid the split fused into the tensor-core kernel."""
+        _lib.check("gb_set_fused_split", self.lib.gb_set_fused_split(self.h, 1 if enable else 0))
+
     def set_wait_limit(self, microseconds: int):
         _lib.check("gb_set_wait_limit", self.lib.gb_set_wait_limit(self.h, int(microseconds)))
 

@@ -156,6 +156,26 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
     char *Pp = Bp + round_up(packed_bytes(mode, n, k), 1024);
     const int splits = split_k_factor(mode, m, n, k);
+    // Split fused into the tensor-core kernel, when the handle allows it and
+    // TMA can read A and B as they are; otherwise the separate split/pack
+    // pass. For K > 2048 both give bit-identical results.
+    if (h->fused_split && fused_supported(mode, A, lda, B, ldb, m, n, k)) {
+        FusedArgs f{};
+        f.mode = mode;
+        f.ta = is_trans(ta); f.tb = is_trans(tb);
+        f.m = m; f.n = n; f.k = k;
+        f.alpha = alpha; f.beta = beta;
+        f.A = A; f.lda = lda; f.B = B; f.ldb = ldb;
+        f.C = C; f.ldc = ldc;
+        f.part = splits > 1 ? reinterpret_cast<float *>(Pp) : nullptr;
+        f.splits = splits;
+        f.dstate = h->dstate;
+        f.wait_limit = h->wait_limit;
+        f.sm_count = h->sm_count;
+        cudaError_t fe = launch_tc_fused(f, s);
+        if (fe == cudaSuccess) return GB_OK;
+        if (fe != cudaErrorNotSupported) return GB_ERR_CUDA;
+    }
     cudaError_t e = pack_operand(mode, true, is_trans(ta), m, k, A, lda, Ap, s);
     if (e == cudaSuccess) e = pack_operand(mode, false, is_trans(tb), n, k, B, ldb, Bp, s);
     if (e != cudaSuccess) return GB_ERR_CUDA;
@@ -409,6 +429,12 @@ GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site) {
     if (cudaMemset(h->dstate->err, 0, sizeof(err)) != cudaSuccess) return GB_ERR_CUDA;
     if (site) *site = (int)err[0];
     return err[1] ? GB_ERR_TIMEOUT : GB_OK;
+}
+
+GB_API int gb_set_fused_split(gb_handle_t h, int enable) {
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    h->fused_split = enable != 0;
+    return GB_OK;
 }
 
 GB_API int gb_set_wait_limit(gb_handle_t h, int64_t polls) {

@@ -17,7 +17,8 @@ enum WaitSite : int {
     kSiteMmaAccEmpty = 3,     // MMA issuer waiting for the epilogue to drain TMEM
     kSiteEpiAccFull = 4,      // epilogue waiting for a finished accumulator
     kSiteTmemAlloc = 5,       // TMEM allocation did not complete
-    kSiteDrain = 6            // final drain of in-flight copies
+    kSiteDrain = 6,           // final drain of in-flight copies
+    kSiteConvert = 7          // split converter waiting for an FP32 tile or a free operand stage
 };
 
 // Device error word layout: err[0] = first failing site (0 = none),
@@ -41,6 +42,7 @@ struct gb_handle_s {
     // 0 = SIMT 64x64 tiles, 1 = SIMT 128x128 tiles, 2 = tensor cores (BF16 x 3).
     bool grouped_tuned;
     int grouped_choice[8];
+    bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
 };
 
 namespace gb {
@@ -95,6 +97,32 @@ cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s);
 // Number of K slices gb_sgemm uses for a split-precision problem (depends on
 // the shape only, so workspace sizes do not depend on the device).
 int split_k_factor(int mode, int64_t m, int64_t n, int64_t k);
+// C = alpha * (sum of S split-K partials, in slice order) + beta * C.
+cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part, float alpha,
+                                 float beta, float *C, int64_t ldc, cudaStream_t s);
+
+// ------------------------------------------ split fused into the kernel --
+struct FusedArgs {
+    int mode;                   // 1 = BF16 x 2 terms, 2 = BF16 x 3 terms
+    bool ta, tb;
+    int64_t m, n, k;
+    float alpha, beta;
+    const float *A; int64_t lda;
+    const float *B; int64_t ldb;
+    float *C; int64_t ldc;
+    float *part;                // split-K partials (splits x m x n floats) or null
+    int splits;
+    DeviceState *dstate;
+    int64_t wait_limit;
+    int sm_count;
+};
+// True when the caller's A and B can be read by TMA directly (16-byte
+// aligned, leading dimensions multiples of 4) for a BF16 split mode.
+bool fused_supported(int mode, const float *A, int64_t lda, const float *B, int64_t ldb,
+                     int64_t m, int64_t n, int64_t k);
+// Split-precision SGEMM reading FP32 operands directly (no pack pass).
+// cudaErrorNotSupported: use the two-pass path instead.
+cudaError_t launch_tc_fused(const FusedArgs &a, cudaStream_t s);
 // Workspace layout helpers shared by the API and the launcher.
 int64_t split_kpad(int mode, int64_t k);
 int split_parts(int mode);

@@ -21,28 +21,10 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "split_common.cuh"
 
 namespace gb {
 namespace {
-
-__device__ __forceinline__ float tf32_rne(float a) {
-    // Round to 10 explicit mantissa bits, nearest-even, by integer arithmetic
-    // on the encoding: add half an ulp of the target precision (minus one,
-    // plus the target's lowest kept bit), then clear the 13 dropped bits.
-    uint32_t u = __float_as_uint(a);
-    if ((u & 0x7f800000u) == 0x7f800000u) return a;
-    const uint32_t r = u + 0x0fffu + ((u >> 13) & 1u);
-    if ((r & 0x7f800000u) == 0x7f800000u) return __uint_as_float(u & 0xffffe000u);  // truncate
-    return __uint_as_float(r & 0xffffe000u);
-}
-
-__device__ __forceinline__ __nv_bfloat16 bf16_rne(float a) {
-    if (!isfinite(a)) return __float2bfloat16_rn(a);
-    __nv_bfloat16 h = __float2bfloat16_rn(a);
-    if (isinf(__bfloat162float(h)))                    // overflowed: truncate instead
-        h = __float2bfloat16_rz(a);
-    return h;
-}
 
 // Splits four consecutive k of one row and stores each term as one vector:
 // 4 TF32 words (16 bytes) or 4 BF16 values (8 bytes). idx is a multiple of 4
@@ -60,27 +42,13 @@ __device__ __forceinline__ void split_store4(const float v[4], void *out, int64_
         *reinterpret_cast<float4 *>(o) = make_float4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<float4 *>(o + ps) = make_float4(l[0], l[1], l[2], l[3]);
     } else {
-        __nv_bfloat16 t0[4], t1[4], t2[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float a = v[i];
-            const bool fin = isfinite(a);
-            t0[i] = bf16_rne(a);
-            const float r1 = fin ? a - __bfloat162float(t0[i]) : 0.f;
-            t1[i] = __float2bfloat16_rn(r1);
-            const float r2 = fin ? r1 - __bfloat162float(t1[i]) : 0.f;
-            t2[i] = __float2bfloat16_rn(r2);
-        }
+        constexpr int P = MODE == 2 ? 3 : 2;
+        uint32_t lo[P], hi[P];
+        split2_bf16<P>(v[0], v[1], lo);
+        split2_bf16<P>(v[2], v[3], hi);
         __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + idx;
-        auto pack = [](const __nv_bfloat16 t[4]) {
-            uint2 u;
-            u.x = (uint32_t)__bfloat16_as_ushort(t[0]) | ((uint32_t)__bfloat16_as_ushort(t[1]) << 16);
-            u.y = (uint32_t)__bfloat16_as_ushort(t[2]) | ((uint32_t)__bfloat16_as_ushort(t[3]) << 16);
-            return u;
-        };
-        *reinterpret_cast<uint2 *>(o) = pack(t0);
-        *reinterpret_cast<uint2 *>(o + ps) = pack(t1);
-        if (MODE == 2) *reinterpret_cast<uint2 *>(o + 2 * ps) = pack(t2);
+#pragma unroll
+        for (int p = 0; p < P; ++p) *reinterpret_cast<uint2 *>(o + p * ps) = make_uint2(lo[p], hi[p]);
     }
 }
 

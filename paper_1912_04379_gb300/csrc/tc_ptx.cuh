@@ -45,6 +45,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// As mbar_try_wait, but the thread may sleep in hardware for up to
+// `hint_ns` nanoseconds (it wakes as soon as the phase completes) instead of
+// returning at once: waiting warps then take no issue slots from the warps
+// doing work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -57,7 +73,7 @@ struct WaitCtx {
     uint64_t limit_ns;
 };
 
-__device__ __noinline__ void record_timeout(const WaitCtx &w, int site) {
+static __device__ __noinline__ void record_timeout(const WaitCtx &w, int site) {
     atomicCAS(&w.dstate->err[0], 0u, (unsigned)site);
     atomicAdd(&w.dstate->err[1], 1u);
     *w.abort = 1;
@@ -69,10 +85,13 @@ __device__ __forceinline__ bool wait_bounded(const WaitCtx &w, uint32_t bar, uin
                                              int site) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+    // Sleep in slices of at most 20 us (well below any useful wait limit) and
+    // check the deadline and the abort flag after each one.
+    const uint32_t slice = w.limit_ns < 20000ull ? (uint32_t)w.limit_ns : 20000u;
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, slice)) return true;
         if (*w.abort) return false;
-        if ((it & 15u) == 15u && global_ns() - t0 > w.limit_ns) {
+        if (global_ns() - t0 > w.limit_ns) {
             record_timeout(w, site);
             return false;
         }
@@ -206,9 +225,6 @@ __device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {
     }
 }
 
-// Tile raster in groups of GROUP_M tile rows (32-bit: the host guarantees
-// that the number of work units fits in an int).
-
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int x, int y) {
     asm volatile(
@@ -222,6 +238,139 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 // async proxy (tensor-core operand reads).
 __device__ __forceinline__ void fence_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+
+constexpr int GROUP_M = 16;                    // tile raster: 16 M-tiles per group
+
+// Tile raster in groups of GROUP_M tile rows (32-bit: the host guarantees
+// that the number of work units fits in an int).
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int64_t &tm,
+                                            int64_t &tn) {
+    const int per_group = GROUP_M * tiles_n;
+    const int g = tile / per_group;
+    const int first_m = g * GROUP_M;
+    const int gm = (tiles_m - first_m) < GROUP_M ? (tiles_m - first_m) : GROUP_M;
+    const int r = tile - g * per_group;
+    tm = first_m + r % gm;
+    tn = r / gm;
+}
+
+// What one work unit is: the operands' tensor maps, the output tile, the
+// range of k-blocks, and where and how the result is written.
+struct UnitInfo {
+    const CUtensorMap *ma, *mb;
+    int64_t M, N;                 // the problem's output size
+    int64_t tm, tn;               // tile coordinates
+    int kb0, kb1;                 // k-blocks [kb0, kb1)
+    float alpha, beta;
+    float *dst;                   // C, or this slice's partial-sum buffer
+    int64_t ldd;
+    bool raw;                     // write raw sums (split-K partial), no alpha/beta
+};
+
+// One GEMM: units are (tile, K slice) pairs in the grouped raster order.
+// Split units write raw partial sums to `part` (slice s at part + s*M*N,
+// column-major, ld = M); a separate pass reduces them.
+template <int BN, int BK>
+struct SingleSource {
+    const CUtensorMap *ma, *mb;
+    int64_t M, N, K;
+    float alpha, beta;
+    float *C;
+    int64_t ldc;
+    float *part;
+    int splits;
+    int tiles_m, tiles_n;
+    int nkb;
+    __device__ __forceinline__ int64_t num_units() const {
+        return (int64_t)tiles_m * tiles_n * splits;
+    }
+    // Not inlined: called once per unit by each role; keeping it out of line
+    // keeps the roles' register footprint small.
+    __device__ __noinline__ void unit(int64_t u64, UnitInfo &ui) const {
+        const int u = (int)u64;
+        tile_coords(u / splits, tiles_m, tiles_n, ui.tm, ui.tn);
+        const int sl = u % splits;
+        ui.kb0 = (int)((int64_t)sl * nkb / splits);
+        ui.kb1 = (int)((int64_t)(sl + 1) * nkb / splits);
+        ui.ma = ma; ui.mb = mb;
+        ui.M = M; ui.N = N;
+        ui.alpha = alpha; ui.beta = beta;
+        ui.raw = part != nullptr;
+        ui.dst = part ? part + sl * M * N : C;
+        ui.ldd = part ? M : ldc;
+    }
+};
+
+// Epilogue of one work unit for one epilogue warp: TMEM lanes q*32..q*32+31
+// (rows of the tile) of the accumulator at TMEM address `taddr`, BN columns,
+// to C (alpha/beta) or to a split-K partial buffer (raw sums).
+template <int BN>
+__device__ __noinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, int q, int lane) {
+    const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
+    float *dst = ui.dst;
+    const float alpha = ui.alpha, beta = ui.beta;
+    const bool part = ui.raw;
+    const float keep = ui.kb0 < ui.kb1 ? 1.f : 0.f;   // an empty K range contributes 0
+    const int64_t row = ui.tm * BM + q * 32 + lane;
+    const int64_t col0 = ui.tn * BN;
+    const bool row_ok = row < M;
+    // Chunks of 16 columns: load from TMEM, wait, store; a warp writes
+    // 128 contiguous bytes of one column per store instruction. (Keeping
+    // more TMEM loads in flight, pipelining them against the stores, or
+    // staging whole 512-byte columns through shared memory all measured
+    // slower on the store-bound K = 64 shapes.) Interior tiles take a
+    // path with no per-element checks and a pointer bump per column:
+    // on store-bound shapes the epilogue's instruction count is the limit.
+    const bool interior = (ui.tm * BM + BM <= M) && (col0 + BN <= N);
+    float *colp = dst + row + col0 * ldd;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c, r);
+        tmem_wait16(r);
+        if (interior) {
+            float *p = colp + c * ldd;
+            if (part) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { *p = keep * __uint_as_float(r[j]); p += ldd; }
+            } else if (beta == 0.f) {
+                const float a = keep * alpha;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { *p = a * __uint_as_float(r[j]); p += ldd; }
+            } else {
+                // read all 16 C values before the first store: a store
+                // may alias a later load, so interleaving them would
+                // serialise 16 memory latencies
+                const float a = keep * alpha;
+                float cv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cv[j] = p[j * ldd];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) p[j * ldd] = fmaf(a, __uint_as_float(r[j]), beta * cv[j]);
+            }
+            continue;
+        }
+        if (!row_ok) continue;
+        {
+            float cv[16];
+            const bool rd = !part && beta != 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                cv[j] = (rd && col0 + c + j < N) ? dst[row + (col0 + c + j) * ldd] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int64_t col = col0 + c + j;
+                if (col < N) {
+                    float *p = dst + row + col * ldd;
+                    const float x = keep * __uint_as_float(r[j]);
+                    if (part) *p = x;
+                    else *p = rd ? fmaf(alpha, x, beta * cv[j]) : alpha * x;
+                }
+            }
+        }
+    }
 }
 
 }  // namespace tcx

@@ -46,7 +46,6 @@ namespace {
 
 using namespace tcx;
 constexpr int NUM_THREADS = 192;
-constexpr int GROUP_M = 16;                    // tile raster: 16 M-tiles per group
 
 // ----------------------------------------------------------- the kernel --
 template <int MODE, int RB>
@@ -68,62 +67,6 @@ struct Cfg {
     static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
     static_assert(STAGES >= 2, "need at least two stages");
     static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
-};
-
-__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int64_t &tm,
-                                            int64_t &tn) {
-    const int per_group = GROUP_M * tiles_n;
-    const int g = tile / per_group;
-    const int first_m = g * GROUP_M;
-    const int gm = (tiles_m - first_m) < GROUP_M ? (tiles_m - first_m) : GROUP_M;
-    const int r = tile - g * per_group;
-    tm = first_m + r % gm;
-    tn = r / gm;
-}
-
-// What one work unit is: the operands' tensor maps, the output tile, the
-// range of k-blocks, and where and how the result is written.
-struct UnitInfo {
-    const CUtensorMap *ma, *mb;
-    int64_t M, N;                 // the problem's output size
-    int64_t tm, tn;               // tile coordinates
-    int kb0, kb1;                 // k-blocks [kb0, kb1)
-    float alpha, beta;
-    float *dst;                   // C, or this slice's partial-sum buffer
-    int64_t ldd;
-    bool raw;                     // write raw sums (split-K partial), no alpha/beta
-};
-
-// One GEMM: units are (tile, K slice) pairs in the grouped raster order.
-// Split units write raw partial sums to `part` (slice s at part + s*M*N,
-// column-major, ld = M); a separate pass reduces them.
-template <int BN, int BK>
-struct SingleSource {
-    const CUtensorMap *ma, *mb;
-    int64_t M, N, K;
-    float alpha, beta;
-    float *C;
-    int64_t ldc;
-    float *part;
-    int splits;
-    int tiles_m, tiles_n;
-    int nkb;
-    __device__ __forceinline__ int64_t num_units() const {
-        return (int64_t)tiles_m * tiles_n * splits;
-    }
-    __device__ __forceinline__ void unit(int64_t u64, UnitInfo &ui) const {
-        const int u = (int)u64;
-        tile_coords(u / splits, tiles_m, tiles_n, ui.tm, ui.tn);
-        const int sl = u % splits;
-        ui.kb0 = (int)((int64_t)sl * nkb / splits);
-        ui.kb1 = (int)((int64_t)(sl + 1) * nkb / splits);
-        ui.ma = ma; ui.mb = mb;
-        ui.M = M; ui.N = N;
-        ui.alpha = alpha; ui.beta = beta;
-        ui.raw = part != nullptr;
-        ui.dst = part ? part + sl * M * N : C;
-        ui.ldd = part ? M : ldc;
-    }
 };
 
 // Many GEMMs: units are the planned (problem, tile) items; each problem has
@@ -295,70 +238,8 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             tc_fence_after();
             UnitInfo ui;
             src.unit(u, ui);
-            const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
-            float *dst = ui.dst;
-            const float alpha = ui.alpha, beta = ui.beta;
-            const bool part = ui.raw;
-            const float keep = ui.kb0 < ui.kb1 ? 1.f : 0.f;   // an empty K range contributes 0
-            const int64_t row = ui.tm * BM + q * 32 + lane;
-            const int64_t col0 = ui.tn * CF::BN;
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
-            const bool row_ok = row < M;
-            // Chunks of 16 columns: load from TMEM, wait, store; a warp writes
-            // 128 contiguous bytes of one column per store instruction. (Keeping
-            // more TMEM loads in flight, pipelining them against the stores, or
-            // staging whole 512-byte columns through shared memory all measured
-            // slower on the store-bound K = 64 shapes.) Interior tiles take a
-            // path with no per-element checks and a pointer bump per column:
-            // on store-bound shapes the epilogue's instruction count is the limit.
-            const bool interior = (ui.tm * BM + BM <= M) && (col0 + CF::BN <= N);
-            float *colp = dst + row + col0 * ldd;
-#pragma unroll 1
-            for (int c = 0; c < CF::BN; c += 16) {
-                uint32_t r[16];
-                tmem_ld16(taddr + (uint32_t)c, r);
-                tmem_wait16(r);
-                if (interior) {
-                    float *p = colp + c * ldd;
-                    if (part) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) { *p = keep * __uint_as_float(r[j]); p += ldd; }
-                    } else if (beta == 0.f) {
-                        const float a = keep * alpha;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) { *p = a * __uint_as_float(r[j]); p += ldd; }
-                    } else {
-                        // read all 16 C values before the first store: a store
-                        // may alias a later load, so interleaving them would
-                        // serialise 16 memory latencies
-                        const float a = keep * alpha;
-                        float cv[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) cv[j] = p[j * ldd];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) p[j * ldd] = fmaf(a, __uint_as_float(r[j]), beta * cv[j]);
-                    }
-                    continue;
-                }
-                if (!row_ok) continue;
-                {
-                    float cv[16];
-                    const bool rd = !part && beta != 0.f;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        cv[j] = (rd && col0 + c + j < N) ? dst[row + (col0 + c + j) * ldd] : 0.f;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = col0 + c + j;
-                        if (col < N) {
-                            float *p = dst + row + col * ldd;
-                            const float x = keep * __uint_as_float(r[j]);
-                            if (part) *p = x;
-                            else *p = rd ? fmaf(alpha, x, beta * cv[j]) : alpha * x;
-                        }
-                    }
-                }
-            }
+            store_tile<CF::BN>(ui, tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN),
+                               q, lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(acc));
@@ -417,16 +298,6 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const float *_
         float *p = C + i + j * ldc;
         *p = beta != 0.f ? fmaf(alpha, acc, beta * *p) : alpha * acc;
     }
-}
-
-cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part, float alpha,
-                                 float beta, float *C, int64_t ldc, cudaStream_t s) {
-    const int64_t total = m * n;
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    if (blocks < 1) blocks = 1;
-    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, n, S, part, alpha, beta, C, ldc);
-    return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------- host --
@@ -522,6 +393,16 @@ cudaError_t launch_grouped_mode(const TcProblem *probs, const TcItem *items, int
 }
 
 }  // namespace
+
+cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part, float alpha,
+                                 float beta, float *C, int64_t ldc, cudaStream_t s) {
+    const int64_t total = m * n;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, n, S, part, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
 
 int tc_tile_n(int mode) { return mode == 2 ? 128 : 256; }
 
