@@ -45,22 +45,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// As mbar_try_wait, but the thread may sleep in hardware for up to
-// `hint_ns` nanoseconds (it wakes as soon as the phase completes) instead of
-// returning at once: waiting warps then take no issue slots from the warps
-// doing work.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -83,15 +67,15 @@ static __device__ __noinline__ void record_timeout(const WaitCtx &w, int site) {
 // Returns false if the limit expired (recorded) or another role aborted.
 __device__ __forceinline__ bool wait_bounded(const WaitCtx &w, uint32_t bar, uint32_t parity,
                                              int site) {
+    // (A variant that sleeps in try_wait with a suspend-time hint measured
+    // slower on short-K shapes: the wake-up latency lands on every tile
+    // hand-off. Plain polling it is.)
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    // Sleep in slices of at most 20 us (well below any useful wait limit) and
-    // check the deadline and the abort flag after each one.
-    const uint32_t slice = w.limit_ns < 20000ull ? (uint32_t)w.limit_ns : 20000u;
-    for (;;) {
-        if (mbar_try_wait_sleep(bar, parity, slice)) return true;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
         if (*w.abort) return false;
-        if (global_ns() - t0 > w.limit_ns) {
+        if ((it & 15u) == 15u && global_ns() - t0 > w.limit_ns) {
             record_timeout(w, site);
             return false;
         }
@@ -286,9 +270,7 @@ struct SingleSource {
     __device__ __forceinline__ int64_t num_units() const {
         return (int64_t)tiles_m * tiles_n * splits;
     }
-    // Not inlined: called once per unit by each role; keeping it out of line
-    // keeps the roles' register footprint small.
-    __device__ __noinline__ void unit(int64_t u64, UnitInfo &ui) const {
+    __device__ __forceinline__ void unit(int64_t u64, UnitInfo &ui) const {
         const int u = (int)u64;
         tile_coords(u / splits, tiles_m, tiles_n, ui.tm, ui.tn);
         const int sl = u % splits;
@@ -307,7 +289,7 @@ struct SingleSource {
 // (rows of the tile) of the accumulator at TMEM address `taddr`, BN columns,
 // to C (alpha/beta) or to a split-K partial buffer (raw sums).
 template <int BN>
-__device__ __noinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, int q, int lane) {
+__device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, int q, int lane) {
     const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
     float *dst = ui.dst;
     const float alpha = ui.alpha, beta = ui.beta;
