@@ -294,7 +294,8 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
     float *dst = ui.dst;
     const float alpha = ui.alpha, beta = ui.beta;
     const bool part = ui.raw;
-    const float keep = ui.kb0 < ui.kb1 ? 1.f : 0.f;   // an empty K range contributes 0
+    const bool empty = ui.kb0 >= ui.kb1;   // an empty K range contributes 0 (TMEM unwritten)
+    const float a = part ? 1.f : alpha;
     const int64_t row = ui.tm * BM + q * 32 + lane;
     const int64_t col0 = ui.tn * BN;
     const bool row_ok = row < M;
@@ -312,45 +313,39 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
         uint32_t r[16];
         tmem_ld16(taddr + (uint32_t)c, r);
         tmem_wait16(r);
-        if (interior) {
-            float *p = colp + c * ldd;
-            if (part) {
+        if (empty) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) { *p = keep * __uint_as_float(r[j]); p += ldd; }
-            } else if (beta == 0.f) {
-                const float a = keep * alpha;
+            for (int j = 0; j < 16; ++j) r[j] = 0u;
+        }
+        float *p = colp + c * ldd;
+        if (interior) {
+            if (part || beta == 0.f) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) { *p = a * __uint_as_float(r[j]); p += ldd; }
             } else {
-                // read all 16 C values before the first store: a store
-                // may alias a later load, so interleaving them would
+                // all 16 C values are read before the first store: a store
+                // may alias a later load, and interleaving them would
                 // serialise 16 memory latencies
-                const float a = keep * alpha;
                 float cv[16];
+                const float *qc = p;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) cv[j] = p[j * ldd];
+                for (int j = 0; j < 16; ++j) { cv[j] = *qc; qc += ldd; }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) p[j * ldd] = fmaf(a, __uint_as_float(r[j]), beta * cv[j]);
+                for (int j = 0; j < 16; ++j) { *p = fmaf(a, __uint_as_float(r[j]), beta * cv[j]); p += ldd; }
             }
             continue;
         }
         if (!row_ok) continue;
-        {
-            float cv[16];
-            const bool rd = !part && beta != 0.f;
+        const int ncol = (int)(N - (col0 + c) < 16 ? N - (col0 + c) : 16);
+        const bool rd = !part && beta != 0.f;
+        float cv[16];
+        const float *qc = p;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                cv[j] = (rd && col0 + c + j < N) ? dst[row + (col0 + c + j) * ldd] : 0.f;
+        for (int j = 0; j < 16; ++j) { cv[j] = (rd && j < ncol) ? *qc : 0.f; qc += ldd; }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int64_t col = col0 + c + j;
-                if (col < N) {
-                    float *p = dst + row + col * ldd;
-                    const float x = keep * __uint_as_float(r[j]);
-                    if (part) *p = x;
-                    else *p = rd ? fmaf(alpha, x, beta * cv[j]) : alpha * x;
-                }
-            }
+        for (int j = 0; j < 16; ++j) {
+            if (j < ncol) *p = rd ? fmaf(a, __uint_as_float(r[j]), beta * cv[j]) : a * __uint_as_float(r[j]);
+            p += ldd;
         }
     }
 }

@@ -178,6 +178,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t idesc = instr_desc<CF::TF32, CF::BN>();
+            const uint64_t desc_a0 = smem_desc<RB>(a_smem), desc_b0 = smem_desc<RB>(b_smem);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -196,17 +197,22 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
                         break;
                     }
                     tc_fence_after();
+                    // The descriptor's start-address field is the byte address
+                    // >> 4, so offsetting a descriptor by whole 16-byte units
+                    // is an add: one base descriptor per stage and operand,
+                    // constant offsets for the term and the k-step.
+                    const uint64_t da = desc_a0 + (uint64_t)((stage * CF::PARTS * CF::A_TILE) >> 4);
+                    const uint64_t db = desc_b0 + (uint64_t)((stage * CF::PARTS * CF::B_TILE) >> 4);
 #pragma unroll
                     for (int q = 0; q < CF::NPAIRS; ++q) {
                         int sa, sb;
                         pair_of<MODE>(q, sa, sb);
-                        const uint32_t a0 = a_smem + (stage * CF::PARTS + sa) * CF::A_TILE;
-                        const uint32_t b0 = b_smem + (stage * CF::PARTS + sb) * CF::B_TILE;
 #pragma unroll
                         for (int ks = 0; ks < CF::KSTEPS; ++ks) {
-                            mma_issue<CF::TF32>(d_tmem, smem_desc<RB>(a0 + ks * CF::KSTEP_BYTES),
-                                                smem_desc<RB>(b0 + ks * CF::KSTEP_BYTES), idesc,
-                                                accumulate);
+                            mma_issue<CF::TF32>(
+                                d_tmem, da + (uint64_t)((sa * CF::A_TILE + ks * CF::KSTEP_BYTES) >> 4),
+                                db + (uint64_t)((sb * CF::B_TILE + ks * CF::KSTEP_BYTES) >> 4), idesc,
+                                accumulate);
                             accumulate = 1;
                         }
                     }
