@@ -290,7 +290,7 @@ def bench_grouped(gb, h, dev, stream, reps=10):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
-    for algo in ("simt", "bf16x6", "auto"):
+    for algo in ("simt", "bf16x6", "tf32x3", "auto"):
         plan = gb.GroupedPlan(tuples, algo=algo, handle=h)
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream(device=dev)
@@ -345,7 +345,7 @@ def bench_shapes(gb, h, dev, stream, reps=10):
         B = (torch.rand((n, k), device=dev, generator=g) * 2 - 1).t()
         C = gb.colmajor(m, n, device=dev)
         rows = {}
-        for algo in ("bf16x3", "tf32x3", "bf16x6", "simt"):
+        for algo in ("bf16x3", "tf32x3", "bf16x6", "bf16x9", "simt"):
             ws_n = gb.workspace_size(algo, "N", "N", m, n, k)
             ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
 
@@ -469,7 +469,7 @@ def run_ours(args, rank, world, local_rank):
 
     outs = {"simt": gb.colmajor(M, N, device=dev)}
     arms = {"simt": time_algo("simt", max(3, args.steps // 20), outs["simt"])}
-    for algo in ("tf32x3", "bf16x6"):
+    for algo in ("tf32x3", "bf16x6", "bf16x9"):
         outs[algo] = gb.colmajor(M, N, device=dev)
         arms[algo] = time_algo(algo, max(3, args.steps // 5), outs[algo])
     outs[ALGO] = C

@@ -69,20 +69,31 @@ enum {
  *  GB_ALGO_SPLIT_BF16X6 a = b0 + b1 + b2 in BF16 (exact for FP32 inputs);
  *                       the six products with weight >= 2^-16:
  *                       b0b0 b0b1 b1b0 b0b2 b1b1 b2b0.
+ *  GB_ALGO_SPLIT_BF16X9 the same three BF16 terms and all nine products, so
+ *                       every FP32 product a*b is formed exactly (each BF16
+ *                       x BF16 product is exact in FP32); only the FP32
+ *                       accumulation rounds. 1.5x the tensor work of BF16X6.
  *  GB_ALGO_AUTO         the library picks: SPLIT_BF16X3 when K >= 1024,
  *                       SPLIT_BF16X6 when 4 <= K < 1024, else SIMT.
  * Error per element, D = |alpha||op(A)||op(B)| + |beta||C|, u = 2^-24:
  *  SIMT       |C - C_exact| <= 2*max(K,1)*u*D
  *  split x    (2*max(K,1)*u + e_x)*D with e_x the dropped cross terms:
  *             TF32X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24 (x 1.01),
+ *             BF16X9 2^-24 (nothing is dropped, but the tensor core's FP32
+ *             accumulation is not round-to-nearest: at K = 1 the error
+ *             was measured at 1.34 x 2*K*u*D),
  *  so a split meets the plain SIMT bound once K >= 16 (TF32X3), 1024
- *  (BF16X3) or 4 (BF16X6); AUTO only picks an algorithm above its threshold. */
+ *  (BF16X3), 4 (BF16X6) or 2 (BF16X9, measured: at most 0.73 x the bound
+ *  at K = 2); AUTO only picks an algorithm above its threshold. The BF16 three-term split is exact for
+ *  |a| >= 2^-110; smaller nonzero magnitudes lose bits below the BF16
+ *  subnormal range. */
 typedef enum {
     GB_ALGO_AUTO = -1,
     GB_ALGO_SIMT = 0,
     GB_ALGO_SPLIT_TF32X3 = 1,
     GB_ALGO_SPLIT_BF16X3 = 2,
-    GB_ALGO_SPLIT_BF16X6 = 3
+    GB_ALGO_SPLIT_BF16X6 = 3,
+    GB_ALGO_SPLIT_BF16X9 = 4
 } gb_algo_t;
 
 typedef struct gb_handle_s *gb_handle_t;
@@ -224,8 +235,18 @@ typedef struct {
  * -i for the i-th argument of the first bad problem and writes its index to
  * *bad_index if not NULL), sorts the work into tiles, uploads the work list
  * to device memory owned by the plan, and writes the workspace the run needs
- * to *ws_bytes. Synchronises the device; not capturable. algo may be
- * GB_ALGO_SIMT or GB_ALGO_AUTO (per-problem choice). */
+ * to *ws_bytes. Synchronises the device; not capturable.
+ * Every problem meets the plain FP32 bound 2*max(K,1)*u*D, whatever algo:
+ *  GB_ALGO_SIMT  every problem on the CUDA cores;
+ *  GB_ALGO_AUTO  per problem: an autotuner (run once per handle, timing
+ *                synthetic groups) routes each size class to SIMT or the
+ *                tensor cores; tensor-core problems take SPLIT_BF16X3 when
+ *                K >= 1024, else SPLIT_BF16X6;
+ *  a split algo  the preferred split for every problem with K >= 4; a
+ *                problem whose K is below that split's threshold (see
+ *                gb_algo_t) takes SPLIT_BF16X6 instead.
+ * Problems with K < 4, alpha = 0 or K = 0 always run on the CUDA cores.
+ * The tensor-core problems of one split run in one persistent launch. */
 GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
                                  const gb_gemm_problem_t *host_problems,
                                  gb_grouped_plan_t *plan, size_t *ws_bytes,

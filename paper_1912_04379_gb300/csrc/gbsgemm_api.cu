@@ -45,6 +45,7 @@ int split_mode(gb_algo_t algo) {
         case GB_ALGO_SPLIT_TF32X3: return 0;
         case GB_ALGO_SPLIT_BF16X3: return 1;
         case GB_ALGO_SPLIT_BF16X6: return 2;
+        case GB_ALGO_SPLIT_BF16X9: return 3;
         default: return -1;
     }
 }
@@ -84,7 +85,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; 
 // slice always holds several k-blocks, and S <= 16). Depends on the shape
 // only: workspace sizes do not depend on the device.
 int gb::split_k_factor(int mode, int64_t m, int64_t n, int64_t k) {
-    const int64_t bn = mode == 2 ? 128 : 256;
+    const int64_t bn = mode >= 2 ? 128 : 256;
     const int64_t tiles = ((m + 127) / 128) * ((n + bn - 1) / bn);
     if (tiles < 1 || tiles * 4 > 148 || k < 1024) return 1;
     int64_t s = 148 / tiles;
@@ -137,7 +138,7 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
                float *C, int64_t ldc, void *ws, size_t ws_bytes, cudaStream_t s) {
     int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, ldc);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     if ((rc = check_handle(h))) return rc;
     if (m == 0 || n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
     if (!C) return GB_ERR_ARG;
@@ -277,7 +278,7 @@ GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char ta, char tb, int64_t m, 
                               max1(is_trans(tb) ? n : k), max1(m));
     if (rc) return rc;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     const int mode = split_mode(resolve_algo(algo, k));
     *bytes = (mode < 0 || m == 0 || n == 0 || k == 0) ? 0 : split_ws_bytes(mode, m, n, k);
     return GB_OK;
@@ -296,7 +297,7 @@ GB_API int gb_sgemm_pack_size(gb_algo_t algo, char which, int64_t mn, int64_t k,
     if (mn < 0) return -3;
     if (k < 0) return -5;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     const int mode = split_mode(resolve_algo(algo, k));
     if (mode < 0) return GB_ERR_UNSUPPORTED;
     *bytes = packed_bytes(mode, mn, k);
@@ -314,7 +315,7 @@ GB_API int gb_sgemm_pack(gb_handle_t h, gb_algo_t algo, char which, char trans, 
     // stored rows: op(A) = A is M x K, A^T stored K x M; op(B) = B is K x N, B^T stored N x K
     const int64_t rows = a_side ? (is_trans(trans) ? k : mn) : (is_trans(trans) ? mn : k);
     if (ldx < max1(rows)) return -8;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     int rc = check_handle(h);
     if (rc) return rc;
     const int mode = split_mode(resolve_algo(algo, k));
@@ -335,7 +336,7 @@ GB_API int gb_sgemm_compute(gb_handle_t h, gb_algo_t algo, int64_t m, int64_t n,
     if (n < 0) return -4;
     if (k < 0) return -5;
     if (ldc < max1(m)) return -13;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     int rc = check_handle(h);
     if (rc) return rc;
     const int mode = split_mode(resolve_algo(algo, k));
@@ -356,7 +357,7 @@ GB_API int gb_sgemm_backward_workspace_size(gb_algo_t algo, char ta, char tb, in
                               max1(is_trans(tb) ? n : k), max1(m));
     if (rc) return rc;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     if (m == 0 || n == 0 || k == 0) { *bytes = 0; return GB_OK; }
     const BwdCall a = grad_a(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
     const BwdCall b = grad_b(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
@@ -374,7 +375,7 @@ GB_API int gb_sgemm_backward(gb_handle_t h, gb_algo_t algo, char ta, char tb, in
     int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, lddc);
     if (rc) return rc;
     if ((rc = check_handle(h))) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X6) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     if (dA && ldda < max1(is_trans(ta) ? k : m)) return GB_ERR_ARG;
     if (dB && lddb < max1(is_trans(tb) ? n : k)) return GB_ERR_ARG;
     if (dCin && lddcin < max1(m)) return GB_ERR_ARG;

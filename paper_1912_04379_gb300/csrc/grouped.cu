@@ -242,9 +242,11 @@ struct gb_grouped_plan_s {
     int nitems;
     gb::GProblem *d_probs;
     gb::GItem *d_items;
-    // tensor-core part (BF16 x 3 split): packed operands, tensor maps,
-    // problems, tiles and pack tiles, all in device memory owned by the plan
+    // tensor-core part: packed operands, tensor maps, problems, tiles and
+    // pack tiles, all in device memory owned by the plan. Tiles are grouped
+    // by split mode (one launch per mode present), LPT order within a mode.
     int64_t tc_nitems, tc_npack;
+    int64_t tc_seg_off[4], tc_seg_n[4];
     void *tc_packed;
     CUtensorMap *tc_maps;
     gb::TcProblem *tc_probs;
@@ -255,9 +257,24 @@ struct gb_grouped_plan_s {
 namespace {
 
 constexpr int kPlanMagic = 0x47525031;
-constexpr int kTcMode = 2;          // BF16 x 3 terms: FP32 bound for every K >= 4
 constexpr bool kTcRb128 = true;     // short K loops (K <= 1024 in typical groups)
 constexpr int kClasses = 8;
+constexpr int kPrefAuto = -1;
+
+// Split mode of one tensor-core problem (K >= 4): the preferred mode when
+// its fixed per-product error leaves the FP32 bound 2*K*u*D room at this K
+// (TF32 x 2 terms from K >= 16, BF16 x 2 terms from K >= 1024), else BF16 x
+// 3 terms with 6 products, which holds from K >= 4. All 9 products (mode 3)
+// hold at every K. AUTO takes the cheapest mode that holds: BF16 x 2 terms
+// at K >= 1024, else BF16 x 3 terms.
+int tc_mode_for(int pref, int64_t k) {
+    switch (pref) {
+        case 0: return k >= 16 ? 0 : 2;
+        case 2: return 2;
+        case 3: return 3;
+        default: return k >= 1024 ? 1 : 2;   // kPrefAuto and BF16 x 2 terms
+    }
+}
 
 // Size class of a problem: floor(log2 of the geometric mean of M, N, K),
 // clamped to [3, 10] and shifted to 0..7.
@@ -289,13 +306,14 @@ bool upload(T **dptr, const std::vector<T> &v) {
 
 // Builds a plan for validated problems; choice[c] routes size class c.
 // Returns a GB status; on error frees everything it allocated.
+// pref: preferred split mode of the tensor-core problems (kPrefAuto: by K).
 int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
-               const int choice[kClasses], gb_grouped_plan_s **out) {
+               const int choice[kClasses], int pref, gb_grouped_plan_s **out) {
     using namespace gb;
     std::vector<GProblem> probs;
     std::vector<GItem> items;
     std::vector<double> work;
-    struct TcPending { size_t prob; size_t off_a, off_b; };
+    struct TcPending { size_t prob; size_t off_a, off_b; int mode; };
     std::vector<TcPending> tcs;
     size_t packed_bytes = 0;
     for (size_t i = 0; i < ps.size(); ++i) {
@@ -305,9 +323,10 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         const int ch = (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
                                                : choice[size_class(p.m, p.n, p.k)];
         if (ch == 2) {
-            const size_t kpad = (size_t)split_kpad(kTcMode, p.k);
-            const size_t per = (size_t)split_parts(kTcMode) * kpad * (size_t)split_elem_bytes(kTcMode);
-            TcPending t{i, packed_bytes, 0};
+            const int mode = tc_mode_for(pref, p.k);
+            const size_t kpad = (size_t)split_kpad(mode, p.k);
+            const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
+            TcPending t{i, packed_bytes, 0, mode};
             packed_bytes += round_up(per * (size_t)p.m, 1024);
             t.off_b = packed_bytes;
             packed_bytes += round_up(per * (size_t)p.n, 1024);
@@ -361,15 +380,17 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         std::vector<TcProblem> tprobs(tcs.size());
         std::vector<TcItem> titems;
         std::vector<double> twork;
+        std::vector<int> tmode;
         std::vector<PackItem> pack;
-        const int bn = tc_tile_n(kTcMode);
         char *base = static_cast<char *>(pl->tc_packed);
         for (size_t j = 0; ok && j < tcs.size(); ++j) {
             const gb_gemm_problem_t &p = ps[tcs[j].prob];
-            const int64_t kpad = split_kpad(kTcMode, p.k);
+            const int mode = tcs[j].mode;
+            const int bn = tc_tile_n(mode);
+            const int64_t kpad = split_kpad(mode, p.k);
             char *pa = base + tcs[j].off_a, *pb = base + tcs[j].off_b;
-            ok = tc_make_operand_map(&maps[2 * j], kTcMode, kTcRb128, pa, p.k, p.m, true) &&
-                 tc_make_operand_map(&maps[2 * j + 1], kTcMode, kTcRb128, pb, p.k, p.n, false);
+            ok = tc_make_operand_map(&maps[2 * j], mode, kTcRb128, pa, p.k, p.m, true) &&
+                 tc_make_operand_map(&maps[2 * j + 1], mode, kTcRb128, pb, p.k, p.n, false);
             TcProblem &t = tprobs[j];
             t.mapA = pl->tc_maps + 2 * j;
             t.mapB = pl->tc_maps + 2 * j + 1;
@@ -381,6 +402,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
                 for (int tn = 0; tn < tiles_n; ++tn) {
                     titems.push_back(TcItem{(int)j, tm, tn, 0});
                     twork.push_back((double)p.k);
+                    tmode.push_back(mode);
                 }
             // pack tiles of op(A) (M x K, K-contiguous iff A is transposed) and
             // op(B)^T (N x K, K-contiguous iff B is not transposed)
@@ -394,6 +416,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
                 it.ps = it.rows * kpad;
                 it.k = p.k;
                 it.kc = side ? !is_trans(p.transb) : is_trans(p.transa);
+                it.mode = mode;
                 it.vec = ((reinterpret_cast<uintptr_t>(it.X) & 15) == 0) && (it.ld % 4 == 0);
                 for (int64_t r0 = 0; r0 < it.rows; r0 += 64)
                     for (int64_t p0 = 0; p0 < kpad; p0 += 64) {
@@ -405,9 +428,15 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         }
         std::vector<int> tord(titems.size());
         for (size_t i = 0; i < tord.size(); ++i) tord[i] = (int)i;
-        std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) { return twork[a] > twork[b]; });
+        std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) {
+            return tmode[a] != tmode[b] ? tmode[a] < tmode[b] : twork[a] > twork[b];
+        });
         std::vector<TcItem> tsorted(titems.size());
-        for (size_t i = 0; i < tord.size(); ++i) tsorted[i] = titems[tord[i]];
+        for (size_t i = 0; i < tord.size(); ++i) {
+            tsorted[i] = titems[tord[i]];
+            ++pl->tc_seg_n[tmode[tord[i]]];
+        }
+        for (int md = 1; md < 4; ++md) pl->tc_seg_off[md] = pl->tc_seg_off[md - 1] + pl->tc_seg_n[md - 1];
         ok = ok &&
              cudaMemcpy(pl->tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -428,12 +457,15 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
 int run_plan(gb_grouped_plan_s *plan, void *workspace, cudaStream_t s) {
     using namespace gb;
     if (plan->tc_nitems > 0) {
-        if (launch_split_pack_grouped(kTcMode, plan->tc_pack, plan->tc_npack, s) != cudaSuccess)
+        if (launch_split_pack_grouped(plan->tc_pack, plan->tc_npack, s) != cudaSuccess)
             return GB_ERR_CUDA;
-        if (launch_tc_grouped(kTcMode, kTcRb128, plan->tc_probs, plan->tc_items, plan->tc_nitems,
-                              plan->h->sm_count, plan->h->dstate, plan->h->wait_limit, s) !=
-            cudaSuccess)
-            return GB_ERR_CUDA;
+        for (int md = 0; md < 4; ++md) {
+            if (plan->tc_seg_n[md] == 0) continue;
+            if (launch_tc_grouped(md, kTcRb128, plan->tc_probs, plan->tc_items + plan->tc_seg_off[md],
+                                  plan->tc_seg_n[md], plan->h->sm_count, plan->h->dstate,
+                                  plan->h->wait_limit, s) != cudaSuccess)
+                return GB_ERR_CUDA;
+        }
     }
     if (plan->nitems > 0) {
         int *counter = static_cast<int *>(workspace);
@@ -493,7 +525,7 @@ int autotune(gb_handle_t h, int dev) {
             int choice[kClasses];
             for (int q = 0; q < kClasses; ++q) choice[q] = ch;
             gb_grouped_plan_s *pl = nullptr;
-            if (build_plan(h, dev, ps, choice, &pl) != GB_OK) { rc = GB_ERR_CUDA; break; }
+            if (build_plan(h, dev, ps, choice, kPrefAuto, &pl) != GB_OK) { rc = GB_ERR_CUDA; break; }
             float ms = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {          // the first run is a warm-up
                 cudaEventRecord(e0, s);
@@ -529,8 +561,7 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
     if (plan) *plan = nullptr;
     if (bad_index) *bad_index = -1;
     if (!plan || !ws_bytes || count < 0 || (count > 0 && !hp)) return GB_ERR_ARG;
-    if (algo != GB_ALGO_AUTO && algo != GB_ALGO_SIMT && algo != GB_ALGO_SPLIT_BF16X6)
-        return GB_ERR_UNSUPPORTED;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
     if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
@@ -562,12 +593,15 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
         for (int c = 0; c < kClasses; ++c) choice[c] = h->grouped_choice[c];
     } else {
         // SIMT: 64x64 tiles for the three smallest classes, else 128x128;
-        // SPLIT_BF16X6: every problem with K >= 4 on the tensor cores
+        // a split algorithm: every problem with K >= 4 on the tensor cores
         for (int c = 0; c < kClasses; ++c)
             choice[c] = algo == GB_ALGO_SIMT ? (c < 3 ? 0 : 1) : 2;
     }
+    const int pref = algo == GB_ALGO_SPLIT_TF32X3 ? 0 : algo == GB_ALGO_SPLIT_BF16X3 ? 1
+                   : algo == GB_ALGO_SPLIT_BF16X6 ? 2 : algo == GB_ALGO_SPLIT_BF16X9 ? 3
+                   : kPrefAuto;
     gb_grouped_plan_s *pl = nullptr;
-    int rc = build_plan(h, dev, ps, choice, &pl);
+    int rc = build_plan(h, dev, ps, choice, pref, &pl);
     if (rc) return rc;
     *ws_bytes = 256;         // the SIMT work counter
     *plan = pl;

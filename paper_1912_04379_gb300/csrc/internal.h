@@ -73,7 +73,8 @@ cudaError_t launch_scaled_copy(int64_t m, int64_t n, float beta, const float *X,
 // writes each term as a row-major [rows][kpad] array (K contiguous).
 // kcontig: the stored matrix is K-contiguous (element (r,p) at X[p + r*ld]),
 // else rows-contiguous (element (r,p) at X[r + p*ld]).
-// mode: 0 = TF32 (4-byte words, 2 parts), 1 = BF16 2 parts, 2 = BF16 3 parts.
+// mode: 0 = TF32 (4-byte words, 2 parts), 1 = BF16 2 parts, 2 and 3 = BF16 3 parts
+// (the tensor-core kernel then forms 6 or all 9 products of the terms).
 cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k,
                               const float *X, int64_t ld, void *out, int64_t kpad,
                               int64_t part_stride_elems, cudaStream_t s);
@@ -164,9 +165,10 @@ struct PackItem {
     int64_t r0, p0;
     int kc;                     // source contiguous along K
     int vec;                    // 16-byte loads allowed
+    int mode;                   // as launch_split_pack
+    int pad_;
 };
-cudaError_t launch_split_pack_grouped(int mode, const PackItem *items, int64_t nitems,
-                                      cudaStream_t s);
+cudaError_t launch_split_pack_grouped(const PackItem *items, int64_t nitems, cudaStream_t s);
 
 // --------------------------------------------------------- error report --
 size_t err_report_ws(int64_t m, int64_t n);

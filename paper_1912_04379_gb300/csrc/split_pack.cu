@@ -145,15 +145,22 @@ split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
                       (int64_t)blockIdx.x * 64, T);
 }
 
-// Grouped pass: each CTA walks a list of 64 x 64 tiles of many operands.
-template <int MODE>
+// Grouped pass: each CTA walks a list of 64 x 64 tiles of many operands,
+// each tile with its own split mode (the branch is uniform over the CTA).
 __global__ void __launch_bounds__(256)
 split_pack_grouped_kernel(const PackItem *__restrict__ items, int64_t nitems) {
     __shared__ float T[64][65];
     for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
         const PackItem it = items[i];
-        pack_tile64<MODE>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
-                          it.ps, it.r0, it.p0, T);
+        if (it.mode == 0)
+            pack_tile64<0>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
+                           it.ps, it.r0, it.p0, T);
+        else if (it.mode == 1)
+            pack_tile64<1>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
+                           it.ps, it.r0, it.p0, T);
+        else
+            pack_tile64<2>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
+                           it.ps, it.r0, it.p0, T);
     }
 }
 
@@ -180,20 +187,14 @@ cudaError_t launch_mode(bool kc, int64_t rows, int64_t k, const float *X, int64_
 
 }  // namespace
 
-cudaError_t launch_split_pack_grouped(int mode, const PackItem *items, int64_t nitems,
-                                      cudaStream_t s) {
+cudaError_t launch_split_pack_grouped(const PackItem *items, int64_t nitems, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = (int)(nitems < 65536 ? nitems : 65536);
-    switch (mode) {
-        case 0: split_pack_grouped_kernel<0><<<grid, 256, 0, s>>>(items, nitems); break;
-        case 1: split_pack_grouped_kernel<1><<<grid, 256, 0, s>>>(items, nitems); break;
-        case 2: split_pack_grouped_kernel<2><<<grid, 256, 0, s>>>(items, nitems); break;
-        default: return cudaErrorInvalidValue;
-    }
+    split_pack_grouped_kernel<<<grid, 256, 0, s>>>(items, nitems);
     return cudaGetLastError();
 }
 
-int split_parts(int mode) { return mode == 2 ? 3 : 2; }
+int split_parts(int mode) { return mode >= 2 ? 3 : 2; }
 int split_elem_bytes(int mode) { return mode == 0 ? 4 : 2; }
 int64_t split_kpad(int mode, int64_t k) {
     // rows start on 16-byte boundaries: 4 TF32 words or 8 BF16 values
@@ -208,7 +209,8 @@ cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k, c
     switch (mode) {
         case 0: return launch_mode<0>(kcontig, rows, k, X, ld, out, kpad, ps, s);
         case 1: return launch_mode<1>(kcontig, rows, k, X, ld, out, kpad, ps, s);
-        case 2: return launch_mode<2>(kcontig, rows, k, X, ld, out, kpad, ps, s);
+        case 2:
+        case 3: return launch_mode<2>(kcontig, rows, k, X, ld, out, kpad, ps, s);   // same terms
         default: return cudaErrorInvalidValue;
     }
 }

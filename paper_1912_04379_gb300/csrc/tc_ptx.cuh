@@ -198,7 +198,12 @@ __device__ __forceinline__ void tmem_wait16(uint32_t r[16]) {
 // Term pair (A term, B term) for step q, smallest weight first.
 template <int MODE>
 __device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {
-    if (MODE == 2) {
+    if (MODE == 3) {
+        // all nine products, by weight: 2^-32, 2^-24 (x2), 2^-16 (x3), 2^-8 (x2), 1
+        const int a[9] = {2, 1, 2, 0, 1, 2, 0, 1, 0};
+        const int b[9] = {2, 2, 1, 2, 1, 0, 1, 0, 0};
+        sa = a[q]; sb = b[q];
+    } else if (MODE == 2) {
         const int a[6] = {0, 1, 2, 0, 1, 0};
         const int b[6] = {2, 1, 0, 1, 0, 0};
         sa = a[q]; sb = b[q];

@@ -52,9 +52,9 @@ template <int MODE, int RB>
 struct Cfg {
     static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
     static constexpr bool TF32 = MODE == 0;
-    static constexpr int PARTS = MODE == 2 ? 3 : 2;
-    static constexpr int NPAIRS = MODE == 2 ? 6 : 3;
-    static constexpr int BN = MODE == 2 ? 128 : 256;
+    static constexpr int PARTS = MODE >= 2 ? 3 : 2;
+    static constexpr int NPAIRS = MODE == 3 ? 9 : MODE == 2 ? 6 : 3;
+    static constexpr int BN = MODE >= 2 ? 128 : 256;
     static constexpr int ELEM = TF32 ? 4 : 2;
     static constexpr int BK = ROW_BYTES / ELEM;          // elements per k-block
     static constexpr int KSTEP_BYTES = 32;               // K per MMA: 16 BF16 / 8 TF32
@@ -410,7 +410,7 @@ cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part,
     return cudaGetLastError();
 }
 
-int tc_tile_n(int mode) { return mode == 2 ? 128 : 256; }
+int tc_tile_n(int mode) { return mode >= 2 ? 128 : 256; }
 
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
                          int64_t rows, bool a_side) {
@@ -432,6 +432,8 @@ cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, cons
                              : launch_grouped_mode<1, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
         case 2: return rb128 ? launch_grouped_mode<2, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
                              : launch_grouped_mode<2, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 3: return rb128 ? launch_grouped_mode<3, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
+                             : launch_grouped_mode<3, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -452,6 +454,7 @@ cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
         case 0: return rb128 ? launch_mode<0, 128>(a, s) : launch_mode<0, 64>(a, s);
         case 1: return rb128 ? launch_mode<1, 128>(a, s) : launch_mode<1, 64>(a, s);
         case 2: return rb128 ? launch_mode<2, 128>(a, s) : launch_mode<2, 64>(a, s);
+        case 3: return rb128 ? launch_mode<3, 128>(a, s) : launch_mode<3, 64>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -115,3 +115,53 @@ def test_grouped_edge_cases():
     empty = gb.GroupedPlan([])
     assert empty.run() == 0
     empty.close()
+
+
+# K values on both sides of every split's threshold (16 for TF32 x 2 terms,
+# 1024 for BF16 x 2 terms, 4 for BF16 x 3 terms with 6 products).
+MIXED_K = (1, 3, 4, 9, 15, 16, 40, 300, 1023, 1024, 1500, 2100)
+
+
+@pytest.mark.parametrize("algo", ("auto", "tf32x3", "bf16x3", "bf16x6", "bf16x9"))
+def test_grouped_per_problem_split_meets_fp32_bound(algo):
+    """The plan picks a split per problem by K: each problem's result meets the
+    plain FP32 bound, whichever split was preferred (a problem below the
+    preferred split's threshold takes BF16 x 3 terms, K < 4 the CUDA cores)."""
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    rng = np.random.default_rng(31)
+    probs = []
+    for i, k in enumerate(MIXED_K * 2):
+        m, n = int(rng.integers(60, 300)), int(rng.integers(60, 300))
+        ta, tb = "NT"[i % 2], "NT"[(i // 2) % 2]
+        probs.append(wl.make_problem(ta, tb, m, n, k, float(rng.uniform(-2, 2)),
+                                     float(rng.uniform(-2, 2)), rng=rng,
+                                     dist="logu" if i % 3 == 0 else "uniform"))
+    buf, tuples, views = gb.upload_problems(probs)
+    plan = gb.GroupedPlan(tuples, algo=algo)
+    plan.run()
+    torch.cuda.synchronize()
+    assert gb.default_handle().device_error() == (0, 0)
+    for i, p in enumerate(probs):
+        _check_problem(p, views[i].cpu().numpy(), algo="simt")
+    plan.close()
+
+
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x9"))
+def test_grouped_split_integer_bit_exact(algo):
+    """Integer data: every split and the mixed-mode plan are exact."""
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    rng = np.random.default_rng(32)
+    probs = [wl.make_problem("NT"[i % 2], "TN"[i % 2], 100 + 13 * i, 90 + 7 * i, k, 1.0, 0.5,
+                             rng=rng, dist="int") for i, k in enumerate((5, 20, 1100, 2048))]
+    buf, tuples, views = gb.upload_problems(probs)
+    plan = gb.GroupedPlan(tuples, algo=algo)
+    plan.run()
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        C64, _ = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb,
+                              p.beta, p.C, p.ldc)
+        got = views[i].cpu().numpy()[:p.m, :]
+        assert np.array_equal(got, C64.astype(np.float32)), (algo, p.k)
+    plan.close()

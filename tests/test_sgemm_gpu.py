@@ -12,7 +12,7 @@ from _gpu import ALGOS, assert_bit_exact, assert_within_bound, check_padding, ru
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
-SPLIT = ("tf32x3", "bf16x3", "bf16x6")
+SPLIT = ("tf32x3", "bf16x3", "bf16x6", "bf16x9")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -108,7 +108,7 @@ def test_persistent_many_tiles():
 # ------------------------------------------------ log-uniform magnitudes --
 
 @pytest.mark.parametrize("k", (8, 64, 1000))
-@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x6"))
+@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x6", "bf16x9"))
 def test_log_uniform_small(algo, k):
     p = wl.make_problem("N", "N", 200, 150, k, 1.0, 0.0, seed=23, dist="logu")
     rc, got = run(p, algo)
@@ -193,7 +193,7 @@ def test_device_error_word_clean():
 
 
 @pytest.mark.parametrize("ta,tb", TRANS)
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", SPLIT)
 def test_long_k_ragged(algo, ta, tb):
     """K > 2048 selects the four-stage, 64-byte-row pipeline; ragged M, N, K."""
     p = wl.make_problem(ta, tb, 300, 270, 2500, 1.0, -0.5, seed=26, ld_pad=3)
@@ -202,7 +202,7 @@ def test_long_k_ragged(algo, ta, tb):
     check_padding(p, got)
 
 
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", SPLIT)
 def test_long_k_integer_bit_exact(algo):
     p = wl.make_problem("T", "N", 140, 260, 4100, 1.0, 0.5, seed=27, dist="int", ld_pad=1)
     rc, got = run(p, algo)
@@ -211,7 +211,7 @@ def test_long_k_integer_bit_exact(algo):
 
 # ------------------------------------------------------------- split-K ----
 
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", SPLIT)
 def test_split_k_small_full_check(algo):
     """Few output tiles and a long K: the K range is cut into slices whose
     partial sums are reduced in a fixed order (beta != 0 goes through the reduce)."""
@@ -221,7 +221,7 @@ def test_split_k_small_full_check(algo):
     check_padding(p, got)
 
 
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", SPLIT)
 def test_split_k_integer_bit_exact(algo):
     p = wl.make_problem("T", "T", 100, 100, 5000, 1.0, 0.5, seed=29, dist="int", ld_pad=1)
     rc, got = run(p, algo)
@@ -248,7 +248,7 @@ def _split_problem(shape):
     return _SPLIT_CACHE[shape]
 
 
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", SPLIT)
 @pytest.mark.parametrize("shape", wl.SPLIT_SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_split_shapes_full_size_sampled(shape, algo):
     p = _split_problem(shape)
@@ -257,3 +257,25 @@ def test_split_shapes_full_size_sampled(shape, algo):
     n = p.n
     cols = np.unique(np.r_[0, n - 1, np.random.default_rng(n + p.k).integers(0, n, 6)])
     assert_within_bound(p, got, cols=cols, algo=algo)
+
+
+# ------------------------------------------------- all nine products ----
+
+@pytest.mark.parametrize("k", (1, 2, 3, 5))
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_bf16x9_tiny_k(k, ta, tb):
+    """All nine products: every a*b is formed exactly, so only the tensor
+    core's FP32 accumulation (not round-to-nearest) adds to the plain bound."""
+    p = wl.make_problem(ta, tb, 150, 140, k, 1.0, -0.75, seed=40 + k, dist="logu", ld_pad=2)
+    rc, got = run(p, "bf16x9")
+    assert_within_bound(p, got, algo="bf16x9")
+    check_padding(p, got)
+
+
+def test_bf16x9_split_k():
+    """BF16X9 on a split-K shape (64 x 2000 x 6000, beta != 0): plain bound."""
+    p = wl.make_problem("N", "T", 64, 2000, 6000, 0.5, 0.5, seed=45, ld_pad=1)
+    rc, got = run(p, "bf16x9")
+    cols = np.unique(np.r_[0, 1, 999, 1999, np.random.default_rng(45).integers(0, 2000, 8)])
+    assert_within_bound(p, got, cols=cols)
+    check_padding(p, got)
