@@ -58,6 +58,8 @@ def parse():
                     help="skip the grouped 2000-problem comparison")
     ap.add_argument("--no-shapes", action="store_true",
                     help="skip the per-shape table (K = 1024, 16384 and the skinny shapes)")
+    ap.add_argument("--no-mlp", action="store_true",
+                    help="skip the training-step measurement of the fully connected network")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--clocks-log", default=None)
@@ -330,6 +332,59 @@ def bench_grouped(gb, h, dev, stream, reps=10):
     return out
 
 
+MLP_WIDTHS = (1024, 4096, 4096, 1024)
+MLP_BATCH = 4096
+
+
+def bench_mlp(gb, h, dev, stream, steps=20):
+    """One training step (forward, loss, backward, gradient-descent update) of
+    a fully connected tanh network, widths 1024-4096-4096-1024, batch 4096
+    (25 M parameters), W ~ N(0, 1/n_in), X, Y ~ N(0, 1) (seed 5), through
+    gb_mlp_train_step with AUTO (BF16 x 2 terms for every GEMM, K >= 1024).
+    Throughput counts the GEMM flops of the step (2 n_l n_{l-1} B per GEMM)."""
+    import torch
+    widths, B = MLP_WIDTHS, MLP_BATCH
+    g = torch.Generator(device=dev).manual_seed(5)
+    net = gb.MLP(widths, B, hidden="tanh", algo="auto", handle=h)
+    for l, W in enumerate(net.W):
+        W.copy_(torch.randn(W.shape, device=dev, generator=g) / widths[l] ** 0.5)
+    X = gb.colmajor(widths[0], B, device=dev)
+    X.copy_(torch.randn(X.shape, device=dev, generator=g))
+    Y = gb.colmajor(widths[-1], B, device=dev)
+    Y.copy_(torch.randn(Y.shape, device=dev, generator=g))
+    L = len(widths) - 1
+    per = [2.0 * widths[l] * widths[l + 1] * B for l in range(L)]
+    flops = 2 * sum(per) + sum(per[1:])          # forward + updates, + G_{l-1} for l > 1
+    fwd_flops = sum(per)
+    lr = 1e-3
+    first = float(net.train_step(X, Y, lr, stream=stream).item())
+    for _ in range(3):
+        net.train_step(X, Y, lr, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        net.train_step(X, Y, lr, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    last = float(net.loss.item())
+    e0.record(stream)
+    for _ in range(steps):
+        net.forward(X, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / steps
+    return {"workload": "fully connected tanh network 1024-4096-4096-1024, batch 4096, "
+                        "MSE loss, gradient descent (seed 5)",
+            "algo": "auto", "params": sum(widths[l] * widths[l + 1] + widths[l + 1]
+                                          for l in range(L)),
+            "train_step_ms": ms, "train_step_tflops": flops / (ms * 1e-3) / 1e12,
+            "forward_ms": fwd_ms, "forward_tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
+            "gemm_gflop_per_step": flops / 1e9, "steps": steps,
+            "loss_first": first, "loss_after": last}
+
+
 def bench_shapes(gb, h, dev, stream, reps=10):
     """gb_sgemm on the split-precision shapes (M=N=8192 with K = 1024, 16384;
     skinny 8192x8192x64 and 64x8192x8192) per algorithm: TFLOP/s and, for the
@@ -509,6 +564,7 @@ def run_ours(args, rank, world, local_rank):
 
     grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
     shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
+    mlp = None if args.no_mlp else bench_mlp(gb, h, dev, stream)
 
     peaks, peak_kind = load_peaks()
     tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
@@ -528,7 +584,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
-            "arms": arms, "grouped": grouped, "shapes": shapes, "clocks": clocks,
+            "arms": arms, "grouped": grouped, "shapes": shapes, "mlp": mlp, "clocks": clocks,
             "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

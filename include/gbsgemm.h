@@ -310,6 +310,56 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
  * (9.2 ms against 1.9 ms at M = N = K = 8192). */
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 
+/* ---------------------------------------------------------------------
+ * Training step of a fully connected network on the SGEMM (the paper's
+ * application, Sec. 4: the SGEMM as the kernel of neural-network training).
+ *
+ * Layers l = 1..L with widths n_0..n_L; examples are columns. All matrices
+ * are column-major FP32 device arrays with leading dimension = rows:
+ *   X  n_0 x B (input),  Y  n_L x B (target),
+ *   W[l-1]  n_l x n_{l-1},  b[l-1]  n_l,  H[l-1], G[l-1]  n_l x B.
+ * W, b, H and G are HOST arrays of L device pointers. The network:
+ *   H_l = phi_l(W_l H_{l-1} + b_l 1^T),  H_0 = X,
+ *   phi_l = `hidden` for l < L, identity for l = L;
+ *   loss E = sum_ij (H_L - Y)_ij^2 / (2B).
+ * No two of these buffers may overlap.
+ * Every GEMM runs through gb_sgemm with `algo` (its error bound applies per
+ * GEMM); the elementwise passes and the fixed-order reductions run in the
+ * library's own kernels. On an error nothing more is enqueued; work already
+ * enqueued is not undone. The calls are asynchronous on `stream`; the
+ * workspace must be 256-byte aligned and at least gb_mlp_workspace_size.
+ * ------------------------------------------------------------------- */
+typedef enum { GB_ACT_IDENTITY = 0, GB_ACT_TANH = 1 } gb_activation_t;
+
+typedef struct {
+    int64_t layers;            /* L >= 1 */
+    const int64_t *widths;     /* host array n_0 .. n_L, each >= 1 */
+    int64_t batch;             /* B >= 1 */
+    gb_activation_t hidden;    /* activation of layers 1 .. L-1 */
+} gb_mlp_desc_t;
+
+/* Workspace bytes of gb_mlp_forward (train = 0) or gb_mlp_train_step
+ * (train != 0). GB_ERR_ARG for an invalid description or algo. */
+GB_API int gb_mlp_workspace_size(gb_algo_t algo, const gb_mlp_desc_t *desc, int train,
+                                 size_t *bytes);
+
+/* Forward pass: writes H_1 .. H_L. */
+GB_API int gb_mlp_forward(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t *desc,
+                          const float *const *W, const float *const *b, const float *X,
+                          float *const *H, void *workspace, size_t ws_bytes, void *stream);
+
+/* One step of gradient descent with learning rate lr: the forward pass
+ * (H_1 .. H_L), the loss E into *loss (one float, device), the backward
+ * pass G_l = dE/dZ_l with Z_l = W_l H_{l-1} + b_l 1^T:
+ *   G_L = (H_L - Y) / B,  G_l = (W_{l+1}^T G_{l+1}) * phi'(Z_l)
+ * (tanh' = 1 - H_l^2, formed with the weights before the update), and the
+ * update W_l <- W_l - lr G_l H_{l-1}^T (one SGEMM with alpha = -lr and
+ * beta = 1 on W_l), b_l <- b_l - lr G_l 1 (row sums in a fixed order). */
+GB_API int gb_mlp_train_step(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t *desc,
+                             float *const *W, float *const *b, const float *X, const float *Y,
+                             float lr, float *const *H, float *const *G, float *loss,
+                             void *workspace, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,7 +10,8 @@ the library is missing.
 from .api import (GroupedPlan, Handle, backward_raw, colmajor, compute_raw, default_handle,
                   err_report, from_fortran, pack_raw, pack_size, sgemm, sgemm_raw, to_fortran,
                   upload_problems, workspace_size)
+from .mlp import MLP
 
-__all__ = ["GroupedPlan", "Handle", "backward_raw", "colmajor", "compute_raw", "default_handle",
+__all__ = ["MLP", "GroupedPlan", "Handle", "backward_raw", "colmajor", "compute_raw", "default_handle",
            "err_report", "from_fortran", "pack_raw", "pack_size", "sgemm", "sgemm_raw",
            "to_fortran", "upload_problems", "workspace_size"]

@@ -45,6 +45,13 @@ class GemmProblem(ctypes.Structure):
                 ("ldb", c_i64), ("C", c_vp), ("ldc", c_i64)]
 
 
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("layers", c_i64), ("widths", ctypes.POINTER(c_i64)), ("batch", c_i64),
+                ("hidden", c_int)]
+
+
+ACTIVATIONS = {"identity": 0, "tanh": 1}
+
 SIGNATURES = {
     "gb_version": ([], c_int),
     "gb_status_string": ([c_int], ctypes.c_char_p),
@@ -77,6 +84,14 @@ SIGNATURES = {
     "gb_get_device_error": ([c_vp, c_vp, ctypes.POINTER(c_int)], c_int),
     "gb_set_wait_limit": ([c_vp, c_i64], c_int),
     "gb_set_fused_split": ([c_vp, c_int], c_int),
+    "gb_mlp_workspace_size": ([c_int, ctypes.POINTER(MlpDesc), c_int, ctypes.POINTER(c_size)],
+                              c_int),
+    "gb_mlp_forward": ([c_vp, c_int, ctypes.POINTER(MlpDesc), ctypes.POINTER(c_vp),
+                        ctypes.POINTER(c_vp), c_vp, ctypes.POINTER(c_vp), c_vp, c_size, c_vp],
+                       c_int),
+    "gb_mlp_train_step": ([c_vp, c_int, ctypes.POINTER(MlpDesc), ctypes.POINTER(c_vp),
+                           ctypes.POINTER(c_vp), c_vp, c_vp, c_f, ctypes.POINTER(c_vp),
+                           ctypes.POINTER(c_vp), c_vp, c_vp, c_size, c_vp], c_int),
 }
 
 
