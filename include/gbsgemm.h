@@ -123,7 +123,8 @@ GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char transa, char transb,
 /* C <- alpha*op(A)*op(B) + beta*C (paper Sec. 1; Level-3 BLAS SGEMM).
  * Requirements: lda >= max(1, rows of stored A) (M if transa is 'N', else K),
  * ldb >= max(1, rows of stored B) (K if transb is 'N', else N),
- * ldc >= max(1, M). C must not overlap A or B. The split algorithms need
+ * ldc >= max(1, M). C must share no element with A or B (disjoint blocks of
+ * one array are allowed). The split algorithms need
  * `workspace` of at least gb_sgemm_workspace_size() bytes, 256-byte aligned
  * (GB_ERR_WORKSPACE otherwise); SIMT ignores it. Enqueues on `stream` and
  * returns without waiting. A bounded-wait timeout inside a tensor-core
@@ -359,6 +360,48 @@ GB_API int gb_mlp_train_step(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t 
                              float *const *W, float *const *b, const float *X, const float *Y,
                              float lr, float *const *H, float *const *G, float *loss,
                              void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
+ * SSYRK and STRSM on the SGEMM core (Level-3 BLAS, whose routines are
+ * written over GEMM; the paper's SGEMM implements the Level-3 BLAS SGEMM
+ * interface, Sec. 1). Both recurse by halving: each level's off-diagonal
+ * block is one gb_sgemm call with `algo` (so its error bound applies per
+ * GEMM), down to diagonal blocks of at most 128 rows handled by the
+ * library's own kernels. Asynchronous on `stream`; the workspace (256-byte
+ * aligned) must hold gb_*_workspace_size bytes (0 means none is needed).
+ * ------------------------------------------------------------------- */
+
+/* Workspace bytes of gb_ssyrk with these arguments. */
+GB_API int gb_ssyrk_workspace_size(gb_algo_t algo, char uplo, char trans, int64_t n, int64_t k,
+                                   size_t *bytes);
+
+/* C <- alpha*op(A)*op(A)^T + beta*C on the `uplo` ('U' or 'L') triangle of
+ * the n x n matrix C; the other triangle is neither read nor written.
+ * op(A) = A (n x k, lda >= max(1, n)) for trans 'N', A^T (A k x n,
+ * lda >= max(1, k)) for 'T' or 'C'; ldc >= max(1, n). C is not read when
+ * beta = 0; A is not read when alpha = 0 or k = 0. Negative returns are
+ * BLAS argument positions (1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc). The
+ * diagonal blocks are computed in FP32 on the CUDA cores whatever `algo`. */
+GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_t n, int64_t k,
+                    float alpha, const float *A, int64_t lda, float beta, float *C, int64_t ldc,
+                    void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace bytes of gb_strsm with these arguments. */
+GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char transa, char diag,
+                                   int64_t m, int64_t n, size_t *bytes);
+
+/* Solves op(A) X = alpha B (side 'L', A m x m) or X op(A) = alpha B (side
+ * 'R', A n x n) for X (m x n), which overwrites B. A is triangular: only
+ * its `uplo` triangle is read, and with diag 'U' its diagonal is taken as 1
+ * and not read. lda >= max(1, m or n), ldb >= max(1, m). B is scaled by
+ * alpha first; alpha = 0 sets B to 0 without reading A or B. A singular A
+ * gives infinities or NaNs, as in BLAS. Negative returns are BLAS argument
+ * positions (1 side, 2 uplo, 3 transa, 4 diag, 5 m, 6 n, 9 lda, 11 ldb).
+ * The diagonal blocks are solved by substitution in FP32; the updates
+ * between them are gb_sgemm calls (alpha = -1, beta = 1). */
+GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
+                    int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
+                    int64_t ldb, void *workspace, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -149,6 +149,41 @@ def sgemm_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, C_pt
     return rc
 
 
+def ssyrk_raw(uplo, trans, n, k, alpha, A_ptr, lda, beta, C_ptr, ldc, algo="auto",
+              handle=None, stream=None, check=True) -> int:
+    """gb_ssyrk on device pointers: C <- alpha op(A) op(A)^T + beta C on the
+    `uplo` triangle. Returns the status."""
+    h = handle or default_handle()
+    need = ctypes.c_size_t(0)
+    rc = h.lib.gb_ssyrk_workspace_size(_lib.ALGOS[algo], uplo.encode(), trans.encode(), n, k,
+                                       ctypes.byref(need))
+    ws = h.workspace(need.value) if rc == 0 else None
+    rc = h.lib.gb_ssyrk(h.h, _lib.ALGOS[algo], uplo.encode(), trans.encode(), n, k, float(alpha),
+                        A_ptr, lda, float(beta), C_ptr, ldc, ws.data_ptr() if ws is not None else 0,
+                        ws.numel() if ws is not None else 0, _stream_ptr(stream))
+    if check:
+        _lib.check("gb_ssyrk", rc)
+    return rc
+
+
+def strsm_raw(side, uplo, transa, diag, m, n, alpha, A_ptr, lda, B_ptr, ldb, algo="auto",
+              handle=None, stream=None, check=True) -> int:
+    """gb_strsm on device pointers: B <- X with op(A) X = alpha B (side 'L') or
+    X op(A) = alpha B (side 'R'). Returns the status."""
+    h = handle or default_handle()
+    need = ctypes.c_size_t(0)
+    rc = h.lib.gb_strsm_workspace_size(_lib.ALGOS[algo], side.encode(), uplo.encode(),
+                                       transa.encode(), diag.encode(), m, n, ctypes.byref(need))
+    ws = h.workspace(need.value) if rc == 0 else None
+    rc = h.lib.gb_strsm(h.h, _lib.ALGOS[algo], side.encode(), uplo.encode(), transa.encode(),
+                        diag.encode(), m, n, float(alpha), A_ptr, lda, B_ptr, ldb,
+                        ws.data_ptr() if ws is not None else 0,
+                        ws.numel() if ws is not None else 0, _stream_ptr(stream))
+    if check:
+        _lib.check("gb_strsm", rc)
+    return rc
+
+
 def pack_size(algo, which, mn, k) -> int:
     lib = _lib.load()
     out = ctypes.c_size_t(0)
