@@ -60,6 +60,8 @@ def parse():
                     help="skip the per-shape table (K = 1024, 16384 and the skinny shapes)")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the training-step measurement of the fully connected network")
+    ap.add_argument("--no-blas3", action="store_true",
+                    help="skip the SSYRK / STRSM measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--clocks-log", default=None)
@@ -385,6 +387,53 @@ def bench_mlp(gb, h, dev, stream, steps=20):
             "loss_first": first, "loss_after": last}
 
 
+def bench_blas3(gb, h, dev, stream, reps=5):
+    """SSYRK ('L', 'N', n = k = 8192, alpha = 1, beta = 0) and STRSM (every
+    side/uplo/trans with diag 'N', m = n = 8192, alpha = 1) with AUTO, on
+    uniform inputs (seed 6); STRSM's A has off-diagonal entries U(-1,1)/8192
+    and |diagonal| in [1, 2], so X stays bounded. Useful flops: n^2 k (SSYRK,
+    the triangle's n(n+1)k rounded) and m^2 n (STRSM)."""
+    import torch
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(6)
+    A = gb.colmajor(n, n, device=dev)
+    A.copy_(torch.rand((n, n), device=dev, generator=g) * 2 - 1)
+    C = gb.colmajor(n, n, device=dev, fill=0.0)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    ms = timed(lambda: gb.ssyrk_raw("L", "N", n, n, 1.0, A.data_ptr(), n, 0.0, C.data_ptr(), n,
+                                    handle=h, stream=stream))
+    out["ssyrk_L_N_8192x8192"] = {"ms": ms, "tflops": float(n) * n * n / (ms * 1e-3) / 1e12}
+    T = gb.colmajor(n, n, device=dev)
+    T.copy_(A / n)
+    d = torch.rand(n, device=dev, generator=g) + 1.0
+    T.diagonal().copy_(torch.where(torch.rand(n, device=dev, generator=g) < 0.5, -d, d))
+    B0 = gb.colmajor(n, n, device=dev)
+    B0.copy_(torch.rand((n, n), device=dev, generator=g) * 2 - 1)
+    B = gb.colmajor(n, n, device=dev)
+    for side, uplo, trans in (("L", "L", "N"), ("L", "U", "T"), ("R", "U", "N"), ("R", "L", "T")):
+        def f():
+            B.copy_(B0)
+            gb.strsm_raw(side, uplo, trans, "N", n, n, 1.0, T.data_ptr(), n, B.data_ptr(), n,
+                         handle=h, stream=stream)
+        cp = timed(lambda: B.copy_(B0))
+        ms = timed(f) - cp
+        out[f"strsm_{side}_{uplo}_{trans}_8192x8192"] = {
+            "ms": ms, "tflops": float(n) * n * n / (ms * 1e-3) / 1e12}
+    return out
+
+
 def bench_shapes(gb, h, dev, stream, reps=10):
     """gb_sgemm on the split-precision shapes (M=N=8192 with K = 1024, 16384;
     skinny 8192x8192x64 and 64x8192x8192) per algorithm: TFLOP/s and, for the
@@ -565,6 +614,7 @@ def run_ours(args, rank, world, local_rank):
     grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
     shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
     mlp = None if args.no_mlp else bench_mlp(gb, h, dev, stream)
+    blas3 = None if args.no_blas3 else bench_blas3(gb, h, dev, stream)
 
     peaks, peak_kind = load_peaks()
     tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
@@ -584,7 +634,8 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
-            "arms": arms, "grouped": grouped, "shapes": shapes, "mlp": mlp, "clocks": clocks,
+            "arms": arms, "grouped": grouped, "shapes": shapes, "mlp": mlp, "blas3": blas3,
+            "clocks": clocks,
             "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -364,10 +364,7 @@ GB_API int gb_mlp_train_step(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t 
 /* ---------------------------------------------------------------------
  * SSYRK and STRSM on the SGEMM core (Level-3 BLAS, whose routines are
  * written over GEMM; the paper's SGEMM implements the Level-3 BLAS SGEMM
- * interface, Sec. 1). Both recurse by halving: each level's off-diagonal
- * block is one gb_sgemm call with `algo` (so its error bound applies per
- * GEMM), down to diagonal blocks of at most 128 rows handled by the
- * library's own kernels. Asynchronous on `stream`; the workspace (256-byte
+ * interface, Sec. 1). Asynchronous on `stream`; the workspace (256-byte
  * aligned) must hold gb_*_workspace_size bytes (0 means none is needed).
  * ------------------------------------------------------------------- */
 
@@ -380,8 +377,13 @@ GB_API int gb_ssyrk_workspace_size(gb_algo_t algo, char uplo, char trans, int64_
  * op(A) = A (n x k, lda >= max(1, n)) for trans 'N', A^T (A k x n,
  * lda >= max(1, k)) for 'T' or 'C'; ldc >= max(1, n). C is not read when
  * beta = 0; A is not read when alpha = 0 or k = 0. Negative returns are
- * BLAS argument positions (1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc). The
- * diagonal blocks are computed in FP32 on the CUDA cores whatever `algo`. */
+ * BLAS argument positions (1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc).
+ * With a split algorithm (AUTO: K >= 4) op(A) is split and packed once into
+ * the workspace and the whole triangle runs in one tensor-core launch (the
+ * algorithm's error bound per element, as for gb_sgemm). With SIMT, or when
+ * alpha = 0 or K = 0, it recurses by halving: each level's off-diagonal
+ * block is one gb_sgemm call and the diagonal blocks (at most 128 rows) run
+ * in FP32 on the CUDA cores. */
 GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_t n, int64_t k,
                     float alpha, const float *A, int64_t lda, float beta, float *C, int64_t ldc,
                     void *workspace, size_t ws_bytes, void *stream);
@@ -397,8 +399,10 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
  * alpha first; alpha = 0 sets B to 0 without reading A or B. A singular A
  * gives infinities or NaNs, as in BLAS. Negative returns are BLAS argument
  * positions (1 side, 2 uplo, 3 transa, 4 diag, 5 m, 6 n, 9 lda, 11 ldb).
- * The diagonal blocks are solved by substitution in FP32; the updates
- * between them are gb_sgemm calls (alpha = -1, beta = 1). */
+ * Recursion by halving: each level's off-diagonal block update is one
+ * gb_sgemm call with `algo` (alpha = -1, beta = 1), and the diagonal blocks
+ * (at most 128 rows) are solved by substitution in FP32, with each diagonal
+ * entry's reciprocal rounded once per block. */
 GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
                     int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
                     int64_t ldb, void *workspace, size_t ws_bytes, void *stream);

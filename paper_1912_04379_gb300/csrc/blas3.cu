@@ -2,17 +2,20 @@
 // written over GEMM; the paper's SGEMM implements the Level-3 BLAS SGEMM
 // interface, Sec. 1).
 //
-// Both recurse by halving: the off-diagonal half-size block of each level is
-// one gb_sgemm call (so almost all flops run through the tensor-core or SIMT
-// GEMM), down to diagonal leaves of at most 128 rows.
+// SSYRK with a split algorithm runs on the tensor cores in one launch over the
+// triangle's tiles (tc_syrk.cu). Otherwise (SIMT, or alpha = 0 / k = 0) and
+// for STRSM, the operation recurses by halving: the off-diagonal half-size
+// block of each level is one gb_sgemm call, down to diagonal leaves of at
+// most 128 rows.
 //   SSYRK  leaves: every diagonal block's triangle in ONE launch of a small
 //          FP32 SIMT kernel (64 x 64 tiles, the tiles above or below the
 //          diagonal skipped).
 //   STRSM  leaves: forward/backward substitution in one kernel per leaf, the
-//          leaf's op(A) block in shared memory; left side: one warp per
-//          column of B (lanes over rows), right side: one warp per row of B
-//          (lanes over columns). Leaves depend on one another through the
-//          GEMM updates, so they run in order.
+//          leaf's op(A) block in shared memory; left side: each warp solves
+//          four columns of B at once (lanes over rows), right side: four rows
+//          (lanes over columns, the rows staged through shared memory).
+//          Leaves depend on one another through the GEMM updates, so they
+//          run in order.
 // X overwrites B in STRSM after B <- alpha B. Each GEMM update is
 // B_rest <- B_rest - op(A)_block * X_done (alpha = -1, beta = 1); operand
 // and output blocks are disjoint parts of the same arrays.
@@ -98,50 +101,99 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 
 // ------------------------------------------------------------- STRSM leaves
 
-// op(A)[r0 + i, r0 + j] of the stored triangle (0 outside it, 1 on a unit
-// diagonal); `tlower`: op(A) is lower triangular.
-__device__ __forceinline__ float tri_elem(const float *A, int64_t lda, int64_t r0, int i, int j,
-                                          int trans, int tlower, int unit) {
-    if (tlower ? i < j : i > j) return 0.f;
-    if (i == j && unit) return 1.f;
-    return trans ? A[(r0 + j) + (r0 + i) * lda] : A[(r0 + i) + (r0 + j) * lda];
+constexpr int kLeafCols = 4;     // columns (left) or rows (right) per warp
+constexpr int kRightRows = 8 * kLeafCols;   // rows of B per CTA, right side
+
+// Loads op(A)'s s x s leaf block at (r0, r0) into shared memory: T[j*s + i]
+// (COLMAJOR) or T[i*s + j], 0 outside the triangle, 1 on a unit diagonal
+// (not read), and the reciprocals of the diagonal into D[0 .. s). Each warp
+// takes stored columns w, w + 8, ... of the leaf, four at a time, with its
+// lanes over stored rows (coalesced; sixteen independent loads per lane in
+// flight).
+template <bool COLMAJOR>
+__device__ __forceinline__ void load_leaf(float *T, float *D, int s, const float *__restrict__ A,
+                                          int64_t lda, int64_t r0, int trans, int tlower,
+                                          int unit) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = warp; b0 < s; b0 += 32) {
+        float v[4][4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int bcol = b0 + 8 * g;
+            const float *src = A + r0 + (r0 + bcol) * lda;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int a = lane + 32 * r;             // stored row
+                const int i = trans ? bcol : a, j = trans ? a : bcol;
+                const bool inside = bcol < s && a < s && (tlower ? i >= j : i <= j) &&
+                                    !(unit && i == j);
+                v[g][r] = inside ? src[a] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int bcol = b0 + 8 * g;
+            if (bcol >= s) break;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int a = lane + 32 * r;
+                if (a >= s) break;
+                const int i = trans ? bcol : a, j = trans ? a : bcol;
+                const float x = (unit && i == j) ? 1.f : v[g][r];
+                T[COLMAJOR ? j * s + i : i * s + j] = x;
+                if (i == j) D[i] = unit ? 1.f : 1.f / x;
+            }
+        }
+    }
 }
 
-// op(A)_leaf X = B_leaf for the s rows r0 .. r0+s of B: warp per column.
-// T is stored column by column (T[j*s + i]) so that the lanes of one step
-// read consecutive words.
+// op(A)_leaf X = B_leaf for the s <= 128 rows r0 .. r0+s of B. Each warp
+// solves kLeafCols columns at once (independent chains for ILP); lanes hold
+// rows lane + 32r. Column-oriented substitution: x_j = b_j * (1 / t_jj), then
+// b_i -= t_ij x_j for the rows still to solve, j in dependency order. (The
+// reciprocal, rounded once per leaf, perturbs t_jj by at most one rounding,
+// as in the reference BLAS's right-side STRSM; a division per step and
+// column made the leaf instruction-bound.)
 __global__ void __launch_bounds__(256)
 trsm_left_leaf_kernel(int s, int64_t n, const float *__restrict__ A, int64_t lda, int64_t r0,
                       int trans, int tlower, int unit, float *__restrict__ B, int64_t ldb) {
     extern __shared__ float T[];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, j = e / s;
-        T[e] = tri_elem(A, lda, r0, i, j, trans, tlower, unit);
-    }
+    float *D = T + s * s;
+    load_leaf<true>(T, D, s, A, lda, r0, trans, tlower, unit);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t col = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (col >= n) return;
-    float *bcol = B + r0 + col * ldb;
-    float b[4];
+    const int64_t col0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * kLeafCols;
+    if (col0 >= n) return;
+    float b[kLeafCols][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = lane + 32 * r;
-        b[r] = i < s ? bcol[i] : 0.f;
-    }
+    for (int q = 0; q < kLeafCols; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = lane + 32 * r;
+            b[q][r] = (col0 + q < n && i < s) ? B[r0 + i + (col0 + q) * ldb] : 0.f;
+        }
     if (tlower) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             for (int jj = 0; jj < 32; ++jj) {
                 const int j = 32 * r + jj;
                 if (j >= s) break;
-                const float bj = __shfl_sync(0xffffffffu, b[r], jj);
-                const float x = unit ? bj : bj / T[j * s + j];
-                if (lane == jj) b[r] = x;
+                const float d = D[j];
+                float x[kLeafCols];
+#pragma unroll
+                for (int q = 0; q < kLeafCols; ++q) {
+                    const float bj = __shfl_sync(0xffffffffu, b[q][r], jj);
+                    x[q] = bj * d;
+                    if (lane == jj) b[q][r] = x[q];
+                }
 #pragma unroll
                 for (int rr = r; rr < 4; ++rr) {
                     const int i = lane + 32 * rr;
-                    if (i > j && i < s) b[rr] = fmaf(-T[j * s + i], x, b[rr]);
+                    if (i > j && i < s) {
+                        const float t = T[j * s + i];
+#pragma unroll
+                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-t, x[q], b[q][rr]);
+                    }
                 }
             }
         }
@@ -151,58 +203,85 @@ trsm_left_leaf_kernel(int s, int64_t n, const float *__restrict__ A, int64_t lda
             for (int jj = 31; jj >= 0; --jj) {
                 const int j = 32 * r + jj;
                 if (j >= s) continue;
-                const float bj = __shfl_sync(0xffffffffu, b[r], jj);
-                const float x = unit ? bj : bj / T[j * s + j];
-                if (lane == jj) b[r] = x;
+                const float d = D[j];
+                float x[kLeafCols];
+#pragma unroll
+                for (int q = 0; q < kLeafCols; ++q) {
+                    const float bj = __shfl_sync(0xffffffffu, b[q][r], jj);
+                    x[q] = bj * d;
+                    if (lane == jj) b[q][r] = x[q];
+                }
 #pragma unroll
                 for (int rr = 0; rr <= r; ++rr) {
                     const int i = lane + 32 * rr;
-                    if (i < j) b[rr] = fmaf(-T[j * s + i], x, b[rr]);
+                    if (i < j) {
+                        const float t = T[j * s + i];
+#pragma unroll
+                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-t, x[q], b[q][rr]);
+                    }
                 }
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = lane + 32 * r;
-        if (i < s) bcol[i] = b[r];
-    }
+    for (int q = 0; q < kLeafCols; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = lane + 32 * r;
+            if (col0 + q < n && i < s) B[r0 + i + (col0 + q) * ldb] = b[q][r];
+        }
 }
 
-// X op(A)_leaf = B_leaf for the s columns c0 .. c0+s of B: warp per row.
-// T is stored row by row (T[i*s + c]).
+// X op(A)_leaf = B_leaf for the s <= 128 columns c0 .. c0+s of B. A CTA
+// takes kRightRows rows, staged through shared memory (Bs[c][row], padded)
+// so that global accesses run along the rows; each warp then solves
+// kLeafCols rows at once with lanes over columns c = lane + 32r.
 __global__ void __launch_bounds__(256)
 trsm_right_leaf_kernel(int s, int64_t m, const float *__restrict__ A, int64_t lda, int64_t c0,
                        int trans, int tlower, int unit, float *__restrict__ B, int64_t ldb) {
     extern __shared__ float T[];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int c = e % s, i = e / s;
-        T[e] = tri_elem(A, lda, c0, i, c, trans, tlower, unit);
+    float *D = T + s * s;
+    float *Bs = D + kLeaf;                            // [s][kRightRows + 1]
+    constexpr int LDS = kRightRows + 1;
+    const int64_t row0 = (int64_t)blockIdx.x * kRightRows;
+    load_leaf<false>(T, D, s, A, lda, c0, trans, tlower, unit);
+    for (int e = threadIdx.x; e < s * kRightRows; e += blockDim.x) {
+        const int rl = e % kRightRows, c = e / kRightRows;
+        Bs[c * LDS + rl] = row0 + rl < m ? B[row0 + rl + (c0 + c) * ldb] : 0.f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (row >= m) return;
-    float *brow = B + row + c0 * ldb;
-    float b[4];
+    const int rw = (threadIdx.x >> 5) * kLeafCols;     // this warp's first row in the CTA
+    float b[kLeafCols][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int c = lane + 32 * r;
-        b[r] = c < s ? brow[c * ldb] : 0.f;
-    }
+    for (int q = 0; q < kLeafCols; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int c = lane + 32 * r;
+            b[q][r] = c < s ? Bs[c * LDS + rw + q] : 0.f;
+        }
     if (!tlower) {          // op(A) upper: columns left to right
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             for (int ii = 0; ii < 32; ++ii) {
                 const int i = 32 * r + ii;
                 if (i >= s) break;
-                const float bi = __shfl_sync(0xffffffffu, b[r], ii);
-                const float x = unit ? bi : bi / T[i * s + i];
-                if (lane == ii) b[r] = x;
+                const float d = D[i];
+                float x[kLeafCols];
+#pragma unroll
+                for (int q = 0; q < kLeafCols; ++q) {
+                    const float bi = __shfl_sync(0xffffffffu, b[q][r], ii);
+                    x[q] = bi * d;
+                    if (lane == ii) b[q][r] = x[q];
+                }
 #pragma unroll
                 for (int rr = r; rr < 4; ++rr) {
                     const int c = lane + 32 * rr;
-                    if (c > i && c < s) b[rr] = fmaf(-x, T[i * s + c], b[rr]);
+                    if (c > i && c < s) {
+                        const float t = T[i * s + c];
+#pragma unroll
+                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-x[q], t, b[q][rr]);
+                    }
                 }
             }
         }
@@ -212,21 +291,37 @@ trsm_right_leaf_kernel(int s, int64_t m, const float *__restrict__ A, int64_t ld
             for (int ii = 31; ii >= 0; --ii) {
                 const int i = 32 * r + ii;
                 if (i >= s) continue;
-                const float bi = __shfl_sync(0xffffffffu, b[r], ii);
-                const float x = unit ? bi : bi / T[i * s + i];
-                if (lane == ii) b[r] = x;
+                const float d = D[i];
+                float x[kLeafCols];
+#pragma unroll
+                for (int q = 0; q < kLeafCols; ++q) {
+                    const float bi = __shfl_sync(0xffffffffu, b[q][r], ii);
+                    x[q] = bi * d;
+                    if (lane == ii) b[q][r] = x[q];
+                }
 #pragma unroll
                 for (int rr = 0; rr <= r; ++rr) {
                     const int c = lane + 32 * rr;
-                    if (c < i) b[rr] = fmaf(-x, T[i * s + c], b[rr]);
+                    if (c < i) {
+                        const float t = T[i * s + c];
+#pragma unroll
+                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-x[q], t, b[q][rr]);
+                    }
                 }
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int c = lane + 32 * r;
-        if (c < s) brow[c * ldb] = b[r];
+    for (int q = 0; q < kLeafCols; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int c = lane + 32 * r;
+            if (c < s) Bs[c * LDS + rw + q] = b[q][r];
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * kRightRows; e += blockDim.x) {
+        const int rl = e % kRightRows, c = e / kRightRows;
+        if (row0 + rl < m) B[row0 + rl + (c0 + c) * ldb] = Bs[c * LDS + rl];
     }
 }
 
@@ -292,6 +387,20 @@ int syrk_rec(const GemmRunner &g, bool lower, bool trans, int64_t r0, int64_t nn
     return g(ta, tb, n1, n2, k, alpha, a1, lda, a2, lda, beta, C + r0 + (r0 + n1) * ldc, ldc);
 }
 
+// Split mode of the tensor-core SSYRK path, or -1 for the recursive path
+// (SIMT GEMMs and the FP32 diagonal kernel; also every scale-only call).
+int syrk_tc_mode(gb_algo_t algo, int64_t k, bool scale_only) {
+    if (scale_only) return -1;
+    return split_mode(resolve_algo(algo, k));
+}
+
+// Bytes of op(A) split and packed once (n rows, K-major), 256-byte rounded.
+size_t syrk_packed_bytes(int mode, int64_t n, int64_t k) {
+    const size_t per = (size_t)split_parts(mode) * (size_t)split_kpad(mode, k) *
+                       (size_t)split_elem_bytes(mode);
+    return (per * (size_t)n + 255) / 256 * 256;
+}
+
 int check_syrk(char uplo, char trans, int64_t n, int64_t k, int64_t lda, int64_t ldc) {
     if (!is_l(uplo) && !is_u(uplo)) return -1;
     if (!is_n(trans) && !is_t(trans)) return -2;
@@ -322,13 +431,14 @@ inline const float *opa_block(const TrsmCtx &c, int64_t R0, int64_t S0, char *t)
 
 int trsm_leaf(const TrsmCtx &c, int64_t r0, int64_t s) {
     if (c.g.ws_need) return GB_OK;
-    const size_t smem = (size_t)s * (size_t)s * sizeof(float);
+    const size_t tri = ((size_t)s * (size_t)s + kLeaf) * sizeof(float);
     if (c.left) {
-        const int64_t blocks = (c.n + 7) / 8;
-        trsm_left_leaf_kernel<<<(unsigned)blocks, 256, smem, c.g.s>>>(
+        const int64_t blocks = (c.n + 8 * kLeafCols - 1) / (8 * kLeafCols);
+        trsm_left_leaf_kernel<<<(unsigned)blocks, 256, tri, c.g.s>>>(
             (int)s, c.n, c.A, c.lda, r0, c.trans, c.tlower, c.unit, c.B, c.ldb);
     } else {
-        const int64_t blocks = (c.m + 7) / 8;
+        const int64_t blocks = (c.m + kRightRows - 1) / kRightRows;
+        const size_t smem = tri + (size_t)s * (kRightRows + 1) * sizeof(float);
         trsm_right_leaf_kernel<<<(unsigned)blocks, 256, smem, c.g.s>>>(
             (int)s, c.m, c.A, c.lda, r0, c.trans, c.tlower, c.unit, c.B, c.ldb);
     }
@@ -389,11 +499,12 @@ bool leaf_attrs_set(int dev) {
     static bool done[64] = {};
     if (dev < 0 || dev >= 64) return false;
     if (done[dev]) return true;
-    const int bytes = kLeaf * kLeaf * (int)sizeof(float);
+    const int bytes = (kLeaf * kLeaf + kLeaf) * (int)sizeof(float);
+    const int rbytes = bytes + kLeaf * (kRightRows + 1) * (int)sizeof(float);
     if (cudaFuncSetAttribute(trsm_left_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes) != cudaSuccess ||
         cudaFuncSetAttribute(trsm_right_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes) != cudaSuccess)
+                             rbytes) != cudaSuccess)
         return false;
     done[dev] = true;
     return true;
@@ -423,11 +534,14 @@ GB_API int gb_ssyrk_workspace_size(gb_algo_t algo, char uplo, char trans, int64_
     int rc = check_syrk(uplo, trans, n, k, max1(is_n(trans) ? n : k), max1(n));
     if (rc) return rc;
     if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    // the larger of the two paths' needs (the path also depends on alpha)
     size_t need = 0;
     GemmRunner g{nullptr, algo, nullptr, 0, nullptr, &need};
     rc = syrk_rec(g, is_l(uplo), is_t(trans), 0, n, k, 1.f, nullptr, max1(is_n(trans) ? n : k),
                   0.f, nullptr, max1(n));
     if (rc) return rc;
+    const int mode = syrk_tc_mode(algo, k, n == 0 || k == 0);
+    if (mode >= 0 && syrk_packed_bytes(mode, n, k) > need) need = syrk_packed_bytes(mode, n, k);
     *bytes = need;
     return GB_OK;
 }
@@ -444,12 +558,34 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
     if (n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
     const bool scale_only = alpha == 0.f || k == 0;
     if (!C || (!scale_only && !A)) return GB_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int mode = syrk_tc_mode(algo, k, scale_only);
+    if (mode >= 0) {
+        // tensor cores: split/pack op(A) once, one launch over the triangle
+        const size_t need = syrk_packed_bytes(mode, n, k);
+        if (ws_bytes < need || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+            return GB_ERR_WORKSPACE;
+        const int64_t kpad = split_kpad(mode, k);
+        if (launch_split_pack(mode, is_t(trans), n, k, A, lda, workspace, kpad, n * kpad, s) !=
+            cudaSuccess)
+            return GB_ERR_CUDA;
+        TcSyrkArgs t{};
+        t.mode = mode;
+        t.packed = workspace;
+        t.n = n; t.k = k;
+        t.alpha = alpha; t.beta = beta;
+        t.C = C; t.ldc = ldc;
+        t.lower = is_l(uplo);
+        t.sm_count = h->sm_count;
+        t.dstate = h->dstate;
+        t.wait_limit = h->wait_limit;
+        return launch_tc_syrk(t, s) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+    }
     size_t need = 0;
     GemmRunner probe{nullptr, algo, nullptr, 0, nullptr, &need};
     rc = syrk_rec(probe, is_l(uplo), is_t(trans), 0, n, k, alpha, A, lda, beta, C, ldc);
     if (rc) return rc;
     if (need && (ws_bytes < need || !workspace)) return GB_ERR_WORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     GemmRunner g{h, algo, workspace, ws_bytes, s, nullptr};
     rc = syrk_rec(g, is_l(uplo), is_t(trans), 0, n, k, alpha, A, lda, beta, C, ldc);
     if (rc) return rc;

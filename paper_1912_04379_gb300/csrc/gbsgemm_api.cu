@@ -40,28 +40,6 @@ int check_handle(gb_handle_t h) {
     return GB_OK;
 }
 
-int split_mode(gb_algo_t algo) {
-    switch (algo) {
-        case GB_ALGO_SPLIT_TF32X3: return 0;
-        case GB_ALGO_SPLIT_BF16X3: return 1;
-        case GB_ALGO_SPLIT_BF16X6: return 2;
-        case GB_ALGO_SPLIT_BF16X9: return 3;
-        default: return -1;
-    }
-}
-
-// AUTO picks the fastest algorithm whose worst-case error stays within the
-// FP32 bound 2*K*u*D for this K. Each split drops a fixed relative term per
-// product (BF16 x 2: 3*2^-16, BF16 x 3: 2*2^-24); requiring it to use at
-// most half of 2*K*u gives K >= 1024 for BF16 x 2 and K >= 4 for BF16 x 3
-// (which is also faster than TF32 x 2 at the same accuracy class).
-gb_algo_t resolve_algo(gb_algo_t algo, int64_t k) {
-    if (algo != GB_ALGO_AUTO) return algo;
-    if (k >= 1024) return GB_ALGO_SPLIT_BF16X3;
-    if (k >= 4) return GB_ALGO_SPLIT_BF16X6;
-    return GB_ALGO_SIMT;
-}
-
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Workspace of a split algorithm: [A terms][B terms][split-K partials],
@@ -78,6 +56,28 @@ size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
 
 }  // namespace
+
+int gb::split_mode(gb_algo_t algo) {
+    switch (algo) {
+        case GB_ALGO_SPLIT_TF32X3: return 0;
+        case GB_ALGO_SPLIT_BF16X3: return 1;
+        case GB_ALGO_SPLIT_BF16X6: return 2;
+        case GB_ALGO_SPLIT_BF16X9: return 3;
+        default: return -1;
+    }
+}
+
+// AUTO picks the fastest algorithm whose worst-case error stays within the
+// FP32 bound 2*K*u*D for this K. Each split drops a fixed relative term per
+// product (BF16 x 2: 3*2^-16, BF16 x 3: 2*2^-24); requiring it to use at
+// most half of 2*K*u gives K >= 1024 for BF16 x 2 and K >= 4 for BF16 x 3
+// (which is also faster than TF32 x 2 at the same accuracy class).
+gb_algo_t gb::resolve_algo(gb_algo_t algo, int64_t k) {
+    if (algo != GB_ALGO_AUTO) return algo;
+    if (k >= 1024) return GB_ALGO_SPLIT_BF16X3;
+    if (k >= 4) return GB_ALGO_SPLIT_BF16X6;
+    return GB_ALGO_SIMT;
+}
 
 // Split-K: when a problem has too few output tiles to occupy the GPU (at most
 // 37 tiles of 128 x BN) and a long K (>= 1024), each tile's K range is cut

@@ -155,6 +155,26 @@ cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, cons
                               int64_t nitems, int sm_count, DeviceState *dstate,
                               int64_t wait_limit, cudaStream_t s);
 
+// SSYRK on the tensor cores: C <- alpha op(A) op(A)^T + beta C on one
+// triangle, op(A) (n x k) already split and packed like an SGEMM A operand.
+struct TcSyrkArgs {
+    int mode;                   // as launch_split_pack
+    const void *packed;         // [parts][n][kpad]
+    int64_t n, k;
+    float alpha, beta;
+    float *C;
+    int64_t ldc;
+    bool lower;
+    int sm_count;
+    DeviceState *dstate;
+    int64_t wait_limit;         // microseconds
+};
+cudaError_t launch_tc_syrk(const TcSyrkArgs &a, cudaStream_t s);
+
+// AUTO's choice for a given K, and the split mode of an algorithm (-1: SIMT).
+gb_algo_t resolve_algo(gb_algo_t algo, int64_t k);
+int split_mode(gb_algo_t algo);
+
 // One 64 x 64 (rows x k) tile of the grouped split/pack pass.
 struct PackItem {
     const float *X;

@@ -1,0 +1,229 @@
+// The warp-specialised tcgen05 kernel body shared by every tensor-core
+// kernel of the library (one GEMM, grouped GEMMs, triangular updates):
+// stage configuration, the per-role loops, and the grouped work source.
+// A work source supplies num_units() and unit(u, UnitInfo&) (tile, K range,
+// tensor maps, output); kTri selects the triangle-masked epilogue.
+#pragma once
+
+#include "tc_ptx.cuh"
+
+namespace gb {
+namespace tcx {
+
+constexpr int NUM_THREADS = 192;
+
+// ----------------------------------------------------------- the kernel --
+template <int MODE, int RB>
+struct Cfg {
+    static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
+    static constexpr bool TF32 = MODE == 0;
+    static constexpr int PARTS = MODE >= 2 ? 3 : 2;
+    static constexpr int NPAIRS = MODE == 3 ? 9 : MODE == 2 ? 6 : 3;
+    static constexpr int BN = MODE >= 2 ? 128 : 256;
+    static constexpr int ELEM = TF32 ? 4 : 2;
+    static constexpr int BK = ROW_BYTES / ELEM;          // elements per k-block
+    static constexpr int KSTEP_BYTES = 32;               // K per MMA: 16 BF16 / 8 TF32
+    static constexpr int KSTEPS = ROW_BYTES / KSTEP_BYTES;
+    static constexpr int A_TILE = BM * ROW_BYTES;        // bytes of one term's A tile
+    static constexpr int B_TILE = BN * ROW_BYTES;
+    static constexpr int STAGE_BYTES = PARTS * (A_TILE + B_TILE);
+    static constexpr int STAGES = (200 * 1024) / STAGE_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
+    static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
+    static_assert(STAGES >= 2, "need at least two stages");
+    static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
+};
+
+// Many GEMMs: units are the planned (problem, tile) items; each problem has
+// its own tensor maps (in device global memory) and output.
+template <int BN, int BK>
+struct GroupSource {
+    static constexpr bool kTri = false;
+    const TcProblem *probs;
+    const TcItem *items;
+    int64_t nitems;
+    __device__ __forceinline__ int64_t num_units() const { return nitems; }
+    __device__ __forceinline__ void unit(int64_t u, UnitInfo &ui) const {
+        const TcItem it = items[u];
+        const TcProblem &P = probs[it.prob];
+        ui.ma = P.mapA; ui.mb = P.mapB;
+        ui.M = P.m; ui.N = P.n;
+        ui.tm = it.tm; ui.tn = it.tn;
+        ui.kb0 = 0;
+        ui.kb1 = (int)((P.k + BK - 1) / BK);
+        ui.alpha = P.alpha; ui.beta = P.beta;
+        ui.dst = P.C; ui.ldd = P.ldc;
+        ui.raw = false;
+    }
+};
+
+template <int MODE, int RB, class Src>
+__device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uint64_t limit_ns) {
+    using CF = Cfg<MODE, RB>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    // [stages][term][A tile] then [stages][term][B tile]
+    const uint32_t a_smem = base;
+    const uint32_t b_smem = base + CF::STAGES * CF::PARTS * CF::A_TILE;
+    const uint32_t bar_base = base + CF::STAGES * CF::STAGE_BYTES;
+    uint8_t *gbar = gbase + CF::STAGES * CF::STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar_base + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (CF::STAGES + s); };
+    auto accf_bar = [&](int b) { return bar_base + 8u * (2 * CF::STAGES + b); };
+    auto acce_bar = [&](int b) { return bar_base + 8u * (2 * CF::STAGES + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * CF::STAGES + 4);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbar + 8 * (2 * CF::STAGES + 5));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbar + 8 * (2 * CF::STAGES + 5) + 4);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    WaitCtx w{abort_flag, dstate, limit_ns};
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 4);       // one arrive per epilogue warp
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_holder), CF::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const int64_t num_units = src.num_units();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, last_parity = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                UnitInfo ui;
+                src.unit(u, ui);
+                const int y_a = (int)(ui.tm * BM), y_b = (int)(ui.tn * CF::BN);
+                for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
+                    if (!wait_bounded(w, empty_bar(stage), phase ^ 1u, kSiteProducerEmpty)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(full_bar(stage), CF::STAGE_BYTES);
+                    for (int t = 0; t < CF::PARTS; ++t) {
+                        tma_load_3d(a_smem + (stage * CF::PARTS + t) * CF::A_TILE, ui.ma,
+                                    full_bar(stage), kb * CF::BK, y_a, t);
+                        tma_load_3d(b_smem + (stage * CF::PARTS + t) * CF::B_TILE, ui.mb,
+                                    full_bar(stage), kb * CF::BK, y_b, t);
+                    }
+                    issued_mask |= 1u << stage;
+                    last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // Wait (bounded, even after an abort) for every copy still in flight.
+            for (int s = 0; s < CF::STAGES; ++s) {
+                if (!(issued_mask & (1u << s))) continue;
+                const uint32_t par = (last_parity >> s) & 1u;
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(full_bar(s), par)) {
+                    if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t idesc = instr_desc<CF::TF32, CF::BN>();
+            const uint64_t desc_a0 = smem_desc<RB>(a_smem), desc_b0 = smem_desc<RB>(b_smem);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
+                uint32_t accumulate = 0;
+                UnitInfo ui;
+                src.unit(u, ui);
+                for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
+                    if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // The descriptor's start-address field is the byte address
+                    // >> 4, so offsetting a descriptor by whole 16-byte units
+                    // is an add: one base descriptor per stage and operand,
+                    // constant offsets for the term and the k-step.
+                    const uint64_t da = desc_a0 + (uint64_t)((stage * CF::PARTS * CF::A_TILE) >> 4);
+                    const uint64_t db = desc_b0 + (uint64_t)((stage * CF::PARTS * CF::B_TILE) >> 4);
+#pragma unroll
+                    for (int q = 0; q < CF::NPAIRS; ++q) {
+                        int sa, sb;
+                        pair_of<MODE>(q, sa, sb);
+#pragma unroll
+                        for (int ks = 0; ks < CF::KSTEPS; ++ks) {
+                            mma_issue<CF::TF32>(
+                                d_tmem, da + (uint64_t)((sa * CF::A_TILE + ks * CF::KSTEP_BYTES) >> 4),
+                                db + (uint64_t)((sb * CF::B_TILE + ks * CF::KSTEP_BYTES) >> 4), idesc,
+                                accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    mma_commit(empty_bar(stage));     // frees the stage once these MMAs finish
+                    if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(accf_bar(acc));            // accumulator ready for the epilogue
+                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+            }
+            // Make sure no MMA is still running before TMEM is released.
+            mma_commit(drain_bar);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(drain_bar, 0)) {
+                if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                       // TMEM lane quarter this warp may read
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t u = blockIdx.x; u < num_units; u += gridDim.x) {
+            // The TMEM loads below are warp-collective: leave (or stay) as a
+            // whole warp even if only some lanes saw their wait expire.
+            const bool got = wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            UnitInfo ui;
+            src.unit(u, ui);
+            store_tile<CF::BN, Src::kTri>(ui, tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN),
+                               q, lane);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(acc));
+            if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, CF::TMEM_COLS);
+}
+
+}  // namespace tcx
+}  // namespace gb

@@ -256,6 +256,7 @@ struct UnitInfo {
     float *dst;                   // C, or this slice's partial-sum buffer
     int64_t ldd;
     bool raw;                     // write raw sums (split-K partial), no alpha/beta
+    bool lower;                   // triangle sources: keep col <= row (else col >= row)
 };
 
 // One GEMM: units are (tile, K slice) pairs in the grouped raster order.
@@ -263,6 +264,7 @@ struct UnitInfo {
 // column-major, ld = M); a separate pass reduces them.
 template <int BN, int BK>
 struct SingleSource {
+    static constexpr bool kTri = false;
     const CUtensorMap *ma, *mb;
     int64_t M, N, K;
     float alpha, beta;
@@ -292,8 +294,10 @@ struct SingleSource {
 
 // Epilogue of one work unit for one epilogue warp: TMEM lanes q*32..q*32+31
 // (rows of the tile) of the accumulator at TMEM address `taddr`, BN columns,
-// to C (alpha/beta) or to a split-K partial buffer (raw sums).
-template <int BN>
+// to C (alpha/beta) or to a split-K partial buffer (raw sums). TRI: only the
+// elements of the ui.lower (col <= row) or upper (col >= row) triangle are
+// stored (and C is read only there).
+template <int BN, bool TRI = false>
 __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, int q, int lane) {
     const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
     float *dst = ui.dst;
@@ -311,7 +315,9 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
     // slower on the store-bound K = 64 shapes.) Interior tiles take a
     // path with no per-element checks and a pointer bump per column:
     // on store-bound shapes the epilogue's instruction count is the limit.
-    const bool interior = (ui.tm * BM + BM <= M) && (col0 + BN <= N);
+    bool interior = (ui.tm * BM + BM <= M) && (col0 + BN <= N);
+    if (TRI)   // the whole tile inside the triangle
+        interior = interior && (ui.lower ? col0 + BN - 1 <= ui.tm * BM : col0 >= ui.tm * BM + BM - 1);
     float *colp = dst + row + col0 * ldd;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
@@ -341,15 +347,21 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
             continue;
         }
         if (!row_ok) continue;
-        const int ncol = (int)(N - (col0 + c) < 16 ? N - (col0 + c) : 16);
+        int jlo = 0, jhi = (int)(N - (col0 + c) < 16 ? N - (col0 + c) : 16);
+        if (TRI) {   // columns col0 + c + j inside the triangle
+            const int64_t d = row - (col0 + c);
+            if (ui.lower) jhi = d + 1 < jhi ? (int)(d + 1 < 0 ? 0 : d + 1) : jhi;
+            else jlo = d > 0 ? (int)(d < 16 ? d : 16) : 0;
+        }
         const bool rd = !part && beta != 0.f;
         float cv[16];
         const float *qc = p;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) { cv[j] = (rd && j < ncol) ? *qc : 0.f; qc += ldd; }
+        for (int j = 0; j < 16; ++j) { cv[j] = (rd && j >= jlo && j < jhi) ? *qc : 0.f; qc += ldd; }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            if (j < ncol) *p = rd ? fmaf(a, __uint_as_float(r[j]), beta * cv[j]) : a * __uint_as_float(r[j]);
+            if (j >= jlo && j < jhi)
+                *p = rd ? fmaf(a, __uint_as_float(r[j]), beta * cv[j]) : a * __uint_as_float(r[j]);
             p += ldd;
         }
     }

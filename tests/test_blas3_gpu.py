@@ -1,10 +1,10 @@
 """GPU parity of gb_ssyrk and gb_strsm against the FP64 oracle (oracle/blas3.py).
 
 SSYRK: every element of the `uplo` triangle within the SGEMM bound
-(2 max(K,1) u + e_algo) D of the algorithm that ran (diagonal blocks run in
-FP32 SIMT, inside any algorithm's bound); the other triangle holds NaN and
-must come back untouched; padding rows keep their canary; integer data is
-bit-exact.
+(2 max(K,1) u + e_algo) D of the algorithm that ran (the one-launch
+tensor-core triangle for a split algorithm; GEMM recursion with FP32
+diagonal blocks for SIMT); the other triangle holds NaN and must come back
+untouched; padding rows keep their canary; integer data is bit-exact.
 
 STRSM: the solution is checked through its residual, a property that holds
 at any size: with s = m (side 'L') or n (side 'R') and the recursion depth d,
@@ -74,6 +74,29 @@ def test_ssyrk_against_oracle(algo, n, k, uplo, trans):
     assert np.all(err[mask] <= bound[mask]), float(np.max(err[mask] / bound[mask]))
     assert np.all(np.isnan(got[:n, :n][~mask]))            # other triangle untouched
     assert np.all(got[n:, :] == wl.CANARY)                 # padding rows
+
+
+@pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
+@pytest.mark.parametrize("n,k", [(300, 20), (520, 2100)])
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x9"))
+def test_ssyrk_tensor_core_algorithms(algo, n, k, uplo, trans):
+    """The one-launch triangle kernel for every split (both stage widths)."""
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    A, C = _syrk_case(uplo, trans, n, k, -0.75, 1.5, seed=3 * n + k, dist="logu")
+    Ad, Cd = _dev(A), _dev(C)
+    gb.ssyrk_raw(uplo, trans, n, k, -0.75, Ad.data_ptr(), A.shape[0], 1.5, Cd.data_ptr(),
+                 C.shape[0], algo=algo)
+    torch.cuda.synchronize()
+    assert gb.default_handle().device_error() == (0, 0)
+    got = gb.to_fortran(Cd)
+    C64, D = blas3.ssyrk(uplo, trans, n, k, -0.75, A, A.shape[0], 1.5, C, C.shape[0])
+    mask = ~np.isnan(C64)
+    bound = (2 * max(k, 1) * U + SPLIT_EXTRA[algo]) * D
+    err = np.abs(got[:n, :n] - C64)
+    assert np.all(err[mask] <= bound[mask]), float(np.max(err[mask] / bound[mask]))
+    assert np.all(np.isnan(got[:n, :n][~mask]))
+    assert np.all(got[n:, :] == wl.CANARY)
 
 
 @pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
