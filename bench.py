@@ -37,7 +37,7 @@ SEED = 2
 ALGO = "bf16x3"
 # Per-launch DRAM traffic of the tensor-core kernel at 8192^3 bf16x3 from one
 # ncu capture, valid only for the kernel source it was taken on.
-TRAFFIC = {"source_sha": "08040fa6f4de48ec", "bytes": 2533570720}
+TRAFFIC = {"source_sha": "a98d937337db1a5f", "bytes": 2524423544}
 
 
 def env_int(name, default):
@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--clocks-log", default=None)
     ap.add_argument("--profile-grouped", default=None, metavar="ALGO",
                     help="run the 2000-problem grouped workload twice with ALGO and exit")
+    ap.add_argument("--profile-blas3", default=None, metavar="ssyrk|strsm[,N]",
+                    help="run SSYRK or STRSM of size N (default 8192) twice and exit")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="run two training steps of the benchmark network and exit")
     ap.add_argument("--profile", default=None, metavar="M,N,K[,ALGO]",
                     help="run one warm-up and one measured SGEMM of this shape (pack A, pack B, "
                          "compute) and exit; a small case for ncu captures")
@@ -113,6 +117,54 @@ def run_profile_grouped(algo):
         plan.run()
     torch.cuda.synchronize()
     print(json.dumps({"profile_grouped": algo, "ok": True}), flush=True)
+    return 0
+
+
+def run_profile_blas3(which):
+    """Two calls of SSYRK ('L', 'N', n = k = N) or STRSM ('L', 'L', 'N', 'N',
+    m = n = N) on device-resident random inputs, N = 8192 or the size after a
+    comma (ncu target)."""
+    import torch
+    import paper_1912_04379_gb300 as gb
+    name, _, size = which.partition(",")
+    n = int(size) if size else 8192
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(6)
+    A = gb.colmajor(n, n)
+    A.copy_(torch.rand((n, n), device="cuda", generator=g) * 2 - 1)
+    C = gb.colmajor(n, n, fill=0.0)
+    if name == "strsm":
+        A.div_(n)
+        A.diagonal().add_(1.5)
+        C.copy_(torch.rand((n, n), device="cuda", generator=g))
+    for _ in range(2):
+        if name == "ssyrk":
+            gb.ssyrk_raw("L", "N", n, n, 1.0, A.data_ptr(), n, 0.0, C.data_ptr(), n)
+        else:
+            gb.strsm_raw("L", "L", "N", "N", n, n, 1.0, A.data_ptr(), n, C.data_ptr(), n)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_blas3": [name, n], "ok": True}), flush=True)
+    return 0
+
+
+def run_profile_mlp():
+    """Two training steps of the benchmark's fully connected network (ncu target)."""
+    import torch
+    import paper_1912_04379_gb300 as gb
+    torch.cuda.set_device(0)
+    widths, B = MLP_WIDTHS, MLP_BATCH
+    net = gb.MLP(widths, B, hidden="tanh", algo="auto")
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for l, W in enumerate(net.W):
+        W.copy_(torch.randn(W.shape, device="cuda", generator=g) / widths[l] ** 0.5)
+    X = gb.colmajor(widths[0], B)
+    X.copy_(torch.randn(X.shape, device="cuda", generator=g))
+    Y = gb.colmajor(widths[-1], B)
+    Y.copy_(torch.randn(Y.shape, device="cuda", generator=g))
+    for _ in range(2):
+        net.train_step(X, Y, 1e-3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_mlp": list(widths), "ok": True}), flush=True)
     return 0
 
 
@@ -263,7 +315,8 @@ def run_reference(args, rank):
 
 def source_sha():
     h = hashlib.sha256()
-    for f in ("tc_sgemm.cu", "tc_ptx.cuh", "split_common.cuh", "split_pack.cu", "internal.h"):
+    for f in ("tc_sgemm.cu", "tc_body.cuh", "tc_ptx.cuh", "split_common.cuh", "split_pack.cu",
+              "internal.h"):
         with open(os.path.join(ROOT, "paper_1912_04379_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -578,22 +631,18 @@ def run_ours(args, rank, world, local_rank):
         arms[algo] = time_algo(algo, max(3, args.steps // 5), outs[algo])
     outs[ALGO] = C
 
-    # -------- end to end: pinned host buffers, copies inside the timed region
+    # -------- end to end: pinned host buffers, copies inside the timed region,
+    # through gb_sgemm_host (A copied once, B and C streamed in column blocks,
+    # uploads, GEMMs and downloads overlapped on the handle's streams)
     A_h = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()     # (cols, ld) = storage
     B_h = torch.from_numpy(np.ascontiguousarray(p.B.T)).pin_memory()
     C_h = torch.empty((N, M), dtype=torch.float32).pin_memory()
-    A_d = torch.empty_like(A_h, device=dev)
-    B_d = torch.empty_like(B_h, device=dev)
-    C_d = torch.empty((N, M), dtype=torch.float32, device=dev)
-    ws_n = gb.workspace_size(ALGO, "N", "N", M, N, K)
+    ws_n = gb.sgemm_host_workspace_size(ALGO, "N", "N", M, N, K)
     ws = torch.empty(ws_n, dtype=torch.uint8, device=dev)
 
     def e2e_step():
-        A_d.copy_(A_h, non_blocking=True)
-        B_d.copy_(B_h, non_blocking=True)
-        gb.sgemm_raw("N", "N", M, N, K, 1.0, A_d.data_ptr(), M, B_d.data_ptr(), K, 0.0,
-                     C_d.data_ptr(), M, algo=ALGO, handle=h, workspace=ws)
-        C_h.copy_(C_d, non_blocking=True)
+        gb.sgemm_host_raw("N", "N", M, N, K, 1.0, A_h.data_ptr(), M, B_h.data_ptr(), K, 0.0,
+                          C_h.data_ptr(), M, algo=ALGO, handle=h, workspace=ws, stream=stream)
 
     for _ in range(2):
         e2e_step()
@@ -677,6 +726,10 @@ def main():
         return run_profile_case(args.profile)
     if args.profile_grouped:
         return run_profile_grouped(args.profile_grouped)
+    if args.profile_blas3:
+        return run_profile_blas3(args.profile_blas3)
+    if args.profile_mlp:
+        return run_profile_mlp()
     if args.impl == "reference":
         return run_reference(args, rank)
     return run_ours(args, rank, world, local_rank)

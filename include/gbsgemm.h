@@ -311,6 +311,29 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
  * (9.2 ms against 1.9 ms at M = N = K = 8192). */
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 
+/* Device workspace bytes gb_sgemm_host needs for this problem. */
+GB_API int gb_sgemm_host_workspace_size(gb_algo_t algo, char transa, char transb, int64_t m,
+                                        int64_t n, int64_t k, size_t *bytes);
+
+/* gb_sgemm with A, B and C in HOST memory (page-locked memory lets the
+ * copies overlap; pageable memory works, slower). Arguments, semantics and
+ * status codes as gb_sgemm; `workspace` is DEVICE memory (256-byte aligned)
+ * of at least gb_sgemm_host_workspace_size bytes. op(A) is copied once (and
+ * split and packed once for a split algorithm); op(B) and C then move in
+ * blocks of columns through two device slots, so that the host->device copy
+ * of block j+1, the GEMM of block j and the device->host copy of block j-1
+ * run concurrently on three streams owned by the handle. The pipeline starts
+ * after the work already enqueued on `stream`, and `stream` waits for its
+ * last copy: the call is ordered on `stream` and returns without waiting
+ * (the host buffers must stay valid until `stream` has reached that point).
+ * Calls on one handle must not run concurrently from several host threads.
+ * For a split algorithm the per-block GEMMs use no split-K, so results can
+ * differ in rounding from gb_sgemm's on shapes where gb_sgemm splits K. */
+GB_API int gb_sgemm_host(gb_handle_t h, gb_algo_t algo, char transa, char transb, int64_t m,
+                         int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                         const float *B, int64_t ldb, float beta, float *C, int64_t ldc,
+                         void *workspace, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * Training step of a fully connected network on the SGEMM (the paper's
  * application, Sec. 4: the SGEMM as the kernel of neural-network training).

@@ -8,11 +8,12 @@ does not load the CUDA library; the first call does, and fails loudly if
 the library is missing.
 """
 from .api import (GroupedPlan, Handle, backward_raw, colmajor, compute_raw, default_handle,
-                  err_report, from_fortran, pack_raw, pack_size, sgemm, sgemm_raw, ssyrk_raw,
-                  strsm_raw, to_fortran, upload_problems, workspace_size)
+                  err_report, from_fortran, pack_raw, pack_size, sgemm, sgemm_host_raw,
+                  sgemm_host_workspace_size, sgemm_raw, ssyrk_raw, strsm_raw, to_fortran,
+                  upload_problems, workspace_size)
 from .mlp import MLP
 
 __all__ = ["MLP", "GroupedPlan", "Handle", "backward_raw", "colmajor", "compute_raw",
            "default_handle", "err_report", "from_fortran", "pack_raw", "pack_size", "sgemm",
-           "sgemm_raw", "ssyrk_raw", "strsm_raw", "to_fortran", "upload_problems",
+           "sgemm_host_raw", "sgemm_host_workspace_size", "sgemm_raw", "ssyrk_raw", "strsm_raw", "to_fortran", "upload_problems",
            "workspace_size"]

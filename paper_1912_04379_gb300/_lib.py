@@ -92,6 +92,10 @@ SIGNATURES = {
     "gb_mlp_train_step": ([c_vp, c_int, ctypes.POINTER(MlpDesc), ctypes.POINTER(c_vp),
                            ctypes.POINTER(c_vp), c_vp, c_vp, c_f, ctypes.POINTER(c_vp),
                            ctypes.POINTER(c_vp), c_vp, c_vp, c_size, c_vp], c_int),
+    "gb_sgemm_host_workspace_size": ([c_int, c_char, c_char, c_i64, c_i64, c_i64,
+                                      ctypes.POINTER(c_size)], c_int),
+    "gb_sgemm_host": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64, c_f, c_vp, c_i64, c_vp,
+                       c_i64, c_f, c_vp, c_i64, c_vp, c_size, c_vp], c_int),
     "gb_ssyrk_workspace_size": ([c_int, c_char, c_char, c_i64, c_i64, ctypes.POINTER(c_size)],
                                 c_int),
     "gb_ssyrk": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_f, c_vp, c_i64, c_f, c_vp, c_i64,

@@ -149,6 +149,34 @@ def sgemm_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, C_pt
     return rc
 
 
+def sgemm_host_workspace_size(algo, transa, transb, m, n, k) -> int:
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    _lib.check("gb_sgemm_host_workspace_size",
+               lib.gb_sgemm_host_workspace_size(_lib.ALGOS[algo], transa.encode(),
+                                                transb.encode(), m, n, k, ctypes.byref(out)))
+    return out.value
+
+
+def sgemm_host_raw(transa, transb, m, n, k, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc,
+                   algo="auto", handle=None, stream=None, workspace=None, check=True) -> int:
+    """gb_sgemm_host: A, B, C are HOST pointers (ints; page-locked memory for
+    overlap), the workspace is device memory. Returns the status."""
+    h = handle or default_handle()
+    if workspace is None:
+        ok = (m >= 0 and n >= 0 and k >= 0 and transa in "NnTtCc" and transb in "NnTtCc")
+        workspace = h.workspace(sgemm_host_workspace_size(algo, transa, transb, m, n, k)
+                                if ok else 0)
+    ws_ptr = workspace.data_ptr() if workspace is not None else 0
+    ws_len = workspace.numel() if workspace is not None else 0
+    rc = h.lib.gb_sgemm_host(h.h, _lib.ALGOS[algo], transa.encode(), transb.encode(), m, n, k,
+                             float(alpha), A_ptr, lda, B_ptr, ldb, float(beta), C_ptr, ldc,
+                             ws_ptr, ws_len, _stream_ptr(stream))
+    if check:
+        _lib.check("gb_sgemm_host", rc)
+    return rc
+
+
 def ssyrk_raw(uplo, trans, n, k, alpha, A_ptr, lda, beta, C_ptr, ldc, algo="auto",
               handle=None, stream=None, check=True) -> int:
     """gb_ssyrk on device pointers: C <- alpha op(A) op(A)^T + beta C on the

@@ -266,6 +266,7 @@ GB_API int gb_destroy(gb_handle_t h) {
     if (!h) return GB_OK;
     if (h->magic != kHandleMagic) return GB_ERR_HANDLE;
     cudaDeviceSynchronize();
+    gb::destroy_pipe(h);
     cudaFree(h->dstate);
     h->magic = 0;
     delete h;

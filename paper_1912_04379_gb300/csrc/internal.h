@@ -43,11 +43,17 @@ struct gb_handle_s {
     bool grouped_tuned;
     int grouped_choice[8];
     bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
+    // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
+    bool pipe_ready;
+    cudaStream_t pipe_stream[3];
+    cudaEvent_t pipe_event[8];
 };
 
 namespace gb {
 
 constexpr int kHandleMagic = 0x6b5e3a21;
+constexpr int kPipeEvents = 8;
+void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events
 
 // ------------------------------------------------------------------ SIMT --
 struct SimtArgs {

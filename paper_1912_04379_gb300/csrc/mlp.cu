@@ -67,13 +67,21 @@ loss_grad_kernel(int64_t total, float fb, const float *__restrict__ H, const flo
     }
 }
 
-// loss = (sum of the partials, in order) / (2B)
-__global__ void loss_finish_kernel(const float *__restrict__ partial, int nblocks, float fb,
-                                   float *__restrict__ loss) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        float s = 0.f;
-        for (int i = 0; i < nblocks; ++i) s += partial[i];
-        *loss = s / (2.f * fb);
+// loss = (sum of the partials) / (2B), one block of kThreads threads: thread
+// t sums partials t, t + kThreads, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(kThreads)
+loss_finish_kernel(const float *__restrict__ partial, int nblocks, float fb,
+                   float *__restrict__ loss) {
+    __shared__ float red[kThreads / 32];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < nblocks; i += kThreads) s += partial[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        *loss = t / (2.f * fb);
     }
 }
 
@@ -256,7 +264,7 @@ GB_API int gb_mlp_train_step(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t 
         if (nblk > kLossBlocksMax) nblk = kLossBlocksMax;
         float *partial = reinterpret_cast<float *>(ws + p.loss_off);
         loss_grad_kernel<<<nblk, kThreads, 0, s>>>(total, fb, H[L - 1], Y, G[L - 1], partial);
-        loss_finish_kernel<<<1, 32, 0, s>>>(partial, nblk, fb, loss);
+        loss_finish_kernel<<<1, kThreads, 0, s>>>(partial, nblk, fb, loss);
         if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
     }
 
