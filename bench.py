@@ -532,6 +532,55 @@ def plan_launches(plan):
     return getattr(plan, "kernels_per_run", 1)
 
 
+class ReplicaGroup:
+    """The replicas of a multi-GPU run: one process per GPU, each running the
+    whole workload on its own data (no data-path collective). The group only
+    lines the ranks up around the timed region and takes the slowest rank's
+    time. backend None = a single process."""
+
+    def __init__(self, backend=None, device=None):
+        self.dist = None
+        self.device = device
+        if backend is not None:
+            import torch.distributed as dist
+            kw = {"device_id": device} if backend == "nccl" and device is not None else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    @property
+    def world(self):
+        return self.dist.get_world_size() if self.dist is not None else 1
+
+    @property
+    def rank(self):
+        return self.dist.get_rank() if self.dist is not None else 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        """The maximum of x over the ranks (every rank gets it)."""
+        if self.dist is None:
+            return x
+        import torch
+        dev = self.device if self.device is not None and self.device.type == "cuda" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_value(flops_per_rank, ms_max, world):
+    """Throughput of the whole job in TFLOP/s: every rank's flops over the
+    slowest rank's time (weak scaling: the per-rank work is fixed)."""
+    return world * flops_per_rank / (ms_max * 1e-3) / 1e12
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -540,22 +589,13 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    group = ReplicaGroup("nccl" if world > 1 else None, dev)
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        group.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = group.max
 
     p = wl.split_case(M, N, K, seed=SEED)
     h = gb.Handle(dev)
@@ -601,7 +641,7 @@ def run_ours(args, rank, world, local_rank):
     ms_step = max_over_ranks(total_ms / args.steps)
     kern_ms = max_over_ranks(kern_ms)
     flops = 2.0 * M * N * K
-    value = world * flops / (ms_step * 1e-3) / 1e12
+    value = whole_job_value(flops, ms_step, world)
     err_rc, site = h.device_error()
     if err_rc != 0:
         raise RuntimeError(f"device wait timeout at site {site}")
@@ -655,7 +695,7 @@ def run_ours(args, rank, world, local_rank):
     s1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(s0.elapsed_time(s1) / e2e_steps)
-    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+    e2e = {"value": whole_job_value(flops, e2e_ms, world), "unit": "TFLOP/s",
            "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4,
            "d2h_bytes_per_step": C_h.numel() * 4}
@@ -709,8 +749,7 @@ def run_ours(args, rank, world, local_rank):
                             "sample_columns": len(cols), "by_algo": acc}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    group.close()
     return 0
 
 
