@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import platform
 import os
 import statistics
 import subprocess
@@ -269,6 +270,92 @@ def cpu_oracle_sample(p, target_s, cols_hint=None):
                           p.C, p.ldc, cols=cols)
     dt = time.perf_counter() - t0
     return cols, C64, D, dt, threads
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name":
+                return val.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                if key.strip() in ("model name", "CPU part"):
+                    return val.strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine() or "unknown"
+
+
+def cpu_single_thread(n=1024):
+    """The oracle on one host thread at n^3 (2 n^3 flops), in seconds."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(0)
+    A = np.asfortranarray(rng.uniform(-1, 1, (n, n)).astype(np.float32))
+    B = np.asfortranarray(rng.uniform(-1, 1, (n, n)).astype(np.float32))
+    t0 = time.perf_counter()
+    oracle.sgemm("N", "N", n, n, n, 1.0, A, n, B, n, 0.0, None, n, nthreads=1)
+    return time.perf_counter() - t0
+
+
+def measure_rooflines(gb, h, dev, stream):
+    """Roofline denominators measured in this run: FP32 FMA throughput of
+    the device (the library's FFMA probe) and the TF32 tensor rate (cuBLAS
+    through torch.matmul with TF32 allowed, M = N = K = 8192), with the
+    nominal FP32 figure (SMs x 128 lanes x 2 flops x 2.07 GHz) beside it."""
+    import ctypes
+    import torch
+    sink = torch.empty(256, dtype=torch.float32, device=dev)
+    fmas = ctypes.c_int64(0)
+
+    def ffma():
+        _lib_check(h.lib.gb_measure_ffma(h.h, 4096, ctypes.c_void_p(sink.data_ptr()),
+                                         ctypes.byref(fmas), ctypes.c_void_p(stream.cuda_stream)))
+
+    ffma()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        ffma()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp32 = 2.0 * fmas.value * 5 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    n = 8192
+    a = torch.randn((n, n), device=dev)
+    b = torch.randn((n, n), device=dev)
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        c = a @ b
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            c = a @ b
+        e1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    tf32 = 2.0 * n ** 3 * 5 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    del a, b, c
+    return {"fp32_simt_tflops": fp32, "fp32_simt_nominal_tflops": nominal,
+            "tf32_tensor_tflops": tf32, "sms": props.multi_processor_count,
+            "how": "FP32: gb_measure_ffma (8 blocks x 256 threads per SM, 128 FMA per thread "
+                   "per iteration); TF32: torch.matmul 8192^3 with TF32 allowed (cuBLAS)"}
+
+
+def _lib_check(rc):
+    if rc != 0:
+        raise RuntimeError(f"library call failed with status {rc}")
 
 
 # --------------------------------------------------------- reference -----
@@ -704,6 +791,7 @@ def run_ours(args, rank, world, local_rank):
     shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
     mlp = None if args.no_mlp else bench_mlp(gb, h, dev, stream)
     blas3 = None if args.no_blas3 else bench_blas3(gb, h, dev, stream)
+    measured = measure_rooflines(gb, h, dev, stream)
 
     peaks, peak_kind = load_peaks()
     tensor_flops = 3.0 * flops                       # three BF16 products per FP32 product
@@ -715,6 +803,22 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peak, "traffic": traffic, "kernel": "tc_sgemm_kernel<bf16x3>",
                 "kernel_ms": kern_ms, "peak_kind": f"{peak_kind} bf16 dense (burst)",
                 "counted": "3 x 2MNK executed BF16 tensor flops per launch"}
+    # the split/pack pass of the step, apart: reads A and B (4 B per element),
+    # writes two BF16 terms (4 B per element)
+    pack_ms = max(ms_step - kern_ms, 1e-9)
+    pack_bytes = 8.0 * (M * K + K * N)
+    pack = {"ms": pack_ms, "bytes": pack_bytes, "gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
+            "hbm_frac": pack_bytes / (pack_ms * 1e-3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+    # each arm against its own ceiling: SIMT against the measured FP32 FMA rate,
+    # the splits against their tensor rate divided by the products per FP32 product
+    bf16 = peak
+    ceilings = {"simt": measured["fp32_simt_tflops"],
+                "tf32x3": measured["tf32_tensor_tflops"] / 3.0,
+                "bf16x6": bf16 / 6.0, "bf16x9": bf16 / 9.0}
+    for algo, row in arms.items():
+        if algo in ceilings:
+            row["ceiling_tflops"] = ceilings[algo]
+            row["frac"] = row["value"] / ceilings[algo]
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -723,17 +827,20 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roofline,
-            "arms": arms, "grouped": grouped, "shapes": shapes, "mlp": mlp, "blas3": blas3,
-            "clocks": clocks,
+            "pack": pack, "arms": arms, "measured_rooflines": measured, "grouped": grouped,
+            "shapes": shapes, "mlp": mlp, "blas3": blas3, "clocks": clocks,
             "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cols, C64, D, dt, threads = cpu_oracle_sample(p, args.cpu_seconds)
         cpu_val = 2.0 * M * K * len(cols) / dt / 1e12
+        t1 = cpu_single_thread(1024)
         line["cpu_baseline"] = {"value": cpu_val, "unit": "TFLOP/s", "cores": threads,
-                                "kind": "oracle", "seconds": dt,
+                                "kind": "oracle", "seconds": dt, "cpu_model": cpu_model(),
                                 "sample": f"{len(cols)} whole output columns of the 8192^3 "
-                                          "product (FP64 triple loop + bound denominator)"}
+                                          "product (FP64 triple loop + bound denominator)",
+                                "single_thread_1024": {"seconds": t1,
+                                                       "tflops": 2.0 * 1024 ** 3 / t1 / 1e12}}
         # accuracy of every arm on the sampled columns (GPU FP64 error report)
         idx = torch.from_numpy(cols).to(dev)
         C64_d = torch.from_numpy(np.ascontiguousarray(C64.T)).to(dev).t()

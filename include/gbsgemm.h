@@ -430,6 +430,16 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
                     int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
                     int64_t ldb, void *workspace, size_t ws_bytes, void *stream);
 
+/* Measurement aid (the paper has no counterpart): enqueues one launch of
+ * an FP32 FMA throughput kernel (8 blocks of 256 threads per SM, 128
+ * independent fused multiply-adds per thread per iteration) on `stream` and
+ * writes the number of FMAs it performs to *fmas. The caller times it (CUDA
+ * events) to measure the FP32 SIMT roofline: 2 * fmas / time. `sink` is a
+ * device buffer of at least 256 floats (written only to keep the work
+ * live). */
+GB_API int gb_measure_ffma(gb_handle_t h, int64_t iterations, float *sink, int64_t *fmas,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ SIGNATURES = {
                                       ctypes.POINTER(c_size)], c_int),
     "gb_sgemm_host": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64, c_f, c_vp, c_i64, c_vp,
                        c_i64, c_f, c_vp, c_i64, c_vp, c_size, c_vp], c_int),
+    "gb_measure_ffma": ([c_vp, c_i64, c_vp, ctypes.POINTER(c_i64), c_vp], c_int),
     "gb_ssyrk_workspace_size": ([c_int, c_char, c_char, c_i64, c_i64, ctypes.POINTER(c_size)],
                                 c_int),
     "gb_ssyrk": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_f, c_vp, c_i64, c_f, c_vp, c_i64,
