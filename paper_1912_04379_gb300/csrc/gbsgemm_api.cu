@@ -267,6 +267,7 @@ GB_API int gb_destroy(gb_handle_t h) {
     if (h->magic != kHandleMagic) return GB_ERR_HANDLE;
     cudaDeviceSynchronize();
     gb::destroy_pipe(h);
+    gb::destroy_side(h);
     cudaFree(h->dstate);
     h->magic = 0;
     delete h;

@@ -47,6 +47,11 @@ struct gb_handle_s {
     bool pipe_ready;
     cudaStream_t pipe_stream[3];
     cudaEvent_t pipe_event[8];
+    // grouped runs: a side stream for the SIMT part, forked from and joined
+    // to the caller's stream (created when a plan has both parts)
+    bool side_ready;
+    cudaStream_t side_stream;
+    cudaEvent_t side_event[2];
 };
 
 namespace gb {
@@ -54,6 +59,7 @@ namespace gb {
 constexpr int kHandleMagic = 0x6b5e3a21;
 constexpr int kPipeEvents = 8;
 void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events
+void destroy_side(gb_handle_t h);     // releases the grouped runs' side stream and events
 
 // ------------------------------------------------------------------ SIMT --
 struct SimtArgs {
