@@ -115,7 +115,8 @@ cudaError_t pack_operand(int mode, bool a_side, bool trans, int64_t mn, int64_t 
 
 int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, float alpha,
                    const void *Ap, const void *Bp, float beta, float *C, int64_t ldc,
-                   cudaStream_t s, float *part = nullptr, int splits = 1) {
+                   cudaStream_t s, float *part = nullptr, int splits = 1,
+                   const EpiOp *epi = nullptr) {
     const int64_t kpad = split_kpad(mode, k);
     TcArgs t{};
     t.mode = mode;
@@ -129,6 +130,7 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     t.dstate = h->dstate;
     t.wait_limit = h->wait_limit;
     t.sm_count = h->sm_count;
+    if (epi) t.epi = *epi;
     cudaError_t e = launch_tc_sgemm(t, s);
     return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
 }
@@ -183,6 +185,37 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     return compute_packed(h, mode, m, n, k, alpha, Ap, Bp, beta, C, ldc, s,
                           splits > 1 ? reinterpret_cast<float *>(Pp) : nullptr, splits);
 }
+
+}  // namespace
+
+int gb::sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_t n,
+                  int64_t k, float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                  float beta, float *C, int64_t ldc, const EpiOp &op, void *ws, size_t ws_bytes,
+                  cudaStream_t s, bool *fused) {
+    *fused = false;
+    int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, ldc);
+    if (rc) return rc;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if ((rc = check_handle(h))) return rc;
+    const int mode = (alpha == 0.f || k == 0) ? -1 : split_mode(resolve_algo(algo, k));
+    const bool can_fuse = op.kind != 0 && m > 0 && n > 0 && A && B && C && (mode == 1 || mode == 2) &&
+                          split_k_factor(mode, m, n, k) == 1;
+    if (!can_fuse)
+        return sgemm_impl(h, algo, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws,
+                          ws_bytes, s);
+    const size_t need = split_ws_bytes(mode, m, n, k);
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
+    char *Ap = static_cast<char *>(ws);
+    char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
+    cudaError_t e = pack_operand(mode, true, is_trans(ta), m, k, A, lda, Ap, s);
+    if (e == cudaSuccess) e = pack_operand(mode, false, is_trans(tb), n, k, B, ldb, Bp, s);
+    if (e != cudaSuccess) return GB_ERR_CUDA;
+    rc = compute_packed(h, mode, m, n, k, alpha, Ap, Bp, beta, C, ldc, s, nullptr, 1, &op);
+    if (rc == GB_OK) *fused = true;
+    return rc;
+}
+
+namespace {
 
 // Backward products (see gb_sgemm_backward in the header for the formulas).
 struct BwdCall {

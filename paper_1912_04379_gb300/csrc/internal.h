@@ -92,6 +92,18 @@ cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k,
                               int64_t part_stride_elems, cudaStream_t s);
 
 // -------------------------------------------------- tensor-core kernel ---
+// Elementwise operation fused into the tensor-core epilogue, applied to
+// v = alpha*acc + beta*C at output element (i, j) before it is stored:
+//   kind 1: v <- act(v + bias[i])    (act = tanh or the identity)
+//   kind 2: v <- v * (1 - aux_ij^2)  (aux: M x N column-major, ld = ldaux)
+struct EpiOp {
+    int kind = 0;
+    int tanh_act = 0;
+    const float *bias = nullptr;
+    const float *aux = nullptr;
+    int64_t ldaux = 0;
+};
+
 struct TcArgs {
     int mode;                   // as launch_split_pack
     int64_t m, n, k, kpad;
@@ -105,7 +117,9 @@ struct TcArgs {
     DeviceState *dstate;
     int64_t wait_limit;
     int sm_count;
+    EpiOp epi;                  // kind != 0: BF16 x 2 or x 3 terms, no split-K
 };
+// cudaErrorNotSupported: an epilogue operation with another mode or split-K.
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s);
 // Number of K slices gb_sgemm uses for a split-precision problem (depends on
 // the shape only, so workspace sizes do not depend on the device).
@@ -182,6 +196,15 @@ struct TcSyrkArgs {
     int64_t wait_limit;         // microseconds
 };
 cudaError_t launch_tc_syrk(const TcSyrkArgs &a, cudaStream_t s);
+
+// gb_sgemm followed by the elementwise operation `op` fused into the
+// tensor-core epilogue when the resolved algorithm is BF16 x 2 or x 3 terms
+// and K is not split (*fused = true); otherwise plain gb_sgemm, and the
+// caller applies `op` itself (*fused = false). Same workspace as gb_sgemm.
+int sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_t n, int64_t k,
+              float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+              float *C, int64_t ldc, const EpiOp &op, void *ws, size_t ws_bytes, cudaStream_t s,
+              bool *fused);
 
 // AUTO's choice for a given K, and the split mode of an algorithm (-1: SIMT).
 gb_algo_t resolve_algo(gb_algo_t algo, int64_t k);

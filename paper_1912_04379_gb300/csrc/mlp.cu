@@ -3,14 +3,18 @@
 // Sec. 4). Examples are columns: X is n_0 x B, layer l has weights W_l
 // (n_l x n_{l-1}, column-major, ld = n_l), bias b_l and output H_l (n_l x B).
 //
-//   forward   H_l = phi_l(W_l H_{l-1} + b_l 1^T)        sgemm + bias_act
+//   forward   H_l = phi_l(W_l H_{l-1} + b_l 1^T)        sgemm, bias + act in its epilogue
 //   loss      E = sum (H_L - Y)^2 / (2B),  G_L = (H_L - Y) / B
-//   backward  G_{l-1} = (W_l^T G_l) * phi'(H_{l-1})     sgemm + tanh_grad
+//   backward  G_{l-1} = (W_l^T G_l) * phi'(H_{l-1})     sgemm, * (1 - H^2) in its epilogue
 //             W_l <- W_l - lr G_l H_{l-1}^T               one sgemm, alpha = -lr, beta = 1
 //             b_l <- b_l - lr G_l 1                       bias_partial + bias_apply
 //
 // The weight update is the gradient GEMM itself (beta = 1 on W_l), so no
 // gradient matrix is stored. G_{l-1} is formed before W_l is overwritten.
+// The bias/activation and the tanh' factor run in the tensor-core GEMM's
+// epilogue when the algorithm resolves to BF16 x 2 or x 3 terms without
+// split-K (rounding exactly as the separate passes); otherwise bias_act and
+// tanh_grad run as passes of their own.
 // Every elementwise pass is a grid-stride, HBM-bound kernel; every reduction
 // (loss, bias) sums in a fixed order, so a step is deterministic on a device.
 #include <stdint.h>
@@ -190,12 +194,21 @@ int forward(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t *d, const float *
     for (int64_t l = 0; l < L; ++l) {
         const int64_t m = d->widths[l + 1], k = d->widths[l];
         const float *prev = l ? H[l - 1] : X;
-        int rc = gb_sgemm(h, algo, 'N', 'N', m, B, k, 1.f, W[l], m, prev, k, 0.f, H[l], m, ws,
-                          ws_bytes, s);
+        const int tanh_act = (l < L - 1 && d->hidden == GB_ACT_TANH) ? 1 : 0;
+        // bias and activation in the GEMM's epilogue where the tensor-core
+        // kernel can take them, else a separate pass
+        EpiOp op;
+        op.kind = 1;
+        op.tanh_act = tanh_act;
+        op.bias = b[l];
+        bool fused = false;
+        int rc = sgemm_epi(h, algo, 'N', 'N', m, B, k, 1.f, W[l], m, prev, k, 0.f, H[l], m, op, ws,
+                           ws_bytes, s, &fused);
         if (rc) return rc;
+        if (fused) continue;
         const int64_t total = m * B;
-        bias_act_kernel<<<grid_for(total, h->sm_count), kThreads, 0, s>>>(
-            m, total, H[l], b[l], (l < L - 1 && d->hidden == GB_ACT_TANH) ? 1 : 0);
+        bias_act_kernel<<<grid_for(total, h->sm_count), kThreads, 0, s>>>(m, total, H[l], b[l],
+                                                                          tanh_act);
         if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
     }
     return GB_OK;
@@ -272,11 +285,17 @@ GB_API int gb_mlp_train_step(gb_handle_t h, gb_algo_t algo, const gb_mlp_desc_t 
         const int64_t m = desc->widths[l + 1], k = desc->widths[l];
         const float *prev = l ? H[l - 1] : X;
         if (l > 0) {
-            // G_{l-1} = W_l^T G_l (with the weights before this step's update)
-            rc = gb_sgemm(h, algo, 'T', 'N', k, B, m, 1.f, W[l], m, G[l], m, 0.f, G[l - 1], k,
-                          ws, p.gemm_ws, s);
+            // G_{l-1} = W_l^T G_l (with the weights before this step's update),
+            // times tanh' = 1 - H_{l-1}^2 in the epilogue where possible
+            EpiOp op;
+            op.kind = desc->hidden == GB_ACT_TANH ? 2 : 0;
+            op.aux = H[l - 1];
+            op.ldaux = k;
+            bool fused = false;
+            rc = sgemm_epi(h, algo, 'T', 'N', k, B, m, 1.f, W[l], m, G[l], m, 0.f, G[l - 1], k, op,
+                           ws, p.gemm_ws, s, &fused);
             if (rc) return rc;
-            if (desc->hidden == GB_ACT_TANH) {
+            if (desc->hidden == GB_ACT_TANH && !fused) {
                 const int64_t total = k * B;
                 tanh_grad_kernel<<<grid_for(total, h->sm_count), kThreads, 0, s>>>(total, G[l - 1],
                                                                                   H[l - 1]);

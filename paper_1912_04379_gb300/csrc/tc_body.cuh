@@ -39,6 +39,7 @@ struct Cfg {
 template <int BN, int BK>
 struct GroupSource {
     static constexpr bool kTri = false;
+    static constexpr int kEpi = 0;
     const TcProblem *probs;
     const TcItem *items;
     int64_t nitems;
@@ -210,8 +211,11 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             tc_fence_after();
             UnitInfo ui;
             src.unit(u, ui);
-            store_tile<CF::BN, Src::kTri>(ui, tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN),
-                               q, lane);
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::BN);
+            if constexpr (Src::kEpi != 0)
+                store_tile_epi<CF::BN, Src::kEpi>(ui, taddr, q, lane, src.ep);
+            else
+                store_tile<CF::BN, Src::kTri>(ui, taddr, q, lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(acc));

@@ -262,9 +262,11 @@ struct UnitInfo {
 // One GEMM: units are (tile, K slice) pairs in the grouped raster order.
 // Split units write raw partial sums to `part` (slice s at part + s*M*N,
 // column-major, ld = M); a separate pass reduces them.
-template <int BN, int BK>
+template <int BN, int BK, int EPI = 0>
 struct SingleSource {
     static constexpr bool kTri = false;
+    static constexpr int kEpi = EPI;
+    EpiOp ep;                     // the fused elementwise operation (EPI != 0)
     const CUtensorMap *ma, *mb;
     int64_t M, N, K;
     float alpha, beta;
@@ -363,6 +365,53 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
             if (j >= jlo && j < jhi)
                 *p = rd ? fmaf(a, __uint_as_float(r[j]), beta * cv[j]) : a * __uint_as_float(r[j]);
             p += ldd;
+        }
+    }
+}
+
+// Epilogue with a fused elementwise operation (EPI = EpiOp::kind, see
+// internal.h) after v = alpha*acc + beta*C; whole-K results only (no
+// split-K). The operations round exactly as the separate passes would:
+// kind 1 adds the bias in FP32 then applies tanhf; kind 2 multiplies by
+// fmaf(-h, h, 1).
+template <int BN, int EPI>
+__device__ __forceinline__ void store_tile_epi(const UnitInfo &ui, uint32_t taddr, int q, int lane,
+                                               const EpiOp &ep) {
+    const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
+    const float alpha = ui.alpha, beta = ui.beta;
+    const bool empty = ui.kb0 >= ui.kb1;
+    const int64_t row = ui.tm * BM + q * 32 + lane;
+    const int64_t col0 = ui.tn * BN;
+    const bool row_ok = row < M;
+    const bool rd = beta != 0.f;
+    const float bias = (EPI == 1 && row_ok) ? ep.bias[row] : 0.f;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c, r);
+        tmem_wait16(r);
+        if (!row_ok) continue;
+        const int ncol = (int)(N - (col0 + c) < 16 ? N - (col0 + c) : 16);
+        float *p = ui.dst + row + (col0 + c) * ldd;
+        const float *ax = EPI == 2 ? ep.aux + row + (col0 + c) * ep.ldaux : nullptr;
+        float cv[16], hv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            cv[j] = (rd && j < ncol) ? p[j * ldd] : 0.f;
+            hv[j] = (EPI == 2 && j < ncol) ? ax[j * ep.ldaux] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j >= ncol) continue;
+            const float acc = empty ? 0.f : __uint_as_float(r[j]);
+            float v = rd ? fmaf(alpha, acc, beta * cv[j]) : alpha * acc;
+            if (EPI == 1) {
+                v = v + bias;
+                if (ep.tanh_act) v = tanhf(v);
+            } else if (EPI == 2) {
+                v = v * fmaf(-hv[j], hv[j], 1.f);
+            }
+            p[j * ldd] = v;
         }
     }
 }

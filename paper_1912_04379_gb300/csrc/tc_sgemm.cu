@@ -45,18 +45,19 @@ namespace gb {
 namespace {
 
 using namespace tcx;
-template <int MODE, int RB>
+template <int MODE, int RB, int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
                 int64_t ldc, float *__restrict__ part, int splits, DeviceState *dstate,
-                uint64_t limit_ns) {
+                uint64_t limit_ns, EpiOp ep) {
     using CF = Cfg<MODE, RB>;
     if (threadIdx.x == 0) {
         prefetch_tmap(&mapA);
         prefetch_tmap(&mapB);
     }
-    SingleSource<CF::BN, CF::BK> src;
+    SingleSource<CF::BN, CF::BK, EPI> src;
+    src.ep = ep;
     src.ma = &mapA; src.mb = &mapB;
     src.M = M; src.N = N; src.K = K;
     src.alpha = alpha; src.beta = beta;
@@ -126,7 +127,7 @@ bool make_map(CUtensorMap *map, bool tf32, const void *ptr, int64_t k, int64_t r
     return r == CUDA_SUCCESS;
 }
 
-template <int MODE, int RB>
+template <int MODE, int RB, int EPI = 0>
 cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     using CF = Cfg<MODE, RB>;
     static bool attr_done[64] = {};
@@ -134,7 +135,7 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<MODE, RB>,
+        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<MODE, RB, EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
@@ -153,9 +154,10 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     int grid = a.sm_count > 0 ? a.sm_count : 1;
     if (units < grid) grid = (int)units;
     const uint64_t limit_ns = (uint64_t)a.wait_limit * 1000ull;
-    tc_sgemm_kernel<MODE, RB><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+    if (EPI != 0 && splits > 1) return cudaErrorNotSupported;
+    tc_sgemm_kernel<MODE, RB, EPI><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
         ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, splits > 1 ? a.part : nullptr, splits,
-        a.dstate, limit_ns);
+        a.dstate, limit_ns, a.epi);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
@@ -236,6 +238,17 @@ cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
         return (v == 64 || v == 128) ? v : 0;
     }();
     const bool rb128 = forced ? forced == 128 : a.k <= 2048;
+    if (a.epi.kind != 0) {
+        // fused elementwise operations: BF16 x 2 terms and x 3 terms (6 products)
+        const int key = a.mode * 10 + a.epi.kind;
+        switch (key) {
+            case 11: return rb128 ? launch_mode<1, 128, 1>(a, s) : launch_mode<1, 64, 1>(a, s);
+            case 12: return rb128 ? launch_mode<1, 128, 2>(a, s) : launch_mode<1, 64, 2>(a, s);
+            case 21: return rb128 ? launch_mode<2, 128, 1>(a, s) : launch_mode<2, 64, 1>(a, s);
+            case 22: return rb128 ? launch_mode<2, 128, 2>(a, s) : launch_mode<2, 64, 2>(a, s);
+            default: return cudaErrorNotSupported;
+        }
+    }
     switch (a.mode) {
         case 0: return rb128 ? launch_mode<0, 128>(a, s) : launch_mode<0, 64>(a, s);
         case 1: return rb128 ? launch_mode<1, 128>(a, s) : launch_mode<1, 64>(a, s);

@@ -22,6 +22,7 @@ using namespace tcx;
 template <int BN, int BK>
 struct TriSource {
     static constexpr bool kTri = true;
+    static constexpr int kEpi = 0;
     static constexpr int R = BN / BM;
     const CUtensorMap *ma, *mb;
     int64_t n;
