@@ -279,3 +279,37 @@ def test_bf16x9_split_k():
     cols = np.unique(np.r_[0, 1, 999, 1999, np.random.default_rng(45).integers(0, 2000, 8)])
     assert_within_bound(p, got, cols=cols)
     check_padding(p, got)
+
+
+# ------------------------------------------------- tile-count independence --
+
+@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6"))
+def test_result_does_not_depend_on_the_tile_count(algo):
+    """Each output element accumulates the same K sequence whatever the number
+    of tiles (and so whatever tiles land in the persistent grid's last
+    round): two problems that differ only in N agree bit for bit on their
+    common columns."""
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    m, k = 4096, 512
+    bn = 256 if algo == "bf16x3" else 128
+    n_wide = 20 * bn                              # 32 x 20 tiles of 128 x 256 (or 40 x 128)
+    n_narrow = 19 * bn
+    g = torch.Generator(device="cuda").manual_seed(42)
+    A = (torch.rand((k, m), device="cuda", generator=g) * 2 - 1).t()
+    B = (torch.rand((n_wide, k), device="cuda", generator=g) * 2 - 1).t()
+    outs = []
+    for n in (n_wide, n_narrow):
+        C = gb.colmajor(m, n)
+        gb.sgemm(A, B[:, :n], C, algo=algo)
+        torch.cuda.synchronize()
+        outs.append(C)
+    assert torch.equal(outs[0][:, :n_narrow], outs[1])
+    # and the wide result (tail units included) is within the bound
+    p = wl.Problem("N", "N", m, n_wide, k, 1.0, 0.0,
+                   np.asfortranarray(A.cpu().numpy()), m,
+                   np.asfortranarray(B.cpu().numpy()), k,
+                   np.zeros((m, n_wide), dtype=np.float32, order="F"), m)
+    got = np.asfortranarray(outs[0].cpu().numpy())
+    cols = np.r_[n_wide - bn:n_wide:7, 0:3]
+    assert_within_bound(p, got, cols=cols, algo=algo)
