@@ -242,7 +242,9 @@ typedef struct {
  *  GB_ALGO_AUTO  per problem: an autotuner (run once per handle, timing
  *                synthetic groups) routes each size class to SIMT or the
  *                tensor cores; tensor-core problems take SPLIT_BF16X3 when
- *                K >= 1024, else SPLIT_BF16X6;
+ *                K >= 1024 (if those fill at least one round of the
+ *                persistent grid, else they join the next), else
+ *                SPLIT_BF16X6;
  *  a split algo  the preferred split for every problem with K >= 4; a
  *                problem whose K is below that split's threshold (see
  *                gb_algo_t) takes SPLIT_BF16X6 instead.

@@ -316,14 +316,33 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
     struct TcPending { size_t prob; size_t off_a, off_b; int mode; };
     std::vector<TcPending> tcs;
     size_t packed_bytes = 0;
+    auto route = [&](const gb_gemm_problem_t &p, bool scale_only) {
+        return (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
+                                       : choice[size_class(p.m, p.n, p.k)];
+    };
+    // Under AUTO, the BF16 x 2 terms problems (K >= 1024) get a launch of
+    // their own only if they fill at least one round of the persistent grid;
+    // fewer tiles join the BF16 x 3 terms launch (which meets the bound too),
+    // since a nearly empty extra launch costs more than the extra products.
+    bool x2_own_launch = true;
+    if (pref == kPrefAuto) {
+        int64_t x2_tiles = 0;
+        for (const gb_gemm_problem_t &p : ps) {
+            const bool so = p.alpha == 0.f || p.k == 0;
+            if (p.m == 0 || p.n == 0 || so || route(p, so) != 2 || tc_mode_for(pref, p.k) != 1)
+                continue;
+            x2_tiles += ((p.m + 127) / 128) * ((p.n + tc_tile_n(1) - 1) / tc_tile_n(1));
+        }
+        x2_own_launch = x2_tiles >= h->sm_count;
+    }
     for (size_t i = 0; i < ps.size(); ++i) {
         const gb_gemm_problem_t &p = ps[i];
         const bool scale_only = p.alpha == 0.f || p.k == 0;
         if (p.m == 0 || p.n == 0 || (scale_only && p.beta == 1.f)) continue;
-        const int ch = (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
-                                               : choice[size_class(p.m, p.n, p.k)];
+        const int ch = route(p, scale_only);
         if (ch == 2) {
-            const int mode = tc_mode_for(pref, p.k);
+            int mode = tc_mode_for(pref, p.k);
+            if (mode == 1 && !x2_own_launch) mode = 2;
             const size_t kpad = (size_t)split_kpad(mode, p.k);
             const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
             TcPending t{i, packed_bytes, 0, mode};
