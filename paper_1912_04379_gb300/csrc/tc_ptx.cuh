@@ -321,6 +321,44 @@ __device__ __forceinline__ void store_tile(const UnitInfo &ui, uint32_t taddr, i
     if (TRI)   // the whole tile inside the triangle
         interior = interior && (ui.lower ? col0 + BN - 1 <= ui.tm * BM : col0 >= ui.tm * BM + BM - 1);
     float *colp = dst + row + col0 * ldd;
+    if (interior && !part && beta != 0.f) {
+        // C of the next 16 columns is requested before this chunk's TMEM
+        // wait and stores, so its latency overlaps them: one memory round
+        // trip per tile instead of one per chunk. (Every load of a chunk is
+        // issued before the previous chunk's stores, which a store could
+        // otherwise alias.)
+        float cv[16];
+        {
+            const float *qc = colp;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) { cv[j] = *qc; qc += ldd; }
+        }
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(taddr + (uint32_t)c, r);
+            float cn[16];
+            if (c + 16 < BN) {
+                const float *qn = colp + (c + 16) * ldd;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { cn[j] = *qn; qn += ldd; }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cn[j] = 0.f;
+            }
+            tmem_wait16(r);
+            if (empty) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r[j] = 0u;
+            }
+            float *p = colp + c * ldd;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) { *p = fmaf(a, __uint_as_float(r[j]), beta * cv[j]); p += ldd; }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cv[j] = cn[j];
+        }
+        return;
+    }
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
         uint32_t r[16];
