@@ -413,7 +413,10 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
                     float alpha, const float *A, int64_t lda, float beta, float *C, int64_t ldc,
                     void *workspace, size_t ws_bytes, void *stream);
 
-/* Workspace bytes of gb_strsm with these arguments. */
+/* Workspace bytes of gb_strsm with these arguments: the GEMM updates' need
+ * (256-byte rounded) plus 68,096 bytes per 128 rows of A's diagonal, where
+ * each diagonal block's triangle and diagonal reciprocals are laid out once
+ * per call for the substitution kernels. */
 GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char transa, char diag,
                                    int64_t m, int64_t n, size_t *bytes);
 
@@ -427,7 +430,9 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
  * Recursion by halving: each level's off-diagonal block update is one
  * gb_sgemm call with `algo` (alpha = -1, beta = 1), and the diagonal blocks
  * (at most 128 rows) are solved by substitution in FP32, with each diagonal
- * entry's reciprocal rounded once per block. */
+ * entry's reciprocal rounded once. `workspace` (16-byte aligned, at least
+ * gb_strsm_workspace_size bytes) is always needed when m, n > 0 and alpha != 0;
+ * otherwise GB_ERR_WORKSPACE. */
 GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
                     int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
                     int64_t ldb, void *workspace, size_t ws_bytes, void *stream);

@@ -10,10 +10,10 @@
 //   SSYRK  leaves: every diagonal block's triangle in ONE launch of a small
 //          FP32 SIMT kernel (64 x 64 tiles, the tiles above or below the
 //          diagonal skipped).
-//   STRSM  leaves: forward/backward substitution in one kernel per leaf, the
-//          leaf's op(A) block in shared memory; left side: each warp solves
-//          four columns of B at once (lanes over rows), right side: four rows
-//          (lanes over columns, the rows staged through shared memory).
+//   STRSM  leaves: substitution in one kernel per leaf, the leaf's triangle
+//          in shared memory; 32 columns (left) or rows (right) of B per CTA,
+//          one per lane, each warp owning 16 rows of the solve and taking
+//          the earlier warps' solved rows as named barriers release them.
 //          Leaves depend on one another through the GEMM updates, so they
 //          run in order.
 // X overwrites B in STRSM after B <- alpha B. Each GEMM update is
@@ -101,231 +101,249 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 
 // ------------------------------------------------------------- STRSM leaves
 
-constexpr int kLeafCols = 4;     // columns (left) or rows (right) per warp
-constexpr int kRightRows = 8 * kLeafCols;   // rows of B per CTA, right side
+// A leaf solves M x = b for every vector of B, with M the s x s diagonal
+// block (s <= 128) of op(A) (left side; the vectors are the columns of B) or
+// of op(A)^T (right side, X op(A) = B read as op(A)^T x = b; the vectors are
+// the rows of B). It is put in forward lower form L' x' = b': L' = M and
+// x' = x when M is lower, else L'(i, j) = M(s-1-i, s-1-j) and x'_i = x_{s-1-i}.
+// Then x'_i = (b'_i - sum over j < i of L'(i, j) x'_j) / L'(i, i), i ascending.
+//
+// A CTA holds 32 vectors (one per lane) and eight warps; warp q owns rows
+// [16q, 16q + 16) of every vector in registers. It subtracts the products of
+// each earlier row block p as soon as warp p has solved it (p ascending,
+// columns ascending within a block, so every x'_i accumulates its terms in
+// j order), then solves its own 16 x 16 diagonal block. Solved blocks pass
+// from warp to warp through shared memory, released by named barriers (warp
+// p arrives on barrier p + 1, the warps after it wait on it). Only entries
+// with j < i are ever multiplied, so a non-finite b'_j reaches exactly the
+// x'_i that depend on it.
+constexpr int kBlk = 16;                       // rows per warp block
+constexpr int kLeafWarps = kLeaf / kBlk;       // 8
+constexpr int kLeafThreads = 32 * kLeafWarps;
+constexpr int kVecs = 32;                      // vectors per CTA
+constexpr int kSP = 132;                       // stride of L's columns and of each vector
+constexpr int kPrepFloats = kLeaf * kSP + kLeaf;                    // one leaf's L' and D
+constexpr size_t kPrepBytes = (size_t)kPrepFloats * sizeof(float);  // 68,096
+constexpr int kRawStride = kLeaf + 1;                                // prep's staging tile
 
-// Loads op(A)'s s x s leaf block at (r0, r0) into shared memory: T[j*s + i]
-// (COLMAJOR) or T[i*s + j], 0 outside the triangle, 1 on a unit diagonal
-// (not read), and the reciprocals of the diagonal into D[0 .. s). Each warp
-// takes stored columns w, w + 8, ... of the leaf, four at a time, with its
-// lanes over stored rows (coalesced; sixteen independent loads per lane in
-// flight).
-template <bool COLMAJOR>
-__device__ __forceinline__ void load_leaf(float *T, float *D, int s, const float *__restrict__ A,
-                                          int64_t lda, int64_t r0, int trans, int tlower,
-                                          int unit) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b0 = warp; b0 < s; b0 += 32) {
-        float v[4][4];
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Builds every leaf's L' and D once per call, one CTA per leaf (rows
+// [128 b, 128 b + s) of op(A)'s diagonal), into prep[b * kPrepFloats ..]:
+// L'(i, j) at [j * kSP + i] for j < i < s and 0 elsewhere, then D[i] =
+// 1 / L'(i, i) (1 for a unit diagonal and for padding rows). The stored
+// block's triangle is read coalesced into shared memory, then written out in
+// L' order, also coalesced. The stored (sr, sc) is M(sr, sc), or M(sc, sr)
+// when exactly one of (right side, transposed op) holds; L'(i, j) is M(i, j),
+// or M(s-1-i, s-1-j) when M is upper.
+template <bool LEFT>
+__global__ void __launch_bounds__(kLeafThreads)
+trsm_leaf_prep_kernel(int64_t ms, const float *__restrict__ A, int64_t lda, int trans,
+                      int tlower, int unit, float *__restrict__ prep) {
+    extern __shared__ float R[];                  // R[sc * kRawStride + sr] = stored (sr, sc)
+    const int64_t r0 = (int64_t)blockIdx.x * kLeaf;
+    const int s = (int)(ms - r0 < kLeaf ? ms - r0 : kLeaf);
+    const bool rev = LEFT ? tlower == 0 : tlower != 0;
+    const bool swap = LEFT == (trans != 0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int sc = warp; sc < s; sc += kLeafWarps) {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int bcol = b0 + 8 * g;
-            const float *src = A + r0 + (r0 + bcol) * lda;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int a = lane + 32 * r;             // stored row
-                const int i = trans ? bcol : a, j = trans ? a : bcol;
-                const bool inside = bcol < s && a < s && (tlower ? i >= j : i <= j) &&
-                                    !(unit && i == j);
-                v[g][r] = inside ? src[a] : 0.f;
-            }
+        for (int k = 0; k < kLeaf / 32; ++k) {
+            const int sr = lane + 32 * k;
+            const int mi = swap ? sc : sr, mj = swap ? sr : sc;
+            const int i = rev ? s - 1 - mi : mi, j = rev ? s - 1 - mj : mj;
+            if (sr < s && (i > j || (i == j && !unit)))
+                R[sc * kRawStride + sr] = A[(r0 + sr) + (r0 + sc) * lda];
         }
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int bcol = b0 + 8 * g;
-            if (bcol >= s) break;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int a = lane + 32 * r;
-                if (a >= s) break;
-                const int i = trans ? bcol : a, j = trans ? a : bcol;
-                const float x = (unit && i == j) ? 1.f : v[g][r];
-                T[COLMAJOR ? j * s + i : i * s + j] = x;
-                if (i == j) D[i] = unit ? 1.f : 1.f / x;
-            }
+    }
+    __syncthreads();
+    float *out = prep + (int64_t)blockIdx.x * kPrepFloats;
+    for (int e = tid; e < kLeaf * kSP; e += kLeafThreads) {
+        const int j = e / kSP, i = e - j * kSP;
+        float v = 0.f;
+        if (i < s && j < i) {
+            const int mi = rev ? s - 1 - i : i, mj = rev ? s - 1 - j : j;
+            const int sr = swap ? mj : mi, sc = swap ? mi : mj;
+            v = R[sc * kRawStride + sr];
         }
+        out[e] = v;
+    }
+    if (tid < kLeaf) {
+        float d = 1.f;
+        if (tid < s && !unit) {
+            const int mi = rev ? s - 1 - tid : tid;
+            d = 1.f / R[mi * kRawStride + mi];
+        }
+        out[kLeaf * kSP + tid] = d;
     }
 }
 
-// op(A)_leaf X = B_leaf for the s <= 128 rows r0 .. r0+s of B. Each warp
-// solves kLeafCols columns at once (independent chains for ILP); lanes hold
-// rows lane + 32r. Column-oriented substitution: x_j = b_j * (1 / t_jj), then
-// b_i -= t_ij x_j for the rows still to solve, j in dependency order. (The
-// reciprocal, rounded once per leaf, perturbs t_jj by at most one rounding,
-// as in the reference BLAS's right-side STRSM; a division per step and
-// column made the leaf instruction-bound.)
-__global__ void __launch_bounds__(256)
-trsm_left_leaf_kernel(int s, int64_t n, const float *__restrict__ A, int64_t lda, int64_t r0,
-                      int trans, int tlower, int unit, float *__restrict__ B, int64_t ldb) {
-    extern __shared__ float T[];
-    float *D = T + s * s;
-    load_leaf<true>(T, D, s, A, lda, r0, trans, tlower, unit);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t col0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * kLeafCols;
-    if (col0 >= n) return;
-    float b[kLeafCols][4];
+// The leaf at rows (left) or columns (right) [r0, r0 + s) of B, its L' and D
+// prepared in prep (kPrepFloats, 16-byte aligned).
+template <bool LEFT>
+__global__ void __launch_bounds__(kLeafThreads, 2)
+trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__restrict__ prep,
+                 float *__restrict__ B, int64_t ldb) {
+    extern __shared__ __align__(16) float smem[];
+    float *S = smem;                      // L' column-major: S[j * kSP + i] = L'(i, j), i > j
+    float *D = S + kLeaf * kSP;           // D[i] = 1 / L'(i, i)
+    float *X = D + kLeaf;                 // X[v * kSP + i] = b'_i, then x'_i, of vector v
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool rev = LEFT ? tlower == 0 : tlower != 0;    // M upper
+    const int64_t v0 = (int64_t)blockIdx.x * kVecs;
+
+    for (int e = tid; e < kPrepFloats / 4; e += kLeafThreads)
+        cp_async16(S + 4 * e, prep + 4 * e);                // L' and D, in flight
+    // b': the leaf's rows (left) or columns (right) of B, coalesced
+    if (LEFT) {
 #pragma unroll
-    for (int q = 0; q < kLeafCols; ++q)
+        for (int g = 0; g < kVecs / kLeafWarps; ++g) {
+            const int v = warp + kLeafWarps * g;
+            float t[kLeaf / 32];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = lane + 32 * r;
-            b[q][r] = (col0 + q < n && i < s) ? B[r0 + i + (col0 + q) * ldb] : 0.f;
-        }
-    if (tlower) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = 32 * r + jj;
-                if (j >= s) break;
-                const float d = D[j];
-                float x[kLeafCols];
-#pragma unroll
-                for (int q = 0; q < kLeafCols; ++q) {
-                    const float bj = __shfl_sync(0xffffffffu, b[q][r], jj);
-                    x[q] = bj * d;
-                    if (lane == jj) b[q][r] = x[q];
-                }
-#pragma unroll
-                for (int rr = r; rr < 4; ++rr) {
-                    const int i = lane + 32 * rr;
-                    if (i > j && i < s) {
-                        const float t = T[j * s + i];
-#pragma unroll
-                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-t, x[q], b[q][rr]);
-                    }
-                }
+            for (int k = 0; k < kLeaf / 32; ++k) {
+                const int i = lane + 32 * k;
+                const int row = rev ? s - 1 - i : i;
+                t[k] = (i < s && v0 + v < nvec) ? B[r0 + row + (v0 + v) * ldb] : 0.f;
             }
+#pragma unroll
+            for (int k = 0; k < kLeaf / 32; ++k) X[v * kSP + lane + 32 * k] = t[k];
         }
     } else {
 #pragma unroll
-        for (int r = 3; r >= 0; --r) {
-            for (int jj = 31; jj >= 0; --jj) {
-                const int j = 32 * r + jj;
-                if (j >= s) continue;
-                const float d = D[j];
-                float x[kLeafCols];
+        for (int g = 0; g < kLeaf / kLeafWarps; g += 4) {
+            float t[4];
 #pragma unroll
-                for (int q = 0; q < kLeafCols; ++q) {
-                    const float bj = __shfl_sync(0xffffffffu, b[q][r], jj);
-                    x[q] = bj * d;
-                    if (lane == jj) b[q][r] = x[q];
-                }
-#pragma unroll
-                for (int rr = 0; rr <= r; ++rr) {
-                    const int i = lane + 32 * rr;
-                    if (i < j) {
-                        const float t = T[j * s + i];
-#pragma unroll
-                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-t, x[q], b[q][rr]);
-                    }
-                }
+            for (int k = 0; k < 4; ++k) {
+                const int i = warp + kLeafWarps * (g + k);
+                const int col = rev ? s - 1 - i : i;
+                t[k] = (i < s && v0 + lane < nvec) ? B[(v0 + lane) + (r0 + col) * ldb] : 0.f;
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) X[lane * kSP + warp + kLeafWarps * (g + k)] = t[k];
         }
     }
-#pragma unroll
-    for (int q = 0; q < kLeafCols; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = lane + 32 * r;
-            if (col0 + q < n && i < s) B[r0 + i + (col0 + q) * ldb] = b[q][r];
-        }
-}
+    cp_async_wait_all();
+    __syncthreads();
 
-// X op(A)_leaf = B_leaf for the s <= 128 columns c0 .. c0+s of B. A CTA
-// takes kRightRows rows, staged through shared memory (Bs[c][row], padded)
-// so that global accesses run along the rows; each warp then solves
-// kLeafCols rows at once with lanes over columns c = lane + 32r.
-__global__ void __launch_bounds__(256)
-trsm_right_leaf_kernel(int s, int64_t m, const float *__restrict__ A, int64_t lda, int64_t c0,
-                       int trans, int tlower, int unit, float *__restrict__ B, int64_t ldb) {
-    extern __shared__ float T[];
-    float *D = T + s * s;
-    float *Bs = D + kLeaf;                            // [s][kRightRows + 1]
-    constexpr int LDS = kRightRows + 1;
-    const int64_t row0 = (int64_t)blockIdx.x * kRightRows;
-    load_leaf<false>(T, D, s, A, lda, c0, trans, tlower, unit);
-    for (int e = threadIdx.x; e < s * kRightRows; e += blockDim.x) {
-        const int rl = e % kRightRows, c = e / kRightRows;
-        Bs[c * LDS + rl] = row0 + rl < m ? B[row0 + rl + (c0 + c) * ldb] : 0.f;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int rw = (threadIdx.x >> 5) * kLeafCols;     // this warp's first row in the CTA
-    float b[kLeafCols][4];
+    const int nblk = (s + kBlk - 1) / kBlk;
+    const int q = warp;
+    if (q < nblk) {                       // warp-uniform: every lane reaches each barrier
+        float x[kBlk];
+        const float4 *xq = reinterpret_cast<const float4 *>(X + lane * kSP + q * kBlk);
 #pragma unroll
-    for (int q = 0; q < kLeafCols; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int c = lane + 32 * r;
-            b[q][r] = c < s ? Bs[c * LDS + rw + q] : 0.f;
+        for (int g = 0; g < kBlk / 4; ++g) {
+            const float4 f = xq[g];
+            x[4 * g] = f.x; x[4 * g + 1] = f.y; x[4 * g + 2] = f.z; x[4 * g + 3] = f.w;
         }
-    if (!tlower) {          // op(A) upper: columns left to right
+#pragma unroll 1
+        for (int p = 0; p < q; ++p) {
+            named_bar_sync(1 + p, 32 * (nblk - p));       // block p solved
+            float y[kBlk];
+            const float4 *xp = reinterpret_cast<const float4 *>(X + lane * kSP + p * kBlk);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            for (int ii = 0; ii < 32; ++ii) {
-                const int i = 32 * r + ii;
-                if (i >= s) break;
-                const float d = D[i];
-                float x[kLeafCols];
+            for (int g = 0; g < kBlk / 4; ++g) {
+                const float4 f = xp[g];
+                y[4 * g] = f.x; y[4 * g + 1] = f.y; y[4 * g + 2] = f.z; y[4 * g + 3] = f.w;
+            }
 #pragma unroll
-                for (int q = 0; q < kLeafCols; ++q) {
-                    const float bi = __shfl_sync(0xffffffffu, b[q][r], ii);
-                    x[q] = bi * d;
-                    if (lane == ii) b[q][r] = x[q];
-                }
+            for (int c = 0; c < kBlk; ++c) {              // column p*16 + c of L'
+                const float4 *lc = reinterpret_cast<const float4 *>(S + (p * kBlk + c) * kSP +
+                                                                     q * kBlk);
 #pragma unroll
-                for (int rr = r; rr < 4; ++rr) {
-                    const int c = lane + 32 * rr;
-                    if (c > i && c < s) {
-                        const float t = T[i * s + c];
-#pragma unroll
-                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-x[q], t, b[q][rr]);
-                    }
+                for (int g = 0; g < kBlk / 4; ++g) {
+                    const float4 l = lc[g];
+                    x[4 * g] = fmaf(-l.x, y[c], x[4 * g]);
+                    x[4 * g + 1] = fmaf(-l.y, y[c], x[4 * g + 1]);
+                    x[4 * g + 2] = fmaf(-l.z, y[c], x[4 * g + 2]);
+                    x[4 * g + 3] = fmaf(-l.w, y[c], x[4 * g + 3]);
                 }
             }
         }
-    } else {                // op(A) lower: columns right to left
+        float d[kBlk];
+        const float4 *dq = reinterpret_cast<const float4 *>(D + q * kBlk);
 #pragma unroll
-        for (int r = 3; r >= 0; --r) {
-            for (int ii = 31; ii >= 0; --ii) {
-                const int i = 32 * r + ii;
-                if (i >= s) continue;
-                const float d = D[i];
-                float x[kLeafCols];
+        for (int g = 0; g < kBlk / 4; ++g) {
+            const float4 f = dq[g];
+            d[4 * g] = f.x; d[4 * g + 1] = f.y; d[4 * g + 2] = f.z; d[4 * g + 3] = f.w;
+        }
 #pragma unroll
-                for (int q = 0; q < kLeafCols; ++q) {
-                    const float bi = __shfl_sync(0xffffffffu, b[q][r], ii);
-                    x[q] = bi * d;
-                    if (lane == ii) b[q][r] = x[q];
-                }
+        for (int j = 0; j < kBlk; ++j) {                  // the diagonal block, column by column
+            x[j] *= d[j];
+            const float4 *lc = reinterpret_cast<const float4 *>(S + (q * kBlk + j) * kSP +
+                                                                 q * kBlk);
 #pragma unroll
-                for (int rr = 0; rr <= r; ++rr) {
-                    const int c = lane + 32 * rr;
-                    if (c < i) {
-                        const float t = T[i * s + c];
+            for (int g = (j + 1) / 4; g < kBlk / 4; ++g) {
+                const float4 l = lc[g];
+                const float lv[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
-                        for (int q = 0; q < kLeafCols; ++q) b[q][rr] = fmaf(-x[q], t, b[q][rr]);
-                    }
-                }
+                for (int e = 0; e < 4; ++e)
+                    if (4 * g + e > j) x[4 * g + e] = fmaf(-lv[e], x[j], x[4 * g + e]);
             }
         }
+        float4 *xo = reinterpret_cast<float4 *>(X + lane * kSP + q * kBlk);
+#pragma unroll
+        for (int g = 0; g < kBlk / 4; ++g)
+            xo[g] = make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
+        if (q + 1 < nblk) named_bar_arrive(1 + q, 32 * (nblk - q));
     }
-#pragma unroll
-    for (int q = 0; q < kLeafCols; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int c = lane + 32 * r;
-            if (c < s) Bs[c * LDS + rw + q] = b[q][r];
-        }
     __syncthreads();
-    for (int e = threadIdx.x; e < s * kRightRows; e += blockDim.x) {
-        const int rl = e % kRightRows, c = e / kRightRows;
-        if (row0 + rl < m) B[row0 + rl + (c0 + c) * ldb] = Bs[c * LDS + rl];
+    if (LEFT) {
+#pragma unroll
+        for (int g = 0; g < kVecs / kLeafWarps; ++g) {
+            const int v = warp + kLeafWarps * g;
+            if (v0 + v >= nvec) continue;
+#pragma unroll
+            for (int k = 0; k < kLeaf / 32; ++k) {
+                const int i = lane + 32 * k;
+                const int row = rev ? s - 1 - i : i;
+                if (i < s) B[r0 + row + (v0 + v) * ldb] = X[v * kSP + i];
+            }
+        }
+    } else if (v0 + lane < nvec) {
+#pragma unroll 4
+        for (int i = warp; i < s; i += kLeafWarps) {
+            const int col = rev ? s - 1 - i : i;
+            B[(v0 + lane) + (r0 + col) * ldb] = X[lane * kSP + i];
+        }
     }
 }
 
 // ------------------------------------------------------------------- host
+
+// Shared memory of a leaf CTA: L' (128 columns of kSP floats), the diagonal
+// reciprocals (128) and the 32 vectors (kSP floats each).
+size_t leaf_smem_bytes() {
+    return (size_t)(kLeaf * kSP + kLeaf + kVecs * kSP) * sizeof(float);
+}
+
+// Shared memory of a prep CTA: the stored 128 x 128 block, padded.
+size_t prep_smem_bytes() { return (size_t)kLeaf * kRawStride * sizeof(float); }
+
+// STRSM workspace: the GEMM updates' area first (256-byte rounded), then
+// every leaf's prepared L' and D.
+struct TrsmWorkspace {
+    size_t gemm_bytes, prep_offset, total;
+};
+TrsmWorkspace trsm_workspace(size_t gemm_need, int64_t ms) {
+    TrsmWorkspace w;
+    w.gemm_bytes = gemm_need;
+    w.prep_offset = (gemm_need + 255) / 256 * 256;
+    w.total = w.prep_offset + (size_t)((ms + kLeaf - 1) / kLeaf) * kPrepBytes;
+    return w;
+}
 
 bool is_t(char c) { return c == 'T' || c == 't' || c == 'C' || c == 'c'; }
 bool is_n(char c) { return c == 'N' || c == 'n'; }
@@ -421,6 +439,7 @@ struct TrsmCtx {
     float *B;
     int64_t ldb;
     int sm_count;
+    const float *prep;      // every leaf's L' and D (kPrepFloats per 128 rows)
 };
 
 // op(A)[R0.., S0..] as a GEMM operand (pointer, trans flag)
@@ -431,17 +450,16 @@ inline const float *opa_block(const TrsmCtx &c, int64_t R0, int64_t S0, char *t)
 
 int trsm_leaf(const TrsmCtx &c, int64_t r0, int64_t s) {
     if (c.g.ws_need) return GB_OK;
-    const size_t tri = ((size_t)s * (size_t)s + kLeaf) * sizeof(float);
-    if (c.left) {
-        const int64_t blocks = (c.n + 8 * kLeafCols - 1) / (8 * kLeafCols);
-        trsm_left_leaf_kernel<<<(unsigned)blocks, 256, tri, c.g.s>>>(
-            (int)s, c.n, c.A, c.lda, r0, c.trans, c.tlower, c.unit, c.B, c.ldb);
-    } else {
-        const int64_t blocks = (c.m + kRightRows - 1) / kRightRows;
-        const size_t smem = tri + (size_t)s * (kRightRows + 1) * sizeof(float);
-        trsm_right_leaf_kernel<<<(unsigned)blocks, 256, smem, c.g.s>>>(
-            (int)s, c.m, c.A, c.lda, r0, c.trans, c.tlower, c.unit, c.B, c.ldb);
-    }
+    const size_t smem = leaf_smem_bytes();
+    const int64_t vecs = c.left ? c.n : c.m;
+    const int64_t blocks = (vecs + kVecs - 1) / kVecs;
+    const float *prep = c.prep + (r0 / kLeaf) * kPrepFloats;
+    if (c.left)
+        trsm_leaf_kernel<true><<<(unsigned)blocks, kLeafThreads, smem, c.g.s>>>(
+            (int)s, c.n, r0, c.tlower, prep, c.B, c.ldb);
+    else
+        trsm_leaf_kernel<false><<<(unsigned)blocks, kLeafThreads, smem, c.g.s>>>(
+            (int)s, c.m, r0, c.tlower, prep, c.B, c.ldb);
     return cudaGetLastError() == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
@@ -499,12 +517,17 @@ bool leaf_attrs_set(int dev) {
     static bool done[64] = {};
     if (dev < 0 || dev >= 64) return false;
     if (done[dev]) return true;
-    const int bytes = (kLeaf * kLeaf + kLeaf) * (int)sizeof(float);
-    const int rbytes = bytes + kLeaf * (kRightRows + 1) * (int)sizeof(float);
-    if (cudaFuncSetAttribute(trsm_left_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int bytes = (int)leaf_smem_bytes(), prep_bytes = (int)prep_smem_bytes();
+    if (cudaFuncSetAttribute(trsm_leaf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes) != cudaSuccess ||
-        cudaFuncSetAttribute(trsm_right_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             rbytes) != cudaSuccess)
+        cudaFuncSetAttribute(trsm_leaf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(trsm_leaf_prep_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             prep_bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(trsm_leaf_prep_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             prep_bytes) != cudaSuccess)
         return false;
     done[dev] = true;
     return true;
@@ -608,9 +631,13 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
     GemmRunner g{nullptr, algo, nullptr, 0, nullptr, &need};
     TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, nullptr, max1(is_l(side) ? m : n),
                          nullptr, max1(m), 0);
-    rc = (m == 0 || n == 0) ? GB_OK : trsm_rec(c, 0, is_l(side) ? m : n);
+    if (m == 0 || n == 0) {
+        *bytes = 0;
+        return GB_OK;
+    }
+    rc = trsm_rec(c, 0, is_l(side) ? m : n);
     if (rc) return rc;
-    *bytes = need;
+    *bytes = trsm_workspace(need, is_l(side) ? m : n).total;
     return GB_OK;
 }
 
@@ -632,14 +659,27 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
     size_t need = 0;
     GemmRunner probe{nullptr, algo, nullptr, 0, nullptr, &need};
     TrsmCtx pc = trsm_ctx(probe, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
-    rc = trsm_rec(pc, 0, is_l(side) ? m : n);
+    const int64_t ms = is_l(side) ? m : n;
+    rc = trsm_rec(pc, 0, ms);
     if (rc) return rc;
-    if (need && (ws_bytes < need || !workspace)) return GB_ERR_WORKSPACE;
+    const TrsmWorkspace w = trsm_workspace(need, ms);
+    if (ws_bytes < w.total || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 15))
+        return GB_ERR_WORKSPACE;
     if (!leaf_attrs_set(h->device)) return GB_ERR_CUDA;
     if (alpha != 1.f && launch_scale_c(m, n, alpha, B, ldb, s) != cudaSuccess) return GB_ERR_CUDA;
-    GemmRunner g{h, algo, workspace, ws_bytes, s, nullptr};
+    GemmRunner g{h, algo, workspace, w.gemm_bytes, s, nullptr};
     TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
-    return trsm_rec(c, 0, is_l(side) ? m : n);
+    float *prep = reinterpret_cast<float *>(static_cast<char *>(workspace) + w.prep_offset);
+    c.prep = prep;
+    const unsigned leaves = (unsigned)((ms + kLeaf - 1) / kLeaf);
+    if (c.left)
+        trsm_leaf_prep_kernel<true><<<leaves, kLeafThreads, prep_smem_bytes(), s>>>(
+            ms, A, lda, c.trans, c.tlower, c.unit, prep);
+    else
+        trsm_leaf_prep_kernel<false><<<leaves, kLeafThreads, prep_smem_bytes(), s>>>(
+            ms, A, lda, c.trans, c.tlower, c.unit, prep);
+    if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
+    return trsm_rec(c, 0, ms);
 }
 
 }  // extern "C"

@@ -256,3 +256,36 @@ def test_strsm_special_cases():
     assert gb.strsm_raw("L", "L", "N", "N", 4, 4, 1.0, 0, 3, 0, 4, check=False) == -9
     assert gb.strsm_raw("R", "L", "N", "N", 4, 6, 1.0, 0, 5, 0, 4, check=False) == -9
     assert gb.strsm_raw("L", "L", "N", "N", 4, 4, 1.0, 0, 4, 0, 3, check=False) == -11
+
+
+def test_strsm_workspace_rules():
+    """The workspace holds the GEMM updates' area and one prepared block per
+    128 rows of A's diagonal: too small or not 16-byte aligned is refused
+    before any launch, and B is untouched."""
+    torch = torch_gpu()
+    import ctypes
+    import paper_1912_04379_gb300 as gb
+    from paper_1912_04379_gb300 import _lib
+    h = gb.api.default_handle()
+    m, n = 300, 50
+    A = _trsm_case("L", "L", "N", m, n, seed=21)
+    B = wl.uniform(np.random.default_rng(22), m, n, m)
+    Ad, Bd = _dev(A), _dev(B)
+    need = ctypes.c_size_t(0)
+    assert h.lib.gb_strsm_workspace_size(_lib.ALGOS["simt"], b"L", b"L", b"N", b"N", m, n,
+                                         ctypes.byref(need)) == _lib.GB_OK
+    assert need.value >= 3 * 68096                      # three diagonal blocks, even for SIMT
+    ws = torch.empty(need.value + 16, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for ptr, size in ((0, 0), (ws.data_ptr(), need.value - 1), (ws.data_ptr() + 4, need.value)):
+        rc = h.lib.gb_strsm(h.h, _lib.ALGOS["simt"], b"L", b"L", b"N", b"N", m, n, 1.0,
+                            Ad.data_ptr(), A.shape[0], Bd.data_ptr(), m, ptr, size, s)
+        assert rc == _lib.GB_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert np.array_equal(gb.to_fortran(Bd), B)
+    rc = h.lib.gb_strsm(h.h, _lib.ALGOS["simt"], b"L", b"L", b"N", b"N", m, n, 1.0,
+                        Ad.data_ptr(), A.shape[0], Bd.data_ptr(), m, ws.data_ptr() + 16,
+                        need.value, s)
+    assert rc == _lib.GB_OK
+    torch.cuda.synchronize()
+    _residual_check("L", "L", "N", "N", m, n, 1.0, A, B, gb.to_fortran(Bd)[:m, :n], "simt")
