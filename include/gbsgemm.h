@@ -414,7 +414,7 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
                     void *workspace, size_t ws_bytes, void *stream);
 
 /* Workspace bytes of gb_strsm with these arguments: the GEMM updates' need
- * (256-byte rounded) plus 68,096 bytes per 128 rows of A's diagonal, where
+ * (256-byte rounded) plus 197,632 bytes per 256 rows of A's diagonal, where
  * each diagonal block's triangle and diagonal reciprocals are laid out once
  * per call for the substitution kernels. */
 GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char transa, char diag,
@@ -429,7 +429,7 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
  * positions (1 side, 2 uplo, 3 transa, 4 diag, 5 m, 6 n, 9 lda, 11 ldb).
  * Recursion by halving: each level's off-diagonal block update is one
  * gb_sgemm call with `algo` (alpha = -1, beta = 1), and the diagonal blocks
- * (at most 128 rows) are solved by substitution in FP32, with each diagonal
+ * (at most 256 rows) are solved by substitution in FP32, with each diagonal
  * entry's reciprocal rounded once. `workspace` (16-byte aligned, at least
  * gb_strsm_workspace_size bytes) is always needed when m, n > 0 and alpha != 0;
  * otherwise GB_ERR_WORKSPACE. */

@@ -6,7 +6,7 @@
 // triangle's tiles (tc_syrk.cu). Otherwise (SIMT, or alpha = 0 / k = 0) and
 // for STRSM, the operation recurses by halving: the off-diagonal half-size
 // block of each level is one gb_sgemm call, down to diagonal leaves of at
-// most 128 rows.
+// most 128 (SSYRK) or 256 (STRSM) rows.
 //   SSYRK  leaves: every diagonal block's triangle in ONE launch of a small
 //          FP32 SIMT kernel (64 x 64 tiles, the tiles above or below the
 //          diagonal skipped).
@@ -26,7 +26,8 @@
 namespace gb {
 namespace {
 
-constexpr int kLeaf = 128;       // largest diagonal leaf
+constexpr int kLeaf = 128;       // largest SSYRK diagonal leaf
+constexpr int kTLeaf = 256;      // largest STRSM diagonal leaf
 constexpr int kTile = 64;        // SSYRK leaf kernel tile
 constexpr int kTk = 16;
 
@@ -102,13 +103,13 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 // ------------------------------------------------------------- STRSM leaves
 
 // A leaf solves M x = b for every vector of B, with M the s x s diagonal
-// block (s <= 128) of op(A) (left side; the vectors are the columns of B) or
+// block (s <= 256) of op(A) (left side; the vectors are the columns of B) or
 // of op(A)^T (right side, X op(A) = B read as op(A)^T x = b; the vectors are
 // the rows of B). It is put in forward lower form L' x' = b': L' = M and
 // x' = x when M is lower, else L'(i, j) = M(s-1-i, s-1-j) and x'_i = x_{s-1-i}.
 // Then x'_i = (b'_i - sum over j < i of L'(i, j) x'_j) / L'(i, i), i ascending.
 //
-// A CTA holds 32 vectors (one per lane) and eight warps; warp q owns rows
+// A CTA holds 32 vectors (one per lane) and sixteen warps; warp q owns rows
 // [16q, 16q + 16) of every vector in registers. It subtracts the products of
 // each earlier row block p as soon as warp p has solved it (p ascending,
 // columns ascending within a block, so every x'_i accumulates its terms in
@@ -116,15 +117,29 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 // from warp to warp through shared memory, released by named barriers (warp
 // p arrives on barrier p + 1, the warps after it wait on it). Only entries
 // with j < i are ever multiplied, so a non-finite b'_j reaches exactly the
-// x'_i that depend on it.
-constexpr int kBlk = 16;                       // rows per warp block
-constexpr int kLeafWarps = kLeaf / kBlk;       // 8
-constexpr int kLeafThreads = 32 * kLeafWarps;
-constexpr int kVecs = 32;                      // vectors per CTA
-constexpr int kSP = 132;                       // stride of L's columns and of each vector
-constexpr int kPrepFloats = kLeaf * kSP + kLeaf;                    // one leaf's L' and D
-constexpr size_t kPrepBytes = (size_t)kPrepFloats * sizeof(float);  // 68,096
-constexpr int kRawStride = kLeaf + 1;                                // prep's staging tile
+// x'_i that depend on it. A 256-row leaf does in one launch what two 128-row
+// leaves and the K = 128 GEMM update between them would do.
+//
+// L' in shared memory keeps what a lower triangle needs, column-major:
+// columns 0..127 with all 256 rows, then columns 128..255 with rows
+// 128..255; L'(i, j) is at colbase(j) + i.
+constexpr int kBlk = 16;                        // rows per warp block
+constexpr int kLeafWarps = kTLeaf / kBlk;       // 16
+constexpr int kLeafThreads = 32 * kLeafWarps;   // 512
+constexpr int kVecs = 32;                       // vectors per CTA
+constexpr int kHalfLeaf = kTLeaf / 2;           // 128
+constexpr int kXS = kTLeaf + 4;                 // stride of each vector
+constexpr int kSFloats = kHalfLeaf * kTLeaf + kHalfLeaf * kHalfLeaf;   // 49,152
+constexpr int kPrepFloats = kSFloats + kTLeaf;                          // L' and D
+constexpr size_t kPrepBytes = (size_t)kPrepFloats * sizeof(float);     // 197,632
+constexpr int kRawStride = kHalfLeaf + 1;                               // prep's staging tile
+constexpr int kPrepThreads = 256;
+
+__host__ __device__ constexpr int colbase(int j) {
+    return j < kHalfLeaf ? kTLeaf * j : kSFloats - kHalfLeaf * kTLeaf + kHalfLeaf * j - kHalfLeaf;
+}
+static_assert(colbase(kHalfLeaf) + kHalfLeaf == kHalfLeaf * kTLeaf, "L' layout");
+static_assert(colbase(kTLeaf - 1) + kTLeaf == kSFloats, "L' layout");
 
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -140,66 +155,77 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Builds every leaf's L' and D once per call, one CTA per leaf (rows
-// [128 b, 128 b + s) of op(A)'s diagonal), into prep[b * kPrepFloats ..]:
-// L'(i, j) at [j * kSP + i] for j < i < s and 0 elsewhere, then D[i] =
-// 1 / L'(i, i) (1 for a unit diagonal and for padding rows). The stored
-// block's triangle is read coalesced into shared memory, then written out in
-// L' order, also coalesced. The stored (sr, sc) is M(sr, sc), or M(sc, sr)
+// Builds every leaf's L' and D once per call into prep[b * kPrepFloats ..]
+// (leaf b = rows [256 b, 256 b + s) of op(A)'s diagonal): L'(i, j) at
+// colbase(j) + i for j < i < s and 0 elsewhere, then D[i] = 1 / L'(i, i) (1
+// for a unit diagonal and for padding rows). One CTA per leaf and 128 x 128
+// region of L' (blockIdx.y: rows/columns 0-127, rows 128-255 x columns
+// 0-127, rows/columns 128-255). The stored (sr, sc) is M(sr, sc), or M(sc, sr)
 // when exactly one of (right side, transposed op) holds; L'(i, j) is M(i, j),
-// or M(s-1-i, s-1-j) when M is upper.
+// or M(s-1-i, s-1-j) when M is upper. The stored tile under the region is
+// read (its triangle only) coalesced into shared memory, then written out in
+// L' order, also coalesced.
 template <bool LEFT>
-__global__ void __launch_bounds__(kLeafThreads)
+__global__ void __launch_bounds__(kPrepThreads)
 trsm_leaf_prep_kernel(int64_t ms, const float *__restrict__ A, int64_t lda, int trans,
                       int tlower, int unit, float *__restrict__ prep) {
-    extern __shared__ float R[];                  // R[sc * kRawStride + sr] = stored (sr, sc)
-    const int64_t r0 = (int64_t)blockIdx.x * kLeaf;
-    const int s = (int)(ms - r0 < kLeaf ? ms - r0 : kLeaf);
+    extern __shared__ float R[];                  // R[scl * kRawStride + srl]
+    const int64_t r0 = (int64_t)blockIdx.x * kTLeaf;
+    const int s = (int)(ms - r0 < kTLeaf ? ms - r0 : kTLeaf);
+    const int ib = blockIdx.y > 0, jb = blockIdx.y > 1;
+    const int i0 = kHalfLeaf * ib, j0 = kHalfLeaf * jb;
     const bool rev = LEFT ? tlower == 0 : tlower != 0;
     const bool swap = LEFT == (trans != 0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int sc = warp; sc < s; sc += kLeafWarps) {
+    // the region's M rows and columns start at mi0, mj0 (negative or past s
+    // for a ragged leaf: those are skipped); stored ones at sr0, sc0
+    const int mi0 = rev ? s - i0 - kHalfLeaf : i0, mj0 = rev ? s - j0 - kHalfLeaf : j0;
+    const int sr0 = swap ? mj0 : mi0, sc0 = swap ? mi0 : mj0;
+    for (int scl = warp; scl < kHalfLeaf; scl += kPrepThreads / 32) {
+        const int sc = sc0 + scl;
 #pragma unroll
-        for (int k = 0; k < kLeaf / 32; ++k) {
-            const int sr = lane + 32 * k;
+        for (int k = 0; k < kHalfLeaf / 32; ++k) {
+            const int srl = lane + 32 * k, sr = sr0 + srl;
+            if (sr < 0 || sr >= s || sc < 0 || sc >= s) continue;
             const int mi = swap ? sc : sr, mj = swap ? sr : sc;
             const int i = rev ? s - 1 - mi : mi, j = rev ? s - 1 - mj : mj;
-            if (sr < s && (i > j || (i == j && !unit)))
-                R[sc * kRawStride + sr] = A[(r0 + sr) + (r0 + sc) * lda];
+            if (i > j || (i == j && !unit))
+                R[scl * kRawStride + srl] = A[(r0 + sr) + (r0 + sc) * lda];
         }
     }
     __syncthreads();
     float *out = prep + (int64_t)blockIdx.x * kPrepFloats;
-    for (int e = tid; e < kLeaf * kSP; e += kLeafThreads) {
-        const int j = e / kSP, i = e - j * kSP;
+    for (int e = tid; e < kHalfLeaf * kHalfLeaf; e += kPrepThreads) {
+        const int i = i0 + (e & (kHalfLeaf - 1)), j = j0 + e / kHalfLeaf;
         float v = 0.f;
         if (i < s && j < i) {
             const int mi = rev ? s - 1 - i : i, mj = rev ? s - 1 - j : j;
             const int sr = swap ? mj : mi, sc = swap ? mi : mj;
-            v = R[sc * kRawStride + sr];
+            v = R[(sc - sc0) * kRawStride + (sr - sr0)];
         }
-        out[e] = v;
+        out[colbase(j) + i] = v;
     }
-    if (tid < kLeaf) {
+    if (ib == jb && tid < kHalfLeaf) {
+        const int i = i0 + tid;
         float d = 1.f;
-        if (tid < s && !unit) {
-            const int mi = rev ? s - 1 - tid : tid;
-            d = 1.f / R[mi * kRawStride + mi];
+        if (i < s && !unit) {
+            const int mi = rev ? s - 1 - i : i;
+            d = 1.f / R[(mi - sc0) * kRawStride + (mi - sr0)];
         }
-        out[kLeaf * kSP + tid] = d;
+        out[kSFloats + i] = d;
     }
 }
 
 // The leaf at rows (left) or columns (right) [r0, r0 + s) of B, its L' and D
 // prepared in prep (kPrepFloats, 16-byte aligned).
 template <bool LEFT>
-__global__ void __launch_bounds__(kLeafThreads, 2)
+__global__ void __launch_bounds__(kLeafThreads, 1)
 trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__restrict__ prep,
                  float *__restrict__ B, int64_t ldb) {
     extern __shared__ __align__(16) float smem[];
-    float *S = smem;                      // L' column-major: S[j * kSP + i] = L'(i, j), i > j
-    float *D = S + kLeaf * kSP;           // D[i] = 1 / L'(i, i)
-    float *X = D + kLeaf;                 // X[v * kSP + i] = b'_i, then x'_i, of vector v
+    float *S = smem;                      // L', at colbase(j) + i
+    float *D = S + kSFloats;              // D[i] = 1 / L'(i, i)
+    float *X = D + kTLeaf;                // X[v * kXS + i] = b'_i, then x'_i, of vector v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool rev = LEFT ? tlower == 0 : tlower != 0;    // M upper
     const int64_t v0 = (int64_t)blockIdx.x * kVecs;
@@ -211,19 +237,19 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
 #pragma unroll
         for (int g = 0; g < kVecs / kLeafWarps; ++g) {
             const int v = warp + kLeafWarps * g;
-            float t[kLeaf / 32];
+            float t[kTLeaf / 32];
 #pragma unroll
-            for (int k = 0; k < kLeaf / 32; ++k) {
+            for (int k = 0; k < kTLeaf / 32; ++k) {
                 const int i = lane + 32 * k;
                 const int row = rev ? s - 1 - i : i;
                 t[k] = (i < s && v0 + v < nvec) ? B[r0 + row + (v0 + v) * ldb] : 0.f;
             }
 #pragma unroll
-            for (int k = 0; k < kLeaf / 32; ++k) X[v * kSP + lane + 32 * k] = t[k];
+            for (int k = 0; k < kTLeaf / 32; ++k) X[v * kXS + lane + 32 * k] = t[k];
         }
     } else {
 #pragma unroll
-        for (int g = 0; g < kLeaf / kLeafWarps; g += 4) {
+        for (int g = 0; g < kTLeaf / kLeafWarps; g += 4) {
             float t[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -232,7 +258,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                 t[k] = (i < s && v0 + lane < nvec) ? B[(v0 + lane) + (r0 + col) * ldb] : 0.f;
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) X[lane * kSP + warp + kLeafWarps * (g + k)] = t[k];
+            for (int k = 0; k < 4; ++k) X[lane * kXS + warp + kLeafWarps * (g + k)] = t[k];
         }
     }
     cp_async_wait_all();
@@ -242,7 +268,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
     const int q = warp;
     if (q < nblk) {                       // warp-uniform: every lane reaches each barrier
         float x[kBlk];
-        const float4 *xq = reinterpret_cast<const float4 *>(X + lane * kSP + q * kBlk);
+        const float4 *xq = reinterpret_cast<const float4 *>(X + lane * kXS + q * kBlk);
 #pragma unroll
         for (int g = 0; g < kBlk / 4; ++g) {
             const float4 f = xq[g];
@@ -252,16 +278,18 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
         for (int p = 0; p < q; ++p) {
             named_bar_sync(1 + p, 32 * (nblk - p));       // block p solved
             float y[kBlk];
-            const float4 *xp = reinterpret_cast<const float4 *>(X + lane * kSP + p * kBlk);
+            const float4 *xp = reinterpret_cast<const float4 *>(X + lane * kXS + p * kBlk);
 #pragma unroll
             for (int g = 0; g < kBlk / 4; ++g) {
                 const float4 f = xp[g];
                 y[4 * g] = f.x; y[4 * g + 1] = f.y; y[4 * g + 2] = f.z; y[4 * g + 3] = f.w;
             }
+            // columns p*16 .. p*16+15 of L' (one side of column 128), rows q*16 ..
+            const float *sp = S + colbase(p * kBlk) + q * kBlk;
+            const int cs = p * kBlk < kHalfLeaf ? kTLeaf : kHalfLeaf;
 #pragma unroll
-            for (int c = 0; c < kBlk; ++c) {              // column p*16 + c of L'
-                const float4 *lc = reinterpret_cast<const float4 *>(S + (p * kBlk + c) * kSP +
-                                                                     q * kBlk);
+            for (int c = 0; c < kBlk; ++c) {
+                const float4 *lc = reinterpret_cast<const float4 *>(sp + c * cs);
 #pragma unroll
                 for (int g = 0; g < kBlk / 4; ++g) {
                     const float4 l = lc[g];
@@ -279,11 +307,12 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             const float4 f = dq[g];
             d[4 * g] = f.x; d[4 * g + 1] = f.y; d[4 * g + 2] = f.z; d[4 * g + 3] = f.w;
         }
+        const float *sq = S + colbase(q * kBlk) + q * kBlk;
+        const int cq = q * kBlk < kHalfLeaf ? kTLeaf : kHalfLeaf;
 #pragma unroll
         for (int j = 0; j < kBlk; ++j) {                  // the diagonal block, column by column
             x[j] *= d[j];
-            const float4 *lc = reinterpret_cast<const float4 *>(S + (q * kBlk + j) * kSP +
-                                                                 q * kBlk);
+            const float4 *lc = reinterpret_cast<const float4 *>(sq + j * cq);
 #pragma unroll
             for (int g = (j + 1) / 4; g < kBlk / 4; ++g) {
                 const float4 l = lc[g];
@@ -293,7 +322,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                     if (4 * g + e > j) x[4 * g + e] = fmaf(-lv[e], x[j], x[4 * g + e]);
             }
         }
-        float4 *xo = reinterpret_cast<float4 *>(X + lane * kSP + q * kBlk);
+        float4 *xo = reinterpret_cast<float4 *>(X + lane * kXS + q * kBlk);
 #pragma unroll
         for (int g = 0; g < kBlk / 4; ++g)
             xo[g] = make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
@@ -306,31 +335,31 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             const int v = warp + kLeafWarps * g;
             if (v0 + v >= nvec) continue;
 #pragma unroll
-            for (int k = 0; k < kLeaf / 32; ++k) {
+            for (int k = 0; k < kTLeaf / 32; ++k) {
                 const int i = lane + 32 * k;
                 const int row = rev ? s - 1 - i : i;
-                if (i < s) B[r0 + row + (v0 + v) * ldb] = X[v * kSP + i];
+                if (i < s) B[r0 + row + (v0 + v) * ldb] = X[v * kXS + i];
             }
         }
     } else if (v0 + lane < nvec) {
 #pragma unroll 4
         for (int i = warp; i < s; i += kLeafWarps) {
             const int col = rev ? s - 1 - i : i;
-            B[(v0 + lane) + (r0 + col) * ldb] = X[lane * kSP + i];
+            B[(v0 + lane) + (r0 + col) * ldb] = X[lane * kXS + i];
         }
     }
 }
 
 // ------------------------------------------------------------------- host
 
-// Shared memory of a leaf CTA: L' (128 columns of kSP floats), the diagonal
-// reciprocals (128) and the 32 vectors (kSP floats each).
+// Shared memory of a leaf CTA: L' (kSFloats), the diagonal reciprocals
+// (256) and the 32 vectors (kXS floats each): 230,912 bytes.
 size_t leaf_smem_bytes() {
-    return (size_t)(kLeaf * kSP + kLeaf + kVecs * kSP) * sizeof(float);
+    return (size_t)(kSFloats + kTLeaf + kVecs * kXS) * sizeof(float);
 }
 
-// Shared memory of a prep CTA: the stored 128 x 128 block, padded.
-size_t prep_smem_bytes() { return (size_t)kLeaf * kRawStride * sizeof(float); }
+// Shared memory of a prep CTA: one stored 128 x 128 tile, padded.
+size_t prep_smem_bytes() { return (size_t)kHalfLeaf * kRawStride * sizeof(float); }
 
 // STRSM workspace: the GEMM updates' area first (256-byte rounded), then
 // every leaf's prepared L' and D.
@@ -341,7 +370,7 @@ TrsmWorkspace trsm_workspace(size_t gemm_need, int64_t ms) {
     TrsmWorkspace w;
     w.gemm_bytes = gemm_need;
     w.prep_offset = (gemm_need + 255) / 256 * 256;
-    w.total = w.prep_offset + (size_t)((ms + kLeaf - 1) / kLeaf) * kPrepBytes;
+    w.total = w.prep_offset + (size_t)((ms + kTLeaf - 1) / kTLeaf) * kPrepBytes;
     return w;
 }
 
@@ -350,6 +379,12 @@ bool is_n(char c) { return c == 'N' || c == 'n'; }
 bool is_l(char c) { return c == 'L' || c == 'l'; }
 bool is_u(char c) { return c == 'U' || c == 'u'; }
 int64_t max1(int64_t x) { return x > 1 ? x : 1; }
+
+// STRSM's split: every leaf starts at a multiple of 256 rows.
+int64_t trsm_split_point(int64_t nn) {
+    const int64_t h = nn / 2;
+    return (h + kTLeaf - 1) / kTLeaf * kTLeaf;
+}
 
 int64_t split_point(int64_t nn) {
     const int64_t h = nn / 2;
@@ -453,7 +488,7 @@ int trsm_leaf(const TrsmCtx &c, int64_t r0, int64_t s) {
     const size_t smem = leaf_smem_bytes();
     const int64_t vecs = c.left ? c.n : c.m;
     const int64_t blocks = (vecs + kVecs - 1) / kVecs;
-    const float *prep = c.prep + (r0 / kLeaf) * kPrepFloats;
+    const float *prep = c.prep + (r0 / kTLeaf) * kPrepFloats;
     if (c.left)
         trsm_leaf_kernel<true><<<(unsigned)blocks, kLeafThreads, smem, c.g.s>>>(
             (int)s, c.n, r0, c.tlower, prep, c.B, c.ldb);
@@ -464,8 +499,8 @@ int trsm_leaf(const TrsmCtx &c, int64_t r0, int64_t s) {
 }
 
 int trsm_rec(const TrsmCtx &c, int64_t r0, int64_t mm) {
-    if (mm <= kLeaf) return trsm_leaf(c, r0, mm);
-    const int64_t m1 = split_point(mm), m2 = mm - m1;
+    if (mm <= kTLeaf) return trsm_leaf(c, r0, mm);
+    const int64_t m1 = trsm_split_point(mm), m2 = mm - m1;
     const int64_t a = r0, b = r0 + m1;          // first and second half
     char t;
     int rc;
@@ -671,12 +706,12 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
     TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
     float *prep = reinterpret_cast<float *>(static_cast<char *>(workspace) + w.prep_offset);
     c.prep = prep;
-    const unsigned leaves = (unsigned)((ms + kLeaf - 1) / kLeaf);
+    const dim3 prep_grid((unsigned)((ms + kTLeaf - 1) / kTLeaf), 3);
     if (c.left)
-        trsm_leaf_prep_kernel<true><<<leaves, kLeafThreads, prep_smem_bytes(), s>>>(
+        trsm_leaf_prep_kernel<true><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
             ms, A, lda, c.trans, c.tlower, c.unit, prep);
     else
-        trsm_leaf_prep_kernel<false><<<leaves, kLeafThreads, prep_smem_bytes(), s>>>(
+        trsm_leaf_prep_kernel<false><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
             ms, A, lda, c.trans, c.tlower, c.unit, prep);
     if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
     return trsm_rec(c, 0, ms);
