@@ -331,7 +331,8 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             const bool so = p.alpha == 0.f || p.k == 0;
             if (p.m == 0 || p.n == 0 || so || route(p, so) != 2 || tc_mode_for(pref, p.k) != 1)
                 continue;
-            x2_tiles += ((p.m + 127) / 128) * ((p.n + tc_tile_n(1) - 1) / tc_tile_n(1));
+            const int64_t bn1 = tc_tile_n(1, kTcRb128);
+            x2_tiles += ((p.m + 127) / 128) * ((p.n + bn1 - 1) / bn1);
         }
         x2_own_launch = x2_tiles >= h->sm_count;
     }
@@ -405,7 +406,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         for (size_t j = 0; ok && j < tcs.size(); ++j) {
             const gb_gemm_problem_t &p = ps[tcs[j].prob];
             const int mode = tcs[j].mode;
-            const int bn = tc_tile_n(mode);
+            const int bn = tc_tile_n(mode, kTcRb128);
             const int64_t kpad = split_kpad(mode, p.k);
             char *pa = base + tcs[j].off_a, *pb = base + tcs[j].off_b;
             ok = tc_make_operand_map(&maps[2 * j], mode, kTcRb128, pa, p.k, p.m, true) &&

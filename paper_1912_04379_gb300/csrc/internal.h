@@ -172,7 +172,7 @@ struct TcItem {
     int tm, tn;                 // output tile (128 x tile_n)
     int pad;
 };
-int tc_tile_n(int mode);
+int tc_tile_n(int mode, bool rb128);
 // Tensor map of one packed operand ([terms][rows][kpad], K innermost) for the
 // kernel variant (mode, 128-byte rows or not); a_side selects the box height.
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,

@@ -19,7 +19,10 @@ struct Cfg {
     static constexpr bool TF32 = MODE == 0;
     static constexpr int PARTS = MODE >= 2 ? 3 : 2;
     static constexpr int NPAIRS = MODE == 3 ? 9 : MODE == 2 ? 6 : 3;
-    static constexpr int BN = MODE >= 2 ? 128 : 256;
+    // 256 output columns per tile, except 3-term operands with 128-byte rows
+    // (a 256-column stage would be 144 KiB: one stage only), which use 128.
+    // Wider tiles halve the MMA's re-reads of A from shared memory per flop.
+    static constexpr int BN = (MODE >= 2 && RB == 128) ? 128 : 256;
     static constexpr int ELEM = TF32 ? 4 : 2;
     static constexpr int BK = ROW_BYTES / ELEM;          // elements per k-block
     static constexpr int KSTEP_BYTES = 32;               // K per MMA: 16 BF16 / 8 TF32
@@ -27,10 +30,11 @@ struct Cfg {
     static constexpr int A_TILE = BM * ROW_BYTES;        // bytes of one term's A tile
     static constexpr int B_TILE = BN * ROW_BYTES;
     static constexpr int STAGE_BYTES = PARTS * (A_TILE + B_TILE);
-    static constexpr int STAGES = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = (216 * 1024) / STAGE_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
     static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
     static_assert(STAGES >= 2, "need at least two stages");
+    static_assert(SMEM_BYTES <= 232448, "opt-in shared memory per block");
     static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
 };
 

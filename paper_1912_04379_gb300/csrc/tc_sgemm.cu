@@ -198,7 +198,7 @@ cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part,
     return cudaGetLastError();
 }
 
-int tc_tile_n(int mode) { return mode >= 2 ? 128 : 256; }
+int tc_tile_n(int mode, bool rb128) { return (mode >= 2 && rb128) ? 128 : 256; }
 
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
                          int64_t rows, bool a_side) {
@@ -206,7 +206,7 @@ bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *pac
     const bool tf32 = mode == 0;
     const int bk = rb / (tf32 ? 4 : 2);
     return make_map(map, tf32, packed, k, rows, split_kpad(mode, k), split_parts(mode),
-                    a_side ? BM : tc_tile_n(mode), bk, rb);
+                    a_side ? BM : tc_tile_n(mode, rb128), bk, rb);
 }
 
 cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, const TcItem *items,
