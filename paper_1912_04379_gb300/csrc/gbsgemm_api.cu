@@ -85,7 +85,7 @@ gb_algo_t gb::resolve_algo(gb_algo_t algo, int64_t k) {
 // slice always holds several k-blocks, and S <= 16). Depends on the shape
 // only: workspace sizes do not depend on the device.
 int gb::split_k_factor(int mode, int64_t m, int64_t n, int64_t k) {
-    const int64_t bn = (mode >= 2 && k <= 2048) ? 128 : 256;   // the kernel's tile width
+    const int64_t bn = tc_tile_n(mode, tc_rb128(mode, m, n, k));   // the kernel's tile width
     const int64_t tiles = ((m + 127) / 128) * ((n + bn - 1) / bn);
     if (tiles < 1 || tiles * 4 > 148 || k < 1024) return 1;
     int64_t s = 148 / tiles;

@@ -173,6 +173,8 @@ struct TcItem {
     int pad;
 };
 int tc_tile_n(int mode, bool rb128);
+// Row width (128 bytes or 64) of the one-GEMM tensor-core kernel for a shape.
+bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k);
 // Tensor map of one packed operand ([terms][rows][kpad], K innermost) for the
 // kernel variant (mode, 128-byte rows or not); a_side selects the box height.
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,

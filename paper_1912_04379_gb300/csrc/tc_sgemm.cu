@@ -226,18 +226,32 @@ cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, cons
     }
 }
 
-cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
-    // Shared-memory row width of a k-block. 64-byte rows (64-byte swizzle,
-    // 48 KiB stages, 4 in flight) hide the TMA latency on long K loops;
-    // 128-byte rows (96 KiB stages, 2 in flight) measured slightly faster
-    // when the K loop is short (K <= 2048 at M = N = 8192). The environment
-    // variable GB_SGEMM_TC_ROW_BYTES = 64 or 128 forces one of them.
+// Shared-memory row width of a k-block for one GEMM. 64-byte rows (64-byte
+// swizzle; 2 terms: four 48 KiB stages; 3 terms: three 72 KiB stages with
+// 256-column tiles) measured faster than 128-byte rows (two 96 KiB stages;
+// 3 terms: 128-column tiles) for both 2-term splits at every K (8192^2,
+// K = 1024: BF16 0.275 against 0.298 ms, TF32 0.478 against 0.543; 4096^2
+// and 2048 x 8192 likewise or equal), and for 3 terms wherever the
+// 256-column tiling has at least 1024 tiles (8192^2, K = 1024: 0.449 against
+// 0.506 ms); with fewer tiles the 3-term modes keep 128-column tiles for a
+// fuller last round (4096^2, K = 1024: 0.152 against 0.155 ms). K <= 128
+// (one or two k-blocks) keeps 128-byte rows: 8192^2 x 64 TF32 0.074 against
+// 0.081 ms, BF16 x 3 terms 0.075 against 0.078. The environment variable
+// GB_SGEMM_TC_ROW_BYTES = 64 or 128 forces one of them.
+bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k) {
     static const int forced = [] {
         const char *e = getenv("GB_SGEMM_TC_ROW_BYTES");
         const int v = e ? atoi(e) : 0;
         return (v == 64 || v == 128) ? v : 0;
     }();
-    const bool rb128 = forced ? forced == 128 : a.k <= 2048;
+    if (forced) return forced == 128;
+    if (k <= 128) return true;
+    if (k > 2048 || mode <= 1) return false;
+    return ((m + BM - 1) / BM) * ((n + 255) / 256) < 1024;
+}
+
+cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
+    const bool rb128 = tc_rb128(a.mode, a.m, a.n, a.k);
     if (a.epi.kind != 0) {
         // fused elementwise operations: BF16 x 2 terms and x 3 terms (6 products)
         const int key = a.mode * 10 + a.epi.kind;

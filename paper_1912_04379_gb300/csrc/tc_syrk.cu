@@ -115,7 +115,7 @@ cudaError_t launch_syrk_mode(const TcSyrkArgs &a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_tc_syrk(const TcSyrkArgs &a, cudaStream_t s) {
-    const bool rb128 = a.k <= 2048;
+    const bool rb128 = tc_rb128(a.mode, a.n, a.n, a.k);   // the one-GEMM kernel's row width rule
     switch (a.mode) {
         case 0: return rb128 ? launch_syrk_mode<0, 128>(a, s) : launch_syrk_mode<0, 64>(a, s);
         case 1: return rb128 ? launch_syrk_mode<1, 128>(a, s) : launch_syrk_mode<1, 64>(a, s);
