@@ -207,7 +207,22 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
         const int q = warp & 3;                       // TMEM lane quarter this warp may read
         int acc = 0;
         uint32_t acc_phase = 0;
+        // What a unit's epilogue will read (C when beta != 0, the factor's
+        // array for the (1 - aux^2) epilogue) is requested from L2 one unit
+        // ahead, while the tensor cores still work on it.
+        auto prefetch_unit = [&](int64_t v) {
+            if (v >= num_units) return;
+            UnitInfo pi;
+            src.unit(v, pi);
+            if (!pi.raw && pi.beta != 0.f)
+                prefetch_tile_rows<CF::BN>(pi.dst, pi.ldd, pi.M, pi.N, pi.tm, pi.tn, q, lane);
+            if constexpr (Src::kEpi == 2)
+                prefetch_tile_rows<CF::BN>(src.ep.aux, src.ep.ldaux, pi.M, pi.N, pi.tm, pi.tn, q,
+                                           lane);
+        };
+        prefetch_unit(blockIdx.x);
         for (int64_t u = blockIdx.x; u < num_units; u += gridDim.x) {
+            prefetch_unit(u + gridDim.x);
             // The TMEM loads below are warp-collective: leave (or stay) as a
             // whole warp even if only some lanes saw their wait expire.
             const bool got = wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull);

@@ -259,6 +259,30 @@ struct UnitInfo {
     bool lower;                   // triangle sources: keep col <= row (else col >= row)
 };
 
+// Asks L2 for the part of a column-major M x N array (leading dimension ld)
+// that epilogue warp q will read for tile (tm, tn): rows tm*128 + 32q ..
+// +31 of the tile's columns, 128 contiguous bytes per column (two lines when
+// they straddle a line boundary). Issued before the tile's accumulator is
+// ready, so that the epilogue's reads of it come from L2, not DRAM.
+__device__ __forceinline__ void prefetch_l2(const float *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <int BN>
+__device__ __forceinline__ void prefetch_tile_rows(const float *base, int64_t ld, int64_t M,
+                                                   int64_t N, int64_t tm, int64_t tn, int q,
+                                                   int lane) {
+    const int64_t r0 = tm * BM + q * 32;
+    if (r0 >= M) return;
+    const int64_t last = (M - 1 - r0 < 31 ? M - 1 - r0 : 31);
+    const int64_t c0 = tn * BN;
+#pragma unroll 1
+    for (int c = lane; c < BN && c0 + c < N; c += 32) {
+        const float *col = base + r0 + (c0 + c) * ld;
+        prefetch_l2(col);
+        prefetch_l2(col + last);
+    }
+}
+
 // One GEMM: units are (tile, K slice) pairs in the grouped raster order.
 // Split units write raw partial sums to `part` (slice s at part + s*M*N,
 // column-major, ld = M); a separate pass reduces them.
