@@ -257,7 +257,6 @@ struct gb_grouped_plan_s {
 namespace {
 
 constexpr int kPlanMagic = 0x47525031;
-constexpr bool kTcRb128 = true;     // short K loops (K <= 1024 in typical groups)
 constexpr int kClasses = 8;
 constexpr int kPrefAuto = -1;
 
@@ -331,10 +330,10 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             const bool so = p.alpha == 0.f || p.k == 0;
             if (p.m == 0 || p.n == 0 || so || route(p, so) != 2 || tc_mode_for(pref, p.k) != 1)
                 continue;
-            const int64_t bn1 = tc_tile_n(1, kTcRb128);
+            const int64_t bn1 = tc_grouped_tile_n();
             x2_tiles += ((p.m + 127) / 128) * ((p.n + bn1 - 1) / bn1);
         }
-        x2_own_launch = x2_tiles >= h->sm_count;
+        x2_own_launch = x2_tiles >= 2 * h->sm_count;   // one round: two CTAs per SM
     }
     for (size_t i = 0; i < ps.size(); ++i) {
         const gb_gemm_problem_t &p = ps[i];
@@ -406,11 +405,11 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         for (size_t j = 0; ok && j < tcs.size(); ++j) {
             const gb_gemm_problem_t &p = ps[tcs[j].prob];
             const int mode = tcs[j].mode;
-            const int bn = tc_tile_n(mode, kTcRb128);
+            const int bn = tc_grouped_tile_n();
             const int64_t kpad = split_kpad(mode, p.k);
             char *pa = base + tcs[j].off_a, *pb = base + tcs[j].off_b;
-            ok = tc_make_operand_map(&maps[2 * j], mode, kTcRb128, pa, p.k, p.m, true) &&
-                 tc_make_operand_map(&maps[2 * j + 1], mode, kTcRb128, pb, p.k, p.n, false);
+            ok = tc_make_grouped_operand_map(&maps[2 * j], mode, pa, p.k, p.m, true) &&
+                 tc_make_grouped_operand_map(&maps[2 * j + 1], mode, pb, p.k, p.n, false);
             TcProblem &t = tprobs[j];
             t.mapA = pl->tc_maps + 2 * j;
             t.mapB = pl->tc_maps + 2 * j + 1;
@@ -493,7 +492,7 @@ int run_plan(gb_grouped_plan_s *plan, void *workspace, cudaStream_t s) {
             return GB_ERR_CUDA;
         for (int md = 0; md < 4; ++md) {
             if (plan->tc_seg_n[md] == 0) continue;
-            if (launch_tc_grouped(md, kTcRb128, plan->tc_probs, plan->tc_items + plan->tc_seg_off[md],
+            if (launch_tc_grouped(md, plan->tc_probs, plan->tc_items + plan->tc_seg_off[md],
                                   plan->tc_seg_n[md], plan->h->sm_count, plan->h->dstate,
                                   plan->h->wait_limit, s) != cudaSuccess)
                 return GB_ERR_CUDA;
@@ -533,11 +532,54 @@ void destroy_plan(gb_grouped_plan_s *plan) {
     delete plan;
 }
 
+// Synthetic square problems of side d over one buffer (A, B, C per problem).
+std::vector<gb_gemm_problem_t> synthetic(float *buf, int64_t g, int64_t d, int64_t first) {
+    const size_t per = (size_t)(3 * d * d);
+    std::vector<gb_gemm_problem_t> ps((size_t)g);
+    for (int64_t i = 0; i < g; ++i) {
+        gb_gemm_problem_t &p = ps[(size_t)i];
+        p.transa = ((first + i) & 1) ? 'T' : 'N';
+        p.transb = ((first + i) & 2) ? 'T' : 'N';
+        p.m = p.n = p.k = d;
+        p.alpha = 1.f; p.beta = 0.f;
+        p.A = buf + per * i; p.lda = d;
+        p.B = buf + per * i + d * d; p.ldb = d;
+        p.C = buf + per * i + 2 * d * d; p.ldc = d;
+    }
+    return ps;
+}
+
+// Best of two timed runs (after a warm-up) of a plan built with `choice`.
+int time_choice(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
+                const int choice[kClasses], void *ws, cudaStream_t s, cudaEvent_t e0,
+                cudaEvent_t e1, float *ms) {
+    gb_grouped_plan_s *pl = nullptr;
+    if (build_plan(h, dev, ps, choice, kPrefAuto, &pl) != GB_OK) return GB_ERR_CUDA;
+    int rc = GB_OK;
+    *ms = 1e30f;
+    for (int rep = 0; rep < 3 && rc == GB_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        if (run_plan(pl, ws, s) != GB_OK) { rc = GB_ERR_CUDA; break; }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) *ms = std::min(*ms, t);
+    }
+    destroy_plan(pl);
+    return rc;
+}
+
 // Autotuner: for each size class, time a synthetic group of square problems
 // of the class's middle size (geometric mean 2^(c+3.5)) under each candidate
 // (SIMT 64x64 tiles, SIMT 128x128 tiles, tensor cores) and keep the fastest.
-// Runs once per handle, on a private stream, with scratch memory freed
-// afterwards; the result is stored in the handle.
+// A class timed alone does not see that its SIMT part and the tensor-core
+// part of a mixed group share the SMs (a SIMT CTA does not fit beside two
+// tensor-core CTAs), so the per-class choice is then checked on one mixed
+// synthetic group (equal problem counts per class, as in a log-uniform
+// group): if routing its SIMT classes to the tensor cores too is faster,
+// they are. Runs once per handle, on a private stream, with scratch memory
+// freed afterwards; the result is stored in the handle.
 int autotune(gb_handle_t h, int dev) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GB_ERR_CUDA;
@@ -557,39 +599,50 @@ int autotune(gb_handle_t h, int dev) {
         const size_t per = (size_t)(3 * d * d);
         if (cudaMalloc(&buf, per * g * sizeof(float)) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
         cudaMemsetAsync(buf, 0x3e, per * g * sizeof(float), s);   // values near 0.19
-        std::vector<gb_gemm_problem_t> ps((size_t)g);
-        for (int64_t i = 0; i < g; ++i) {
-            gb_gemm_problem_t &p = ps[(size_t)i];
-            p.transa = (i & 1) ? 'T' : 'N';
-            p.transb = (i & 2) ? 'T' : 'N';
-            p.m = p.n = p.k = d;
-            p.alpha = 1.f; p.beta = 0.f;
-            p.A = buf + per * i; p.lda = d;
-            p.B = buf + per * i + d * d; p.ldb = d;
-            p.C = buf + per * i + 2 * d * d; p.ldc = d;
-        }
+        const std::vector<gb_gemm_problem_t> ps = synthetic(buf, g, d, 0);
         float best = 1e30f;
         int best_ch = 1;
         for (int ch = 0; ch < 3 && rc == GB_OK; ++ch) {
             int choice[kClasses];
             for (int q = 0; q < kClasses; ++q) choice[q] = ch;
-            gb_grouped_plan_s *pl = nullptr;
-            if (build_plan(h, dev, ps, choice, kPrefAuto, &pl) != GB_OK) { rc = GB_ERR_CUDA; break; }
             float ms = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {          // the first run is a warm-up
-                cudaEventRecord(e0, s);
-                if (run_plan(pl, ws, s) != GB_OK) { rc = GB_ERR_CUDA; break; }
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
-                float t = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (rep > 0) ms = std::min(ms, t);
-            }
-            destroy_plan(pl);
+            rc = time_choice(h, dev, ps, choice, ws, s, e0, e1, &ms);
             if (ms < best) { best = ms; best_ch = ch; }
         }
         cudaFree(buf);
         h->grouped_choice[c] = best_ch;
+    }
+    // The mixed check: 16 problems of each class's middle size (4 of the
+    // largest), about 0.24 GB of scratch.
+    bool any_simt = false;
+    for (int c = 0; c < kClasses; ++c) any_simt |= h->grouped_choice[c] != 2;
+    if (rc == GB_OK && any_simt) {
+        std::vector<gb_gemm_problem_t> mix;
+        std::vector<float *> bufs;
+        for (int c = 0; c < kClasses && rc == GB_OK; ++c) {
+            const int64_t d = (int64_t)llround(pow(2.0, c + 3.5));
+            const int64_t g = c == kClasses - 1 ? 4 : 16;
+            float *buf = nullptr;
+            const size_t bytes = (size_t)(3 * d * d) * g * sizeof(float);
+            if (cudaMalloc(&buf, bytes) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
+            bufs.push_back(buf);
+            cudaMemsetAsync(buf, 0x3e, bytes, s);
+            const std::vector<gb_gemm_problem_t> ps = synthetic(buf, g, d, (int64_t)mix.size());
+            mix.insert(mix.end(), ps.begin(), ps.end());
+        }
+        if (rc == GB_OK) {
+            int tuned[kClasses], all_tc[kClasses];
+            for (int c = 0; c < kClasses; ++c) {
+                tuned[c] = h->grouped_choice[c];
+                all_tc[c] = 2;
+            }
+            float t_tuned = 1e30f, t_tc = 1e30f;
+            rc = time_choice(h, dev, mix, tuned, ws, s, e0, e1, &t_tuned);
+            if (rc == GB_OK) rc = time_choice(h, dev, mix, all_tc, ws, s, e0, e1, &t_tc);
+            if (rc == GB_OK && t_tc < t_tuned)
+                for (int c = 0; c < kClasses; ++c) h->grouped_choice[c] = 2;
+        }
+        for (float *b : bufs) cudaFree(b);
     }
     cudaFree(ws);
     cudaEventDestroy(e0);

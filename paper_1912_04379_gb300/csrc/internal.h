@@ -179,7 +179,11 @@ bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k);
 // kernel variant (mode, 128-byte rows or not); a_side selects the box height.
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
                          int64_t rows, bool a_side);
-cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, const TcItem *items,
+// The grouped kernel's tile width (128 for every split) and operand maps.
+int tc_grouped_tile_n();
+bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, const void *packed, int64_t k,
+                                 int64_t rows, bool a_side);
+cudaError_t launch_tc_grouped(int mode, const TcProblem *probs, const TcItem *items,
                               int64_t nitems, int sm_count, DeviceState *dstate,
                               int64_t wait_limit, cudaStream_t s);
 

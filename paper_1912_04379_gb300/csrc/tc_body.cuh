@@ -13,7 +13,9 @@ namespace tcx {
 constexpr int NUM_THREADS = 192;
 
 // ----------------------------------------------------------- the kernel --
-template <int MODE, int RB>
+// BNX != 0 fixes the tile width; BUDGET_KB is the shared memory the stages
+// may take (the one-GEMM kernels: 216 KiB, one CTA per SM).
+template <int MODE, int RB, int BNX = 0, int BUDGET_KB = 216>
 struct Cfg {
     static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
     static constexpr bool TF32 = MODE == 0;
@@ -22,7 +24,7 @@ struct Cfg {
     // 256 output columns per tile, except 3-term operands with 128-byte rows
     // (a 256-column stage would be 144 KiB: one stage only), which use 128.
     // Wider tiles halve the MMA's re-reads of A from shared memory per flop.
-    static constexpr int BN = (MODE >= 2 && RB == 128) ? 128 : 256;
+    static constexpr int BN = BNX ? BNX : (MODE >= 2 && RB == 128) ? 128 : 256;
     static constexpr int ELEM = TF32 ? 4 : 2;
     static constexpr int BK = ROW_BYTES / ELEM;          // elements per k-block
     static constexpr int KSTEP_BYTES = 32;               // K per MMA: 16 BF16 / 8 TF32
@@ -30,7 +32,7 @@ struct Cfg {
     static constexpr int A_TILE = BM * ROW_BYTES;        // bytes of one term's A tile
     static constexpr int B_TILE = BN * ROW_BYTES;
     static constexpr int STAGE_BYTES = PARTS * (A_TILE + B_TILE);
-    static constexpr int STAGES = (216 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = (BUDGET_KB * 1024) / STAGE_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
     static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
     static_assert(STAGES >= 2, "need at least two stages");
@@ -62,9 +64,16 @@ struct GroupSource {
     }
 };
 
-template <int MODE, int RB, class Src>
+// Grouped runs: 128 x 128 tiles of 64-byte rows in 96 KiB of stages, so that
+// two CTAs share an SM (two 256-column TMEM allocations, 2 x 99.6 KB of
+// shared memory): many small tiles are latency-bound, and a second CTA per
+// SM runs its own load / MMA / epilogue pipeline beside the first.
+template <int MODE>
+using GroupedCfg = Cfg<MODE, 64, 128, 96>;
+
+template <int MODE, int RB, class Src, class CF = Cfg<MODE, RB>>
 __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uint64_t limit_ns) {
-    using CF = Cfg<MODE, RB>;
+    static_assert(CF::ROW_BYTES == RB, "configuration row width");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;

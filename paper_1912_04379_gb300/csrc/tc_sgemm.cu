@@ -69,13 +69,13 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     tc_body<MODE, RB>(src, dstate, limit_ns);
 }
 
-template <int MODE, int RB>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+template <int MODE>
+__global__ void __launch_bounds__(NUM_THREADS, 2)
 tc_grouped_kernel(const TcProblem *__restrict__ probs, const TcItem *__restrict__ items,
                   int64_t nitems, DeviceState *dstate, uint64_t limit_ns) {
-    using CF = Cfg<MODE, RB>;
+    using CF = GroupedCfg<MODE>;
     GroupSource<CF::BN, CF::BK> src{probs, items, nitems};
-    tc_body<MODE, RB>(src, dstate, limit_ns);
+    tc_body<MODE, CF::ROW_BYTES, GroupSource<CF::BN, CF::BK>, CF>(src, dstate, limit_ns);
 }
 
 // C = alpha * (sum over slices s = 0..S-1, in that order, of part_s) + beta*C
@@ -163,25 +163,25 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
 }
 
-template <int MODE, int RB>
+template <int MODE>
 cudaError_t launch_grouped_mode(const TcProblem *probs, const TcItem *items, int64_t nitems,
                                 int sm_count, DeviceState *dstate, int64_t wait_limit,
                                 cudaStream_t s) {
-    using CF = Cfg<MODE, RB>;
+    using CF = GroupedCfg<MODE>;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MODE, RB>,
+        cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
-    int grid = sm_count > 0 ? sm_count : 1;
+    int grid = sm_count > 0 ? 2 * sm_count : 1;           // two CTAs per SM
     if (nitems < grid) grid = (int)nitems;
-    tc_grouped_kernel<MODE, RB><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+    tc_grouped_kernel<MODE><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
         probs, items, nitems, dstate, (uint64_t)wait_limit * 1000ull);
     return cudaGetLastError();
 }
@@ -209,19 +209,27 @@ bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *pac
                     a_side ? BM : tc_tile_n(mode, rb128), bk, rb);
 }
 
-cudaError_t launch_tc_grouped(int mode, bool rb128, const TcProblem *probs, const TcItem *items,
+int tc_grouped_tile_n() { return GroupedCfg<1>::BN; }
+
+bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, const void *packed, int64_t k,
+                                 int64_t rows, bool a_side) {
+    constexpr int rb = GroupedCfg<1>::ROW_BYTES;
+    static_assert(GroupedCfg<0>::ROW_BYTES == rb && GroupedCfg<2>::ROW_BYTES == rb &&
+                  GroupedCfg<0>::BN == GroupedCfg<2>::BN, "one grouped layout for every split");
+    const bool tf32 = mode == 0;
+    return make_map(map, tf32, packed, k, rows, split_kpad(mode, k), split_parts(mode),
+                    a_side ? BM : tc_grouped_tile_n(), rb / (tf32 ? 4 : 2), rb);
+}
+
+cudaError_t launch_tc_grouped(int mode, const TcProblem *probs, const TcItem *items,
                               int64_t nitems, int sm_count, DeviceState *dstate,
                               int64_t wait_limit, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     switch (mode) {
-        case 0: return rb128 ? launch_grouped_mode<0, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
-                             : launch_grouped_mode<0, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 1: return rb128 ? launch_grouped_mode<1, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
-                             : launch_grouped_mode<1, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 2: return rb128 ? launch_grouped_mode<2, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
-                             : launch_grouped_mode<2, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 3: return rb128 ? launch_grouped_mode<3, 128>(probs, items, nitems, sm_count, dstate, wait_limit, s)
-                             : launch_grouped_mode<3, 64>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 0: return launch_grouped_mode<0>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 1: return launch_grouped_mode<1>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 2: return launch_grouped_mode<2>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 3: return launch_grouped_mode<3>(probs, items, nitems, sm_count, dstate, wait_limit, s);
         default: return cudaErrorInvalidValue;
     }
 }
