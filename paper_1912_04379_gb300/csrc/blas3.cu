@@ -386,6 +386,7 @@ int64_t trsm_split_point(int64_t nn) {
     return (h + kTLeaf - 1) / kTLeaf * kTLeaf;
 }
 
+// SSYRK's split: every diagonal leaf starts at a multiple of 128 rows.
 int64_t split_point(int64_t nn) {
     const int64_t h = nn / 2;
     return (h + kLeaf - 1) / kLeaf * kLeaf;
@@ -474,7 +475,7 @@ struct TrsmCtx {
     float *B;
     int64_t ldb;
     int sm_count;
-    const float *prep;      // every leaf's L' and D (kPrepFloats per 128 rows)
+    const float *prep;      // every leaf's L' and D (kPrepFloats per 256 rows)
 };
 
 // op(A)[R0.., S0..] as a GEMM operand (pointer, trans flag)
