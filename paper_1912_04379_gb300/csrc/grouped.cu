@@ -525,6 +525,18 @@ void gb::destroy_side(gb_handle_t h) {
 
 namespace {
 
+// The side stream and fork/join events of plans with both parts, created
+// once per handle.
+bool ensure_side(gb_handle_t h) {
+    if (h->side_ready) return true;
+    if (cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side_event[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side_event[1], cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    h->side_ready = true;
+    return true;
+}
+
 void destroy_plan(gb_grouped_plan_s *plan) {
     cudaDeviceSynchronize();
     free_plan_memory(plan);
@@ -616,6 +628,8 @@ int autotune(gb_handle_t h, int dev) {
     // largest), about 0.24 GB of scratch.
     bool any_simt = false;
     for (int c = 0; c < kClasses; ++c) any_simt |= h->grouped_choice[c] != 2;
+    // a mixed plan runs its two parts concurrently only on the side stream
+    if (rc == GB_OK && any_simt && !ensure_side(h)) rc = GB_ERR_CUDA;
     if (rc == GB_OK && any_simt) {
         std::vector<gb_gemm_problem_t> mix;
         std::vector<float *> bufs;
@@ -705,14 +719,9 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
     gb_grouped_plan_s *pl = nullptr;
     int rc = build_plan(h, dev, ps, choice, pref, &pl);
     if (rc) return rc;
-    if (pl->tc_nitems > 0 && pl->nitems > 0 && !h->side_ready) {
-        if (cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->side_event[0], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->side_event[1], cudaEventDisableTiming) != cudaSuccess) {
-            destroy_plan(pl);
-            return GB_ERR_CUDA;
-        }
-        h->side_ready = true;
+    if (pl->tc_nitems > 0 && pl->nitems > 0 && !ensure_side(h)) {
+        destroy_plan(pl);
+        return GB_ERR_CUDA;
     }
     *ws_bytes = 256;         // the SIMT work counter
     *plan = pl;
