@@ -114,3 +114,29 @@ def test_no_handle_without_gpu_or_bad_handle():
     assert lib.gb_destroy(None) == 0
     assert lib.gb_set_wait_limit(None, 10) == _lib.GB_ERR_HANDLE
     assert lib.gb_sgemm_grouped_destroy(None) == 0
+
+
+def test_blas3_and_split_k_workspace_sizes():
+    """Workspace sizes that follow from the library's layout rules, with no GPU:
+    STRSM lays out every 256-row diagonal block's triangle and reciprocals
+    (256 x 128 + 128 x 128 floats, then 256) after the GEMM updates' area
+    (none for SIMT); BF16 x 3 terms keeps 256-column tiles for K > 2048, so a
+    64 x 8192 output (32 tiles) with K = 8192 is cut into 4 K-slices of FP32
+    partials, while at K = 2048 its 128-column tiles (64 of them) are enough."""
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    simt = _lib.ALGOS["simt"]
+    per_leaf = (256 * 128 + 128 * 128 + 256) * 4
+    for side, uplo, tr, diag, m, n, leaves in (("L", "L", "N", "N", 300, 50, 2),
+                                               ("R", "U", "T", "U", 10, 513, 3),
+                                               ("L", "U", "N", "N", 256, 1, 1),
+                                               ("L", "L", "N", "N", 0, 5, 0)):
+        assert lib.gb_strsm_workspace_size(simt, side.encode(), uplo.encode(), tr.encode(),
+                                           diag.encode(), m, n, ctypes.byref(out)) == 0
+        assert out.value == leaves * per_leaf
+    x6 = _lib.ALGOS["bf16x6"]
+    packed = lambda rows, k: 3 * 2 * k * rows            # three BF16 terms, K padded to 8
+    assert lib.gb_sgemm_workspace_size(x6, b"N", b"N", 64, 8192, 8192, ctypes.byref(out)) == 0
+    assert out.value == packed(64, 8192) + packed(8192, 8192) + 4 * 64 * 8192 * 4
+    assert lib.gb_sgemm_workspace_size(x6, b"N", b"N", 64, 8192, 2048, ctypes.byref(out)) == 0
+    assert out.value == packed(64, 2048) + packed(8192, 2048)
