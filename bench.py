@@ -782,10 +782,39 @@ def run_ours(args, rank, world, local_rank):
     s1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(s0.elapsed_time(s1) / e2e_steps)
+    # The host link alone on this machine: the step's uploads (A, B) on one stream
+    # and its download (C) on another, at once, with no GEMM; a lower bound
+    # for the step above, which varies from box to box with the link.
+    A_l = torch.empty_like(A_h, device=dev)
+    B_l = torch.empty_like(B_h, device=dev)
+    C_l = torch.zeros(C_h.shape, dtype=torch.float32, device=dev)
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def transfers():
+        s_up.wait_stream(stream)
+        s_down.wait_stream(stream)
+        with torch.cuda.stream(s_up):
+            A_l.copy_(A_h, non_blocking=True)
+            B_l.copy_(B_h, non_blocking=True)
+        with torch.cuda.stream(s_down):
+            C_h.copy_(C_l, non_blocking=True)
+        stream.wait_stream(s_up)
+        stream.wait_stream(s_down)
+
+    transfers()
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(3):
+        transfers()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    link_ms = s0.elapsed_time(s1) / 3
+    del A_l, B_l, C_l
     e2e = {"value": whole_job_value(flops, e2e_ms, world), "unit": "TFLOP/s",
            "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4,
-           "d2h_bytes_per_step": C_h.numel() * 4}
+           "d2h_bytes_per_step": C_h.numel() * 4,
+           "transfers_only_ms": link_ms}
 
     grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
     shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
