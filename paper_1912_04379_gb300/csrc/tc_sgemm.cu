@@ -20,13 +20,16 @@
 //     (TMEM), two of them so the epilogue of one tile overlaps the next;
 //   * L1 staging + prefetch -> a ring of shared-memory stages filled by TMA
 //     (cp.async.bulk.tensor) ahead of the MMAs, handshaken with mbarriers:
-//     four 48 KiB stages of 64-byte rows (64-byte swizzle) for long K loops,
-//     two 96 KiB stages of 128-byte rows (128-byte swizzle) for short ones;
+//     64-byte rows (64-byte swizzle) in four 48 KiB stages for two terms or
+//     three 72 KiB stages for three, or 128-byte rows (128-byte swizzle) in
+//     two 96 KiB stages for the shapes tc_rb128() picks (K <= 128, short
+//     3-term GEMMs with few tiles);
 //   * the inner loop        -> tcgen05.mma (M = 128, N = BN, K = 16 BF16 or
 //     8 TF32 per instruction) issued by one thread;
-//   * L2 blocking           -> a persistent grid (one CTA per SM) walking the
-//     output tiles in groups of 16 M-tiles so concurrently running CTAs
-//     share A and B panels in L2.
+//   * L2 blocking           -> a persistent grid (one CTA per SM; two with the
+//     grouped kernel's smaller configuration) walking the output tiles in
+//     groups of 16 M-tiles so concurrently running CTAs share A and B panels
+//     in L2.
 // Warp roles in a 192-thread CTA: warp 0 = TMA producer, warp 1 = TMEM owner
 // and MMA issuer, warps 2..5 = epilogue (TMEM -> registers -> global).
 //
