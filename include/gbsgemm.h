@@ -308,7 +308,7 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
  * the FP32 operands once and needs no operand workspace (the workspace is
  * still required for split-K partials). It consumes K in 32-element stages,
  * so for K > 2048 its results are bit-identical to the two-pass form's. It
- * is off by default because it is slower on this build: its in-place
+ * is off by default because it measured slower than the two-pass form: its in-place
  * conversion moves each operand stage through shared memory three times
  * (9.2 ms against 1.9 ms at M = N = K = 8192). */
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
