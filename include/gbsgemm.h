@@ -128,7 +128,11 @@ GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char transa, char transb,
  * `workspace` of at least gb_sgemm_workspace_size() bytes, 256-byte aligned
  * (GB_ERR_WORKSPACE otherwise); SIMT ignores it. Enqueues on `stream` and
  * returns without waiting. A bounded-wait timeout inside a tensor-core
- * kernel is reported by gb_get_device_error, not by this call. */
+ * kernel is reported by gb_get_device_error, not by this call. The split
+ * kernels choose their shared-memory row width (64 or 128 bytes of K per
+ * row) by shape; the environment variable GB_SGEMM_TC_ROW_BYTES = 64 or 128,
+ * read once per process, forces one of them (results stay within the same
+ * bound; the order of the term products within a k-block differs). */
 GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb,
                     int64_t m, int64_t n, int64_t k,
                     float alpha, const float *A, int64_t lda,
