@@ -145,13 +145,44 @@ split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
                       (int64_t)blockIdx.x * 64, T);
 }
 
+// A K-contiguous 64 x 64 tile straight from registers: each thread loads four
+// consecutive k of a row (as pack_tile64 would) and splits and stores exactly
+// those, so the shared-memory round trip and its barriers are not needed.
+template <int MODE>
+__device__ __forceinline__ void pack_tile64_kc_direct(const PackItem &it) {
+    const int t = threadIdx.x;
+    const int l4 = (t & 15) * 4, l16 = t >> 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int64_t rr = it.r0 + l16 + 16 * e, pp = it.p0 + l4;
+        if (rr >= it.rows || pp >= it.kpad) continue;
+        const float *src = it.X + pp + rr * it.ld;
+        float v[4];
+        if (it.vec && pp + 3 < it.k) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(src));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = pp + i < it.k ? __ldg(src + i) : 0.f;
+        }
+        split_store4<MODE>(v, it.out, it.ps, rr * it.kpad + pp);
+    }
+}
+
 // Grouped pass: each CTA walks a list of 64 x 64 tiles of many operands,
-// each tile with its own split mode (the branch is uniform over the CTA).
+// each tile with its own split mode and source order (both branches are
+// uniform over the CTA; only the rows-contiguous tiles use shared memory).
 __global__ void __launch_bounds__(256)
 split_pack_grouped_kernel(const PackItem *__restrict__ items, int64_t nitems) {
     __shared__ float T[64][65];
     for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
         const PackItem it = items[i];
+        if (it.kc) {
+            if (it.mode == 0)      pack_tile64_kc_direct<0>(it);
+            else if (it.mode == 1) pack_tile64_kc_direct<1>(it);
+            else                   pack_tile64_kc_direct<2>(it);
+            continue;
+        }
         if (it.mode == 0)
             pack_tile64<0>(it.X, it.ld, it.kc != 0, it.vec != 0, it.rows, it.k, it.out, it.kpad,
                            it.ps, it.r0, it.p0, T);
