@@ -33,3 +33,26 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_record_follows_the_kernel_code_not_its_comments():
+    """The recorded DRAM traffic of the timed kernel is keyed to a hash of its
+    sources without comments: a comment edit keeps the key, a code edit does
+    not (bench.py then reports the traffic as null until it is recaptured)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    src = {}
+    for f in bench.KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1912_04379_gb300", "csrc", f)) as fh:
+            src[f] = fh.read()
+    base = bench.source_sha(lambda f: src[f])
+    assert base == bench.source_sha()
+    commented = dict(src)
+    commented["tc_body.cuh"] = "// a new comment\n" + src["tc_body.cuh"].replace(
+        "#pragma once", "#pragma once  /* block comment */\n\n// line comment")
+    assert bench.source_sha(lambda f: commented[f]) == base
+    changed = dict(src)
+    changed["tc_body.cuh"] = src["tc_body.cuh"] + "\nconstexpr int kUnusedProbe = 1;\n"
+    assert bench.source_sha(lambda f: changed[f]) != base
