@@ -17,7 +17,9 @@ from . import api
 
 
 def _as_colmajor(t):
-    """A column-major (stride(0) == 1) float32 CUDA tensor with the same values."""
+    """The same values as a column-major (stride(0) == 1) tensor, on the same
+    device and in the same dtype; anything but a float32 CUDA tensor is then
+    rejected by the SGEMM call (there is no CPU path)."""
     if t.dim() == 2 and (t.stride(0) == 1 or t.shape[0] <= 1) and t.is_cuda and \
             t.dtype == torch.float32:
         return t
