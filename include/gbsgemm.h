@@ -106,7 +106,9 @@ GB_API int gb_version(void);
 GB_API const char *gb_status_string(int status);
 
 /* Create a handle bound to the CURRENT CUDA device. Allocates a few hundred
- * bytes of device memory for the device error word and scratch counters.
+ * bytes of device memory for the device error word and scratch counters,
+ * and looks up the device address of gb_sgemm_noalloc's static scratch
+ * array (the first handle on a device thereby reserves its 32 MiB).
  * Returns GB_ERR_UNSUPPORTED if the device is not compute capability 10.3,
  * GB_ERR_CUDA if no device is usable, GB_ERR_ARG if h is NULL. */
 GB_API int gb_create(gb_handle_t *h);
@@ -153,15 +155,15 @@ GB_API int gb_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb,
  * (32 MiB) in device memory that belongs to the library, and the call
  * allocates nothing (no cudaMalloc, no cudaFree, no allocating library
  * routine). The caller still owns and passes A, B and C.
- * - Every GPU that loads the library keeps those 32 MiB reserved until the
- *   process exits.
+ * - The 32 MiB are reserved on a device when the first handle is created
+ *   there (gb_create looks up the array's device address with that device
+ *   current and keeps it in the handle) and stay reserved until the process
+ *   exits. The call itself loads nothing and looks nothing up. A handle does
+ *   not survive a reset of its device (cudaDeviceReset): create a new one.
  * - Returns GB_ERR_WORKSPACE, with nothing enqueued, when the problem's
  *   split workspace (gb_sgemm_workspace_size) is larger than
  *   GB_STATIC_SCRATCH_BYTES, e.g. BF16X3 fits M = N = K = 2048. SIMT needs
  *   no workspace and has no size limit here.
- * - The first call on a device looks up the array's device address (once
- *   per device, with that device current); make that first call before any
- *   stream capture.
  * - All calls share the one array. Each call overwrites every byte of it
  *   that it reads, so no state carries over, but calls whose executions
  *   overlap on the GPU (different streams, or different host threads) race

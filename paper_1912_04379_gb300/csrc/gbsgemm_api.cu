@@ -291,6 +291,14 @@ GB_API int gb_create(gb_handle_t *out) {
         delete h;
         return GB_ERR_CUDA;
     }
+    // gb_sgemm_noalloc's scratch array: looked up here, at set-up, so that it
+    // is reserved on this device now and its calls never load anything.
+    if (gb::noalloc_scratch_lookup(&h->noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->dstate);
+        delete h;
+        return GB_ERR_CUDA;
+    }
     *out = h;
     return GB_OK;
 }

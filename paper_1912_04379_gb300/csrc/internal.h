@@ -52,6 +52,9 @@ struct gb_handle_s {
     bool side_ready;
     cudaStream_t side_stream;
     cudaEvent_t side_event[2];
+    // device address of gb_sgemm_noalloc's static scratch array on this
+    // handle's device, looked up by gb_create (null if that failed)
+    void *noalloc_scratch;
 };
 
 namespace gb {
@@ -60,6 +63,9 @@ constexpr int kHandleMagic = 0x6b5e3a21;
 constexpr int kPipeEvents = 8;
 void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events
 void destroy_side(gb_handle_t h);     // releases the grouped runs' side stream and events
+// Device address of gb_sgemm_noalloc's static scratch array on the current
+// device (loads the module that holds it, which reserves the array there).
+cudaError_t noalloc_scratch_lookup(void **addr);
 
 // ------------------------------------------------------------------ SIMT --
 struct SimtArgs {

@@ -11,39 +11,28 @@
 // workspace lives in one fixed array in device global memory that is part
 // of the library itself, so the call allocates nothing.
 //
-// The array is GB_STATIC_SCRATCH_BYTES (32 MiB) of device memory that every
-// GPU which loads this library keeps reserved until the process exits.
-// Host code must not use the array's name as a device address (on the host
-// it names a stand-in object); its device address is obtained once per
-// device with cudaGetSymbolAddress and handed to the kernels.
-#include <mutex>
-
+// The array is GB_STATIC_SCRATCH_BYTES (32 MiB) of device memory. Its
+// module is loaded on a device, and the array reserved there until the
+// process exits, when gb_create looks up the array's device address with
+// that device current; the address is kept in the handle. Host code must not
+// use the array's name as a device address (on the host it names a stand-in
+// object): only the looked-up address is handed to the kernels.
 #include "internal.h"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_split_scratch[GB_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_split_scratch on the current device, looked up once
-// per device (with that device current) and cached.
-int scratch_address(int dev, void **out) {
-    if (dev < 0 || dev >= kMaxDevices) return GB_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_split_scratch);
-        if (e != cudaSuccess || !p) return GB_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return GB_OK;
-}
-
 }  // namespace
+
+cudaError_t gb::noalloc_scratch_lookup(void **addr) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_split_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    *addr = p;
+    return cudaSuccess;
+}
 
 extern "C" GB_API int gb_sgemm_noalloc(gb_handle_t h, gb_algo_t algo, char transa, char transb,
                                        int64_t m, int64_t n, int64_t k, float alpha,
@@ -54,12 +43,7 @@ extern "C" GB_API int gb_sgemm_noalloc(gb_handle_t h, gb_algo_t algo, char trans
     if (rc) return rc;
     if (need > (size_t)GB_STATIC_SCRATCH_BYTES) return GB_ERR_WORKSPACE;
     if (!h || h->magic != gb::kHandleMagic) return GB_ERR_HANDLE;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
-    if (dev != h->device) return GB_ERR_HANDLE;
-    void *scratch = nullptr;
-    rc = scratch_address(dev, &scratch);
-    if (rc) return rc;
+    if (!h->noalloc_scratch) return GB_ERR_CUDA;
     return gb_sgemm(h, algo, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                    scratch, (size_t)GB_STATIC_SCRATCH_BYTES, stream);
+                    h->noalloc_scratch, (size_t)GB_STATIC_SCRATCH_BYTES, stream);
 }

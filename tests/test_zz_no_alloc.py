@@ -6,10 +6,12 @@ library a workspace. gb_sgemm_noalloc runs the same split-precision kernels
 as gb_sgemm with its workspace in a fixed 32 MiB array inside the library.
 This file checks, through the C ABI, that two calls in a row (different
 shapes, transposes and data, so the second call must not depend on what the
-first left in the shared array) give the same result as gb_sgemm within the
-tests' error bound, and that a problem too large for the array is refused
-with GB_ERR_WORKSPACE and no write to C. It is named so that pytest collects
-it last.
+first left in the shared array) give bit for bit the result of gb_sgemm
+(same kernels, same routing, fixed-order split-K reduce) and stay within the
+tests' error bound, that the call takes no device memory once the handle
+exists, and that a problem too large for the array is refused with
+GB_ERR_WORKSPACE and no write to C. It is named so that pytest collects it
+last.
 """
 import numpy as np
 import pytest
@@ -54,6 +56,7 @@ def test_noalloc_matches_gb_sgemm_on_two_calls_in_a_row(algo):
     torch.cuda.synchronize()
     for p, _, _, C_new, C_ref in dev:
         new, ref = gb.to_fortran(C_new), gb.to_fortran(C_ref)
+        assert np.array_equal(new, ref), "gb_sgemm_noalloc differs from gb_sgemm"
         C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb,
                               p.beta, p.C, p.ldc)
         bound = oracle.bound(D, p.k, SPLIT_EXTRA[algo])
@@ -62,6 +65,28 @@ def test_noalloc_matches_gb_sgemm_on_two_calls_in_a_row(algo):
         assert_within_bound(p, new, algo=algo)
         assert np.all(new[p.m:] == wl.CANARY)
     assert h.device_error() == (0, 0)
+
+
+def test_noalloc_takes_no_device_memory_after_handle_creation():
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    h = gb.Handle()
+    p = wl.make_problem("N", "N", 640, 384, 1100, 1.0, 0.0, seed=53)   # beta = 0: repeat calls agree
+    _, A = gb.from_fortran(p.A)
+    _, B = gb.from_fortran(p.B)
+    C_ref, _ = gb.from_fortran(p.C)
+    C_new, _ = gb.from_fortran(p.C)
+    # gb_sgemm once first, so that every kernel module the call launches is loaded
+    gb.sgemm_raw(p.ta, p.tb, p.m, p.n, p.k, p.alpha, A.data_ptr(), p.lda, B.data_ptr(), p.ldb,
+                 p.beta, C_ref.data_ptr(), p.ldc, algo="bf16x3", handle=h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert _noalloc(h, "bf16x3", p, A, B, C_new) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device memory changed by {free0 - free1} bytes"
+    assert np.array_equal(gb.to_fortran(C_new), gb.to_fortran(C_ref))
 
 
 def test_noalloc_refuses_problems_larger_than_the_static_array():
