@@ -319,6 +319,28 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
  * (9.2 ms against 1.9 ms at M = N = K = 8192). */
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 
+/* Promoted accumulation in the split algorithms' tensor-core kernel
+ * (default 0 = off). The tensor cores add the term products of a tile into
+ * an FP32 accumulator in tensor memory, and that addition is not IEEE
+ * round-to-nearest: it truncates, so its errors share a sign and grow with
+ * the number of accumulation steps. With k_chunk > 0 the kernel starts a
+ * fresh accumulator for every k_chunk elements of K (rounded up to whole
+ * k-blocks of 32 elements for the BF16 splits, 16 for TF32X3) and adds the
+ * finished chunks on the CUDA cores in FP32 with round-to-nearest, in K
+ * order, into a running sum kept in registers; the α/β epilogue then reads
+ * that sum. The truncation then acts only within a chunk. The product is
+ * the same (paper Sec. 1); only the order and rounding of the additions
+ * change, so every algorithm keeps its error bound, and the measured error
+ * falls (see the accuracy report of the benchmark). With k_chunk >= K the
+ * result equals the unpromoted kernel's with 64-byte rows bit for bit.
+ * Applies to gb_sgemm, gb_sgemm_compute, gb_sgemm_backward, gb_sgemm_host
+ * and the GEMMs inside gb_strsm and the training step (which then apply
+ * their elementwise operations in separate passes); grouped runs, gb_ssyrk
+ * and the fused in-kernel split (gb_set_fused_split) do not promote.
+ * GB_ERR_ARG for k_chunk < 0. gb_get_promotion reads the setting back. */
+GB_API int gb_set_promotion(gb_handle_t h, int64_t k_chunk);
+GB_API int gb_get_promotion(gb_handle_t h, int64_t *k_chunk);
+
 /* Device workspace bytes gb_sgemm_host needs for this problem. */
 GB_API int gb_sgemm_host_workspace_size(gb_algo_t algo, char transa, char transb, int64_t m,
                                         int64_t n, int64_t k, size_t *bytes);

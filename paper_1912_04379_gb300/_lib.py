@@ -84,6 +84,8 @@ SIGNATURES = {
     "gb_get_device_error": ([c_vp, c_vp, ctypes.POINTER(c_int)], c_int),
     "gb_set_wait_limit": ([c_vp, c_i64], c_int),
     "gb_set_fused_split": ([c_vp, c_int], c_int),
+    "gb_set_promotion": ([c_vp, c_i64], c_int),
+    "gb_get_promotion": ([c_vp, ctypes.POINTER(c_i64)], c_int),
     "gb_mlp_workspace_size": ([c_int, ctypes.POINTER(MlpDesc), c_int, ctypes.POINTER(c_size)],
                               c_int),
     "gb_mlp_forward": ([c_vp, c_int, ctypes.POINTER(MlpDesc), ctypes.POINTER(c_vp),

@@ -102,6 +102,16 @@ class Handle:
         """Allow (default) or forbid the split fused into the tensor-core kernel."""
         _lib.check("gb_set_fused_split", self.lib.gb_set_fused_split(self.h, 1 if enable else 0))
 
+    def set_promotion(self, k_chunk: int):
+        """Promoted accumulation: a fresh tensor-core accumulator every k_chunk
+        elements of K, chunks added in FP32 round-to-nearest (0 = off)."""
+        _lib.check("gb_set_promotion", self.lib.gb_set_promotion(self.h, int(k_chunk)))
+
+    def promotion(self) -> int:
+        v = ctypes.c_int64(0)
+        _lib.check("gb_get_promotion", self.lib.gb_get_promotion(self.h, ctypes.byref(v)))
+        return v.value
+
     def set_wait_limit(self, microseconds: int):
         _lib.check("gb_set_wait_limit", self.lib.gb_set_wait_limit(self.h, int(microseconds)))
 

@@ -131,6 +131,11 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     t.wait_limit = h->wait_limit;
     t.sm_count = h->sm_count;
     if (epi) t.epi = *epi;
+    if (h->promote_k > 0) {
+        const int64_t bk = tc_promo_kblock(mode);
+        const int64_t kb = (h->promote_k + bk - 1) / bk;
+        t.promote_kb = (int)(kb < 1 ? 1 : kb > (1 << 24) ? (1 << 24) : kb);
+    }
     cudaError_t e = launch_tc_sgemm(t, s);
     return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
 }
@@ -162,7 +167,7 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     // Split fused into the tensor-core kernel, when the handle allows it and
     // TMA can read A and B as they are; otherwise the separate split/pack
     // pass. For K > 2048 both give bit-identical results.
-    if (h->fused_split && fused_supported(mode, A, lda, B, ldb, m, n, k)) {
+    if (h->fused_split && h->promote_k == 0 && fused_supported(mode, A, lda, B, ldb, m, n, k)) {
         FusedArgs f{};
         f.mode = mode;
         f.ta = is_trans(ta); f.tb = is_trans(tb);
@@ -199,7 +204,7 @@ int gb::sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, in
     if ((rc = check_handle(h))) return rc;
     const int mode = (alpha == 0.f || k == 0) ? -1 : split_mode(resolve_algo(algo, k));
     const bool can_fuse = op.kind != 0 && m > 0 && n > 0 && A && B && C && (mode == 1 || mode == 2) &&
-                          split_k_factor(mode, m, n, k) == 1;
+                          split_k_factor(mode, m, n, k) == 1 && h->promote_k == 0;
     if (!can_fuse)
         return sgemm_impl(h, algo, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws,
                           ws_bytes, s);
@@ -478,6 +483,20 @@ GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site) {
 GB_API int gb_set_fused_split(gb_handle_t h, int enable) {
     if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
     h->fused_split = enable != 0;
+    return GB_OK;
+}
+
+GB_API int gb_set_promotion(gb_handle_t h, int64_t k_chunk) {
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    if (k_chunk < 0) return GB_ERR_ARG;
+    h->promote_k = k_chunk;
+    return GB_OK;
+}
+
+GB_API int gb_get_promotion(gb_handle_t h, int64_t *k_chunk) {
+    if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
+    if (!k_chunk) return GB_ERR_ARG;
+    *k_chunk = h->promote_k;
     return GB_OK;
 }
 

@@ -43,6 +43,7 @@ struct gb_handle_s {
     bool grouped_tuned;
     int grouped_choice[8];
     bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
+    int64_t promote_k;          // promoted accumulation: chunk length in K (0 = off)
     // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
     bool pipe_ready;
     cudaStream_t pipe_stream[3];
@@ -124,9 +125,14 @@ struct TcArgs {
     int64_t wait_limit;
     int sm_count;
     EpiOp epi;                  // kind != 0: BF16 x 2 or x 3 terms, no split-K
+    int promote_kb;             // > 0: promoted accumulation, k-blocks per chunk
 };
-// cudaErrorNotSupported: an epilogue operation with another mode or split-K.
+// cudaErrorNotSupported: an epilogue operation with another mode or split-K,
+// or with promoted accumulation.
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s);
+// Elements of K in one k-block of the promoted-accumulation kernel (its
+// chunks are whole k-blocks): 16 for TF32 terms, 32 for BF16 terms.
+int tc_promo_kblock(int mode);
 // Number of K slices gb_sgemm uses for a split-precision problem (depends on
 // the shape only, so workspace sizes do not depend on the device).
 int split_k_factor(int mode, int64_t m, int64_t n, int64_t k);

@@ -14,8 +14,12 @@ constexpr int NUM_THREADS = 192;
 
 // ----------------------------------------------------------- the kernel --
 // BNX != 0 fixes the tile width; BUDGET_KB is the shared memory the stages
-// may take (the one-GEMM kernels: 216 KiB, one CTA per SM).
-template <int MODE, int RB, int BNX = 0, int BUDGET_KB = 216>
+// may take (the one-GEMM kernels: 216 KiB, one CTA per SM). PROMO selects
+// promoted accumulation: the MMA warp starts a fresh TMEM accumulator every
+// few k-blocks (a chunk of K) and eight epilogue warps add the finished
+// chunks, in FP32 with round-to-nearest, into a running sum they keep in
+// registers (each warp one TMEM lane quarter and half of the tile's columns).
+template <int MODE, int RB, int BNX = 0, int BUDGET_KB = 216, bool PROMO_ = false>
 struct Cfg {
     static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
     static constexpr bool TF32 = MODE == 0;
@@ -35,6 +39,22 @@ struct Cfg {
     static constexpr int STAGES = (BUDGET_KB * 1024) / STAGE_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
     static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
+    static constexpr bool PROMO = PROMO_;
+    static constexpr int EPI_WARPS = PROMO ? 8 : 4;
+    // Warp roles: 0 = TMA producer, 1 = MMA issuer, then the epilogue warps
+    // from EPI_WARP0. The promoted kernel runs three warpgroups (warps 2-3
+    // idle) so that it can move registers between them (setmaxnreg, which
+    // acts on whole warpgroups): 56 per thread in warpgroup 0, 224 in the
+    // two epilogue warpgroups, which hold the running sums.
+    static constexpr int EPI_WARP0 = PROMO ? 4 : 2;
+    static constexpr int THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
+    static constexpr int ECOLS = BN * 4 / EPI_WARPS;     // columns of one epilogue warp
+    static constexpr int REG_LOW = 56, REG_HIGH = 224;   // promoted: per-thread registers
+    // registers the promoted kernel must be launched with (per thread) so
+    // that the split fits: 128 * REG_LOW + 256 * REG_HIGH <= THREADS * this
+    static constexpr int REG_LAUNCH_MIN = (128 * REG_LOW + 256 * REG_HIGH + THREADS - 1) / THREADS;
+    static_assert(!PROMO || (ECOLS % 32 == 0 && ECOLS <= 128), "promoted epilogue columns");
+    static_assert(!PROMO || THREADS == 384, "promoted kernel: three warpgroups");
     static_assert(STAGES >= 2, "need at least two stages");
     static_assert(SMEM_BYTES <= 232448, "opt-in shared memory per block");
     static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
@@ -71,6 +91,69 @@ struct GroupSource {
 template <int MODE>
 using GroupedCfg = Cfg<MODE, 64, 128, 96>;
 
+// Promoted accumulation for one GEMM: 128 x 256 tiles of 64-byte rows (the
+// long-K configuration of the plain kernel), 320 threads.
+template <int MODE>
+using PromoCfg = Cfg<MODE, 64, 256, 216, true>;
+
+// Waits for this thread's outstanding TMEM loads, with the 32 registers of
+// two 16-column loads as in/out operands (see tmem_wait16).
+__device__ __forceinline__ void tmem_wait32(uint32_t a[16], uint32_t b[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                   "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]),
+                   "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                   "+r"(b[14]), "+r"(b[15])
+                 :
+                 : "memory");
+}
+
+// Stores one epilogue warp's part of a unit's result from registers: row
+// tm*128 + 32q + lane, the EC columns from tn*BN + hcol, value v[j] for
+// column j. C <- alpha*v + beta*C (C not read when beta == 0), or the raw
+// sum for a split-K partial. Same arithmetic as store_tile.
+template <int BN, int EC>
+__device__ __forceinline__ void store_regs(const UnitInfo &ui, const float (&v)[EC], int hcol,
+                                           int q, int lane) {
+    const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
+    const bool part = ui.raw;
+    const float a = part ? 1.f : ui.alpha;
+    const float beta = part ? 0.f : ui.beta;
+    const int64_t row = ui.tm * BM + q * 32 + lane;
+    const int64_t col0 = ui.tn * BN + hcol;
+    float *colp = ui.dst + row + col0 * ldd;
+    if ((ui.tm * BM + BM <= M) && (col0 + EC <= N)) {
+        if (beta == 0.f) {
+#pragma unroll
+            for (int j = 0; j < EC; ++j) { *colp = a * v[j]; colp += ldd; }
+        } else {
+            // the chunk's C values are all read before its first store (a
+            // store may alias a later load)
+#pragma unroll
+            for (int c = 0; c < EC; c += 16) {
+                float cv[16];
+                const float *qc = colp;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { cv[j] = *qc; qc += ldd; }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { *colp = fmaf(a, v[c + j], beta * cv[j]); colp += ldd; }
+            }
+        }
+        return;
+    }
+    if (row >= M || col0 >= N) return;
+    const int ncol = (int)(N - col0 < EC ? N - col0 : EC);
+#pragma unroll
+    for (int j = 0; j < EC; ++j) {
+        if (j < ncol) {
+            float *p = colp + (int64_t)j * ldd;
+            *p = beta != 0.f ? fmaf(a, v[j], beta * *p) : a * v[j];
+        }
+    }
+}
+
 template <int MODE, int RB, class Src, class CF = Cfg<MODE, RB>>
 __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uint64_t limit_ns) {
     static_assert(CF::ROW_BYTES == RB, "configuration row width");
@@ -102,7 +185,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf_bar(b), 1);
-            mbar_init(acce_bar(b), 4);       // one arrive per epilogue warp
+            mbar_init(acce_bar(b), CF::EPI_WARPS);   // one arrive per epilogue warp
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -115,7 +198,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
     const uint32_t tmem_base = *tmem_holder;
     const int64_t num_units = src.num_units();
 
-    if (warp == 0) {
+    auto producer_role = [&]() {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             int stage = 0;
@@ -154,7 +237,8 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
+    };
+    auto mma_role = [&]() {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t idesc = instr_desc<CF::TF32, CF::BN>();
@@ -164,44 +248,77 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-                if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) break;
+            // One k-block: wait for its stage, issue every term pair's MMAs
+            // into d_tmem, free the stage when they finish.
+            auto kblock = [&](uint32_t d_tmem, uint32_t &accumulate) -> bool {
+                if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) return false;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
-                uint32_t accumulate = 0;
-                UnitInfo ui;
-                src.unit(u, ui);
-                for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
-                    if (!wait_bounded(w, full_bar(stage), phase, kSiteMmaFull)) {
-                        ok = false;
-                        break;
+                // The descriptor's start-address field is the byte address
+                // >> 4, so offsetting a descriptor by whole 16-byte units
+                // is an add: one base descriptor per stage and operand,
+                // constant offsets for the term and the k-step.
+                const uint64_t da = desc_a0 + (uint64_t)((stage * CF::PARTS * CF::A_TILE) >> 4);
+                const uint64_t db = desc_b0 + (uint64_t)((stage * CF::PARTS * CF::B_TILE) >> 4);
+#pragma unroll
+                for (int q = 0; q < CF::NPAIRS; ++q) {
+                    int sa, sb;
+                    pair_of<MODE>(q, sa, sb);
+#pragma unroll
+                    for (int ks = 0; ks < CF::KSTEPS; ++ks) {
+                        mma_issue<CF::TF32>(
+                            d_tmem, da + (uint64_t)((sa * CF::A_TILE + ks * CF::KSTEP_BYTES) >> 4),
+                            db + (uint64_t)((sb * CF::B_TILE + ks * CF::KSTEP_BYTES) >> 4), idesc,
+                            accumulate);
+                        accumulate = 1;
                     }
-                    tc_fence_after();
-                    // The descriptor's start-address field is the byte address
-                    // >> 4, so offsetting a descriptor by whole 16-byte units
-                    // is an add: one base descriptor per stage and operand,
-                    // constant offsets for the term and the k-step.
-                    const uint64_t da = desc_a0 + (uint64_t)((stage * CF::PARTS * CF::A_TILE) >> 4);
-                    const uint64_t db = desc_b0 + (uint64_t)((stage * CF::PARTS * CF::B_TILE) >> 4);
-#pragma unroll
-                    for (int q = 0; q < CF::NPAIRS; ++q) {
-                        int sa, sb;
-                        pair_of<MODE>(q, sa, sb);
-#pragma unroll
-                        for (int ks = 0; ks < CF::KSTEPS; ++ks) {
-                            mma_issue<CF::TF32>(
-                                d_tmem, da + (uint64_t)((sa * CF::A_TILE + ks * CF::KSTEP_BYTES) >> 4),
-                                db + (uint64_t)((sb * CF::B_TILE + ks * CF::KSTEP_BYTES) >> 4), idesc,
-                                accumulate);
-                            accumulate = 1;
+                }
+                mma_commit(empty_bar(stage));     // frees the stage once these MMAs finish
+                if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
+                return true;
+            };
+            if constexpr (CF::PROMO) {
+                // Chunks of pk k-blocks, each into a fresh accumulator (the
+                // two TMEM buffers alternate), handed to the epilogue warps
+                // as soon as the chunk's MMAs finish.
+                const int pk = src.chunk_kb;
+                for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                    UnitInfo ui;
+                    src.unit(u, ui);
+                    int rel = 0;
+                    uint32_t d_tmem = 0, accumulate = 0;
+                    for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
+                        if (rel == 0) {
+                            if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
+                            accumulate = 0;
+                        }
+                        if (!kblock(d_tmem, accumulate)) { ok = false; break; }
+                        if (++rel == pk || kb + 1 == ui.kb1) {
+                            mma_commit(accf_bar(acc));    // chunk ready for the epilogue
+                            if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                            rel = 0;
                         }
                     }
-                    mma_commit(empty_bar(stage));     // frees the stage once these MMAs finish
-                    if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
-                mma_commit(accf_bar(acc));            // accumulator ready for the epilogue
-                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+            } else {
+                for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                    if (!wait_bounded(w, acce_bar(acc), acc_phase ^ 1u, kSiteMmaAccEmpty)) break;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::BN);
+                    uint32_t accumulate = 0;
+                    UnitInfo ui;
+                    src.unit(u, ui);
+                    for (int kb = ui.kb0; kb < ui.kb1; ++kb) {
+                        if (!kblock(d_tmem, accumulate)) { ok = false; break; }
+                    }
+                    if (!ok) break;
+                    mma_commit(accf_bar(acc));            // accumulator ready for the epilogue
+                    if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                }
             }
             // Make sure no MMA is still running before TMEM is released.
             mma_commit(drain_bar);
@@ -211,7 +328,68 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             }
         }
         __syncwarp();
-    } else {
+    };
+    auto promo_epilogue_role = [&]() {
+      if constexpr (CF::PROMO) {
+        // ------------- promoted epilogue (warps 4..11) -------------
+        const int q = warp & 3;                       // TMEM lane quarter this warp may read
+        const int hcol = ((warp - CF::EPI_WARP0) >> 2) * CF::ECOLS;   // first tile column
+        const int pk = src.chunk_kb;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        auto prefetch_unit = [&](int64_t v) {
+            if (v >= num_units) return;
+            UnitInfo pi;
+            src.unit(v, pi);
+            if (!pi.raw && pi.beta != 0.f)
+                prefetch_tile_rows<CF::ECOLS>(pi.dst + hcol * pi.ldd, pi.ldd, pi.M,
+                                              pi.N - hcol, pi.tm, pi.tn * (CF::BN / CF::ECOLS),
+                                              q, lane);
+        };
+        prefetch_unit(blockIdx.x);
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            prefetch_unit(u + gridDim.x);
+            int nch;
+            {
+                UnitInfo ui;
+                src.unit(u, ui);
+                const int nkb = ui.kb1 - ui.kb0;
+                nch = nkb > 0 ? (nkb + pk - 1) / pk : 0;
+            }
+            float v[CF::ECOLS];
+#pragma unroll
+            for (int j = 0; j < CF::ECOLS; ++j) v[j] = 0.f;
+            for (int ch = 0; ch < nch; ++ch) {
+                // The TMEM loads are warp-collective: leave as a whole warp.
+                const bool got = wait_bounded(w, accf_bar(acc), acc_phase, kSiteEpiAccFull);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) +
+                                       (uint32_t)(acc * CF::BN + hcol);
+#pragma unroll
+                for (int c = 0; c < CF::ECOLS; c += 16) {
+                    uint32_t ra[16];
+                    tmem_ld16(taddr + (uint32_t)c, ra);
+                    tmem_wait16(ra);
+                    // the chunks are summed in order, each addition rounded
+                    // to nearest (0 + x = x for the first)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[c + j] = __fadd_rn(v[c + j], __uint_as_float(ra[j]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(acc));
+                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+            }
+            if (!ok) break;
+            UnitInfo ui;            // looked up again: not kept live across the chunks
+            src.unit(u, ui);
+            store_regs<CF::BN, CF::ECOLS>(ui, v, hcol, q, lane);
+        }
+      }
+    };
+    auto epilogue_role = [&]() {
         // ---------------- epilogue (warps 2..5) ----------------
         const int q = warp & 3;                       // TMEM lane quarter this warp may read
         int acc = 0;
@@ -249,6 +427,23 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             if (lane == 0) mbar_arrive(acce_bar(acc));
             if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
         }
+    };
+
+    if constexpr (CF::PROMO) {
+        // Registers move between whole warpgroups, so each setmaxnreg sits at
+        // the top of a branch that a whole warpgroup takes.
+        if (warp < 4) {
+            asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CF::REG_LOW));
+            if (warp == 0) producer_role();
+            else if (warp == 1) mma_role();
+        } else {
+            asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(CF::REG_HIGH));
+            promo_epilogue_role();
+        }
+    } else {
+        if (warp == 0) producer_role();
+        else if (warp == 1) mma_role();
+        else epilogue_role();
     }
 
     tc_fence_before();

@@ -300,6 +300,7 @@ struct SingleSource {
     int splits;
     int tiles_m, tiles_n;
     int nkb;
+    int chunk_kb;                 // promoted accumulation: k-blocks per chunk
     __device__ __forceinline__ int64_t num_units() const {
         return (int64_t)tiles_m * tiles_n * splits;
     }

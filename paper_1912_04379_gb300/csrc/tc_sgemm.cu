@@ -72,6 +72,32 @@ tc_sgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     tc_body<MODE, RB>(src, dstate, limit_ns);
 }
 
+// Promoted accumulation: fresh FP32 accumulator every chunk_kb k-blocks,
+// chunks added in FP32 round-to-nearest by eight epilogue warps.
+template <int MODE>
+__global__ void __launch_bounds__(PromoCfg<MODE>::THREADS, 1)
+tc_promo_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
+                int64_t ldc, float *__restrict__ part, int splits, int chunk_kb,
+                DeviceState *dstate, uint64_t limit_ns) {
+    using CF = PromoCfg<MODE>;
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&mapA);
+        prefetch_tmap(&mapB);
+    }
+    SingleSource<CF::BN, CF::BK, 0> src;
+    src.ma = &mapA; src.mb = &mapB;
+    src.M = M; src.N = N; src.K = K;
+    src.alpha = alpha; src.beta = beta;
+    src.C = C; src.ldc = ldc;
+    src.part = part; src.splits = splits;
+    src.tiles_m = (int)((M + BM - 1) / BM);
+    src.tiles_n = (int)((N + CF::BN - 1) / CF::BN);
+    src.nkb = (int)((K + CF::BK - 1) / CF::BK);
+    src.chunk_kb = chunk_kb;
+    tc_body<MODE, CF::ROW_BYTES, SingleSource<CF::BN, CF::BK, 0>, CF>(src, dstate, limit_ns);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 2)
 tc_grouped_kernel(const TcProblem *__restrict__ probs, const TcItem *__restrict__ items,
@@ -161,6 +187,47 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     tc_sgemm_kernel<MODE, RB, EPI><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
         ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, splits > 1 ? a.part : nullptr, splits,
         a.dstate, limit_ns, a.epi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
+}
+
+template <int MODE>
+cudaError_t launch_promo_mode(const TcArgs &a, cudaStream_t s) {
+    using CF = PromoCfg<MODE>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        // The kernel moves registers between its warpgroups (setmaxnreg):
+        // launched with fewer than REG_LAUNCH_MIN per thread, the epilogue
+        // warpgroups' request could never be met. Refuse rather than launch.
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, tc_promo_kernel<MODE>);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs < CF::REG_LAUNCH_MIN || fa.maxThreadsPerBlock < CF::THREADS)
+            return cudaErrorNotSupported;
+        e = cudaFuncSetAttribute(tc_promo_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CF::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
+        return cudaErrorNotSupported;
+    alignas(64) CUtensorMap ma, mb;
+    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK, CF::ROW_BYTES) ||
+        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK, CF::ROW_BYTES))
+        return cudaErrorInvalidValue;
+    const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
+    const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
+    if (units > 2147483647LL) return cudaErrorNotSupported;
+    int grid = a.sm_count > 0 ? a.sm_count : 1;
+    if (units < grid) grid = (int)units;
+    const int chunk_kb = a.promote_kb > 0 ? a.promote_kb : 1;
+    tc_promo_kernel<MODE><<<grid, CF::THREADS, CF::SMEM_BYTES, s>>>(
+        ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, splits > 1 ? a.part : nullptr, splits,
+        chunk_kb, a.dstate, (uint64_t)a.wait_limit * 1000ull);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
@@ -261,7 +328,19 @@ bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k) {
     return ((m + BM - 1) / BM) * ((n + 255) / 256) < 1024;
 }
 
+int tc_promo_kblock(int mode) { return mode == 0 ? PromoCfg<0>::BK : PromoCfg<1>::BK; }
+
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
+    if (a.promote_kb > 0) {
+        if (a.epi.kind != 0) return cudaErrorNotSupported;
+        switch (a.mode) {
+            case 0: return launch_promo_mode<0>(a, s);
+            case 1: return launch_promo_mode<1>(a, s);
+            case 2: return launch_promo_mode<2>(a, s);
+            case 3: return launch_promo_mode<3>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const bool rb128 = tc_rb128(a.mode, a.m, a.n, a.k);
     if (a.epi.kind != 0) {
         // fused elementwise operations: BF16 x 2 terms and x 3 terms (6 products)

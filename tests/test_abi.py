@@ -140,3 +140,14 @@ def test_blas3_and_split_k_workspace_sizes():
     assert out.value == packed(64, 8192) + packed(8192, 8192) + 4 * 64 * 8192 * 4
     assert lib.gb_sgemm_workspace_size(x6, b"N", b"N", 64, 8192, 2048, ctypes.byref(out)) == 0
     assert out.value == packed(64, 2048) + packed(8192, 2048)
+
+
+def test_promotion_setting_arguments():
+    """gb_set_promotion / gb_get_promotion validate their arguments without a
+    device: a NULL handle is GB_ERR_HANDLE, a negative chunk GB_ERR_ARG."""
+    lib = _lib.load()
+    v = ctypes.c_int64(5)
+    assert lib.gb_set_promotion(None, 64) == _lib.GB_ERR_HANDLE
+    assert lib.gb_get_promotion(None, ctypes.byref(v)) == _lib.GB_ERR_HANDLE
+    assert v.value == 5
+
