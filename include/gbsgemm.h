@@ -73,12 +73,24 @@ enum {
  *                       every FP32 product a*b is formed exactly (each BF16
  *                       x BF16 product is exact in FP32); only the FP32
  *                       accumulation rounds. 1.5x the tensor work of BF16X6.
+ *  GB_ALGO_SPLIT_FP16X3 each row of op(A) and each column of op(B) is first
+ *                       scaled by a power of two (from its largest finite
+ *                       magnitude, so that the FP16 terms stay in range), then
+ *                       split as x = h + l*2^-11, h and l FP16 (11 significant
+ *                       bits each, round to nearest even); h*h + h*l + l*h on
+ *                       the tensor cores (kind::f16) in one FP32 accumulator,
+ *                       at the rate of BF16X3, with TF32X3's per-product
+ *                       error; the scaling is undone exactly in the epilogue.
+ *                       It always runs the promoted-accumulation kernel (see
+ *                       gb_set_promotion; with promotion off, one chunk spans
+ *                       K). Grouped runs and gb_ssyrk's triangle kernel take
+ *                       SPLIT_TF32X3 for it.
  *  GB_ALGO_AUTO         the library picks: SPLIT_BF16X3 when K >= 1024,
  *                       SPLIT_BF16X6 when 4 <= K < 1024, else SIMT.
  * Error per element, D = |alpha||op(A)||op(B)| + |beta||C|, u = 2^-24:
  *  SIMT       |C - C_exact| <= 2*max(K,1)*u*D
  *  split x    (2*max(K,1)*u + e_x)*D with e_x the dropped cross terms:
- *             TF32X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24 (x 1.01),
+ *             TF32X3 and FP16X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24 (x 1.01),
  *             BF16X9 2^-24 (nothing is dropped, but the tensor core's FP32
  *             accumulation is not round-to-nearest: at K = 1 the error
  *             was measured at 1.34 x 2*K*u*D),
@@ -93,7 +105,8 @@ typedef enum {
     GB_ALGO_SPLIT_TF32X3 = 1,
     GB_ALGO_SPLIT_BF16X3 = 2,
     GB_ALGO_SPLIT_BF16X6 = 3,
-    GB_ALGO_SPLIT_BF16X9 = 4
+    GB_ALGO_SPLIT_BF16X9 = 4,
+    GB_ALGO_SPLIT_FP16X3 = 5
 } gb_algo_t;
 
 typedef struct gb_handle_s *gb_handle_t;

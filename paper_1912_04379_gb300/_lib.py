@@ -21,7 +21,7 @@ c_char = ctypes.c_char
 c_int = ctypes.c_int
 c_size = ctypes.c_size_t
 
-ALGOS = {"auto": -1, "simt": 0, "tf32x3": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4}
+ALGOS = {"auto": -1, "simt": 0, "tf32x3": 1, "bf16x3": 2, "bf16x6": 3, "bf16x9": 4, "fp16x3": 5}
 
 GB_OK = 0
 GB_ERR_CUDA = 1

@@ -445,7 +445,8 @@ int syrk_rec(const GemmRunner &g, bool lower, bool trans, int64_t r0, int64_t nn
 // (SIMT GEMMs and the FP32 diagonal kernel; also every scale-only call).
 int syrk_tc_mode(gb_algo_t algo, int64_t k, bool scale_only) {
     if (scale_only) return -1;
-    return split_mode(resolve_algo(algo, k));
+    const int mode = split_mode(resolve_algo(algo, k));
+    return mode == 4 ? 0 : mode;   // no triangle kernel for the scaled FP16 split: TF32X3
 }
 
 // Bytes of op(A) split and packed once (n rows, K-major), 256-byte rounded.
@@ -592,7 +593,7 @@ GB_API int gb_ssyrk_workspace_size(gb_algo_t algo, char uplo, char trans, int64_
     using namespace gb;
     int rc = check_syrk(uplo, trans, n, k, max1(is_n(trans) ? n : k), max1(n));
     if (rc) return rc;
-    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     // the larger of the two paths' needs (the path also depends on alpha)
     size_t need = 0;
     GemmRunner g{nullptr, algo, nullptr, 0, nullptr, &need};
@@ -611,7 +612,7 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
     using namespace gb;
     int rc = check_syrk(uplo, trans, n, k, lda, ldc);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     rc = check_handle(h);
     if (rc) return rc;
     if (n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
@@ -662,7 +663,7 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
     using namespace gb;
     int rc = check_trsm(side, uplo, transa, diag, m, n, max1(is_l(side) ? m : n), max1(m));
     if (rc) return rc;
-    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     size_t need = 0;
     GemmRunner g{nullptr, algo, nullptr, 0, nullptr, &need};
     TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, nullptr, max1(is_l(side) ? m : n),
@@ -683,7 +684,7 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
     using namespace gb;
     int rc = check_trsm(side, uplo, transa, diag, m, n, lda, ldb);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     rc = check_handle(h);
     if (rc) return rc;
     if (m == 0 || n == 0) return GB_OK;

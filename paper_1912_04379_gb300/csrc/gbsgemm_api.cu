@@ -42,15 +42,33 @@ int check_handle(gb_handle_t h) {
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace of a split algorithm: [A terms][B terms][split-K partials],
+// Bytes of the terms of one packed operand (mn rows of op(A), or mn columns
+// of op(B)): terms x mn x kpad elements, K contiguous.
+size_t terms_bytes(int mode, bool a_side, int64_t mn, int64_t k) {
+    return (size_t)split_parts_side(mode, a_side) * (size_t)split_kpad(mode, k) *
+           (size_t)split_elem_bytes(mode) * (size_t)mn;
+}
+
+// Bytes of one packed operand: its terms, and for the scaled FP16 split the
+// largest magnitude of each row after them (256-byte aligned, mn words).
+size_t packed_bytes(int mode, bool a_side, int64_t mn, int64_t k) {
+    const size_t t = terms_bytes(mode, a_side, mn, k);
+    return mode == 4 ? round_up(t, 256) + (size_t)mn * sizeof(uint32_t) : t;
+}
+
+// The row maxima inside a packed operand of the scaled FP16 split.
+uint32_t *packed_max(void *packed, int mode, bool a_side, int64_t mn, int64_t k) {
+    return reinterpret_cast<uint32_t *>(static_cast<char *>(packed) +
+                                        round_up(terms_bytes(mode, a_side, mn, k), 256));
+}
+
+// Workspace of a split algorithm: [A packed][B packed][split-K partials],
 // each region 1 KiB aligned; the partials exist only when K is split.
 size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
-    const size_t kpad = (size_t)split_kpad(mode, k);
-    const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
     const int s = split_k_factor(mode, m, n, k);
     const size_t partials = s > 1 ? (size_t)s * (size_t)m * (size_t)n * sizeof(float) : 0;
-    return round_up(per * (size_t)m, 1024) + round_up(per * (size_t)n, 1024) +
-           round_up(partials, 1024);
+    return round_up(packed_bytes(mode, true, m, k), 1024) +
+           round_up(packed_bytes(mode, false, n, k), 1024) + round_up(partials, 1024);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
@@ -63,6 +81,7 @@ int gb::split_mode(gb_algo_t algo) {
         case GB_ALGO_SPLIT_BF16X3: return 1;
         case GB_ALGO_SPLIT_BF16X6: return 2;
         case GB_ALGO_SPLIT_BF16X9: return 3;
+        case GB_ALGO_SPLIT_FP16X3: return 4;
         default: return -1;
     }
 }
@@ -96,12 +115,6 @@ int gb::split_k_factor(int mode, int64_t m, int64_t n, int64_t k) {
 
 namespace {
 
-// Bytes of one packed operand (mn rows of op(A), or mn columns of op(B)).
-size_t packed_bytes(int mode, int64_t mn, int64_t k) {
-    return (size_t)split_parts(mode) * (size_t)split_kpad(mode, k) *
-           (size_t)split_elem_bytes(mode) * (size_t)mn;
-}
-
 // Split + pack one operand. a_side: op(A) (element (i,p) = op(A)[i,p]);
 // else op(B)^T (element (j,p) = op(B)[p,j]).
 cudaError_t pack_operand(int mode, bool a_side, bool trans, int64_t mn, int64_t k,
@@ -110,6 +123,9 @@ cudaError_t pack_operand(int mode, bool a_side, bool trans, int64_t mn, int64_t 
     // op(A): stored A is K-contiguous iff transposed; op(B)^T: stored B is
     // K-contiguous iff NOT transposed.
     const bool kcontig = a_side ? trans : !trans;
+    if (mode == 4)
+        return launch_split_pack_fp16(a_side, kcontig, mn, k, X, ldx, out, kpad, mn * kpad,
+                                      packed_max(out, mode, a_side, mn, k), s);
     return launch_split_pack(mode, kcontig, mn, k, X, ldx, out, kpad, mn * kpad, s);
 }
 
@@ -131,6 +147,10 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     t.wait_limit = h->wait_limit;
     t.sm_count = h->sm_count;
     if (epi) t.epi = *epi;
+    if (mode == 4) {
+        t.amax = packed_max(const_cast<void *>(Ap), mode, true, m, k);
+        t.bmax = packed_max(const_cast<void *>(Bp), mode, false, n, k);
+    }
     if (h->promote_k > 0) {
         const int64_t bk = tc_promo_kblock(mode);
         const int64_t kb = (h->promote_k + bk - 1) / bk;
@@ -145,7 +165,7 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
                float *C, int64_t ldc, void *ws, size_t ws_bytes, cudaStream_t s) {
     int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, ldc);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if ((rc = check_handle(h))) return rc;
     if (m == 0 || n == 0 || ((alpha == 0.f || k == 0) && beta == 1.f)) return GB_OK;
     if (!C) return GB_ERR_ARG;
@@ -161,8 +181,8 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     const size_t need = split_ws_bytes(mode, m, n, k);
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
     char *Ap = static_cast<char *>(ws);
-    char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
-    char *Pp = Bp + round_up(packed_bytes(mode, n, k), 1024);
+    char *Bp = Ap + round_up(packed_bytes(mode, true, m, k), 1024);
+    char *Pp = Bp + round_up(packed_bytes(mode, false, n, k), 1024);
     const int splits = split_k_factor(mode, m, n, k);
     // Split fused into the tensor-core kernel, when the handle allows it and
     // TMA can read A and B as they are; otherwise the separate split/pack
@@ -200,7 +220,7 @@ int gb::sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, in
     *fused = false;
     int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, ldc);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if ((rc = check_handle(h))) return rc;
     const int mode = (alpha == 0.f || k == 0) ? -1 : split_mode(resolve_algo(algo, k));
     const bool can_fuse = op.kind != 0 && m > 0 && n > 0 && A && B && C && (mode == 1 || mode == 2) &&
@@ -211,7 +231,7 @@ int gb::sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, in
     const size_t need = split_ws_bytes(mode, m, n, k);
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return GB_ERR_WORKSPACE;
     char *Ap = static_cast<char *>(ws);
-    char *Bp = Ap + round_up(packed_bytes(mode, m, k), 1024);
+    char *Bp = Ap + round_up(packed_bytes(mode, true, m, k), 1024);
     cudaError_t e = pack_operand(mode, true, is_trans(ta), m, k, A, lda, Ap, s);
     if (e == cudaSuccess) e = pack_operand(mode, false, is_trans(tb), n, k, B, ldb, Bp, s);
     if (e != cudaSuccess) return GB_ERR_CUDA;
@@ -326,7 +346,7 @@ GB_API int gb_sgemm_workspace_size(gb_algo_t algo, char ta, char tb, int64_t m, 
                               max1(is_trans(tb) ? n : k), max1(m));
     if (rc) return rc;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     const int mode = split_mode(resolve_algo(algo, k));
     *bytes = (mode < 0 || m == 0 || n == 0 || k == 0) ? 0 : split_ws_bytes(mode, m, n, k);
     return GB_OK;
@@ -345,10 +365,10 @@ GB_API int gb_sgemm_pack_size(gb_algo_t algo, char which, int64_t mn, int64_t k,
     if (mn < 0) return -3;
     if (k < 0) return -5;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     const int mode = split_mode(resolve_algo(algo, k));
     if (mode < 0) return GB_ERR_UNSUPPORTED;
-    *bytes = packed_bytes(mode, mn, k);
+    *bytes = packed_bytes(mode, which == 'A' || which == 'a', mn, k);
     return GB_OK;
 }
 
@@ -363,14 +383,14 @@ GB_API int gb_sgemm_pack(gb_handle_t h, gb_algo_t algo, char which, char trans, 
     // stored rows: op(A) = A is M x K, A^T stored K x M; op(B) = B is K x N, B^T stored N x K
     const int64_t rows = a_side ? (is_trans(trans) ? k : mn) : (is_trans(trans) ? mn : k);
     if (ldx < max1(rows)) return -8;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     int rc = check_handle(h);
     if (rc) return rc;
     const int mode = split_mode(resolve_algo(algo, k));
     if (mode < 0) return GB_ERR_UNSUPPORTED;
     if (mn == 0 || k == 0) return GB_OK;
     if (!X) return GB_ERR_ARG;
-    if (!packed || bytes < packed_bytes(mode, mn, k) ||
+    if (!packed || bytes < packed_bytes(mode, a_side, mn, k) ||
         (reinterpret_cast<uintptr_t>(packed) & 255))
         return GB_ERR_WORKSPACE;
     return cuda_status(pack_operand(mode, a_side, is_trans(trans), mn, k, X, ldx, packed,
@@ -384,7 +404,7 @@ GB_API int gb_sgemm_compute(gb_handle_t h, gb_algo_t algo, int64_t m, int64_t n,
     if (n < 0) return -4;
     if (k < 0) return -5;
     if (ldc < max1(m)) return -13;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     int rc = check_handle(h);
     if (rc) return rc;
     const int mode = split_mode(resolve_algo(algo, k));
@@ -405,7 +425,7 @@ GB_API int gb_sgemm_backward_workspace_size(gb_algo_t algo, char ta, char tb, in
                               max1(is_trans(tb) ? n : k), max1(m));
     if (rc) return rc;
     if (!bytes) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if (m == 0 || n == 0 || k == 0) { *bytes = 0; return GB_OK; }
     const BwdCall a = grad_a(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
     const BwdCall b = grad_b(ta, tb, m, n, k, nullptr, 1, nullptr, 1, nullptr, 1);
@@ -423,7 +443,7 @@ GB_API int gb_sgemm_backward(gb_handle_t h, gb_algo_t algo, char ta, char tb, in
     int rc = check_sgemm_args(ta, tb, m, n, k, lda, ldb, lddc);
     if (rc) return rc;
     if ((rc = check_handle(h))) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if (dA && ldda < max1(is_trans(ta) ? k : m)) return GB_ERR_ARG;
     if (dB && lddb < max1(is_trans(tb) ? n : k)) return GB_ERR_ARG;
     if (dCin && lddcin < max1(m)) return GB_ERR_ARG;

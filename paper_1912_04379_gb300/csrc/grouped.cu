@@ -677,7 +677,7 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
     if (plan) *plan = nullptr;
     if (bad_index) *bad_index = -1;
     if (!plan || !ws_bytes || count < 0 || (count > 0 && !hp)) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
@@ -713,7 +713,10 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
         for (int c = 0; c < kClasses; ++c)
             choice[c] = algo == GB_ALGO_SIMT ? (c < 3 ? 0 : 1) : 2;
     }
-    const int pref = algo == GB_ALGO_SPLIT_TF32X3 ? 0 : algo == GB_ALGO_SPLIT_BF16X3 ? 1
+    // the scaled FP16 split has no grouped kernel: its problems take TF32X3,
+    // whose per-product error is of the same order (3 * 2^-22)
+    const int pref = (algo == GB_ALGO_SPLIT_TF32X3 || algo == GB_ALGO_SPLIT_FP16X3) ? 0
+                   : algo == GB_ALGO_SPLIT_BF16X3 ? 1
                    : algo == GB_ALGO_SPLIT_BF16X6 ? 2 : algo == GB_ALGO_SPLIT_BF16X9 ? 3
                    : kPrefAuto;
     gb_grouped_plan_s *pl = nullptr;

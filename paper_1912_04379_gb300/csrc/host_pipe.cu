@@ -110,7 +110,7 @@ GB_API int gb_sgemm_host_workspace_size(gb_algo_t algo, char ta, char tb, int64_
     using namespace gb;
     int rc = check_args(ta, tb, m, n, k, max1(is_t(ta) ? k : m), max1(is_t(tb) ? n : k), max1(m));
     if (rc) return rc;
-    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (!bytes || algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if (m == 0 || n == 0) { *bytes = 0; return GB_OK; }
     Layout L;
     rc = layout(algo, ta, tb, m, n, k, 1.f, &L);
@@ -126,7 +126,7 @@ GB_API int gb_sgemm_host(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_
     using namespace gb;
     int rc = check_args(ta, tb, m, n, k, lda, ldb, ldc);
     if (rc) return rc;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;

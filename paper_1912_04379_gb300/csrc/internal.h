@@ -97,6 +97,12 @@ cudaError_t launch_scaled_copy(int64_t m, int64_t n, float beta, const float *X,
 cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k,
                               const float *X, int64_t ld, void *out, int64_t kpad,
                               int64_t part_stride_elems, cudaStream_t s);
+// Mode 4 (the scaled FP16 split, FP16X3): first mx[r] = the largest finite
+// |x| of row r (FP32 bits), then the terms of each row scaled by its power of
+// two: op(A) rows (a_side) as 3 terms (2^11 h, h, l), op(B)^T rows as 2 (h, l).
+cudaError_t launch_split_pack_fp16(bool a_side, bool kcontig, int64_t rows, int64_t k,
+                                   const float *X, int64_t ld, void *out, int64_t kpad,
+                                   int64_t part_stride_elems, uint32_t *mx, cudaStream_t s);
 
 // -------------------------------------------------- tensor-core kernel ---
 // Elementwise operation fused into the tensor-core epilogue, applied to
@@ -126,6 +132,8 @@ struct TcArgs {
     int sm_count;
     EpiOp epi;                  // kind != 0: BF16 x 2 or x 3 terms, no split-K
     int promote_kb;             // > 0: promoted accumulation, k-blocks per chunk
+    const uint32_t *amax;       // mode 4: largest |op(A)| per row (FP32 bits)
+    const uint32_t *bmax;       // mode 4: largest |op(B)| per column
 };
 // cudaErrorNotSupported: an epilogue operation with another mode or split-K,
 // or with promoted accumulation.
@@ -165,6 +173,7 @@ cudaError_t launch_tc_fused(const FusedArgs &a, cudaStream_t s);
 // Workspace layout helpers shared by the API and the launcher.
 int64_t split_kpad(int mode, int64_t k);
 int split_parts(int mode);
+int split_parts_side(int mode, bool a_side);   // mode 4: 3 terms for op(A), 2 for op(B)
 int split_elem_bytes(int mode);
 
 // ------------------------------------------------ grouped tensor-core path --

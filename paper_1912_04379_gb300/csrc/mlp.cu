@@ -140,7 +140,7 @@ struct Plan {
 int layout(gb_algo_t algo, const gb_mlp_desc_t *d, bool train, Plan *p) {
     if (!d || !d->widths || d->layers < 1 || d->layers > 4096 || d->batch < 1) return GB_ERR_ARG;
     if (d->hidden != GB_ACT_IDENTITY && d->hidden != GB_ACT_TANH) return GB_ERR_ARG;
-    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_BF16X9) return GB_ERR_ARG;
+    if (algo < GB_ALGO_AUTO || algo > GB_ALGO_SPLIT_FP16X3) return GB_ERR_ARG;
     const int64_t B = d->batch;
     int64_t max_n = 1;
     size_t ws = 0;

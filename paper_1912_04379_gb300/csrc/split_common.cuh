@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace gb {
@@ -68,6 +69,32 @@ __device__ __forceinline__ void split2_bf16(float a0, float a1, uint32_t w[PARTS
         const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - __low2float(m), r1 - __high2float(m));
         w[PARTS - 1] = *reinterpret_cast<const uint32_t *>(&l);
     }
+}
+
+// ---------------------------------------------- scaled FP16 split (FP16X3) --
+// Each row of op(A) and each column of op(B) is scaled by a power of two
+// 2^e chosen from its largest finite magnitude m (kept as FP32 bits, 0 when
+// the row has no nonzero finite entry): A rows to [2^3, 2^4), B columns to
+// [2^14, 2^15), so that every FP16 term below is finite. e = top - floor(log2 m),
+// with floor(log2 m) read off the FP32 encoding (subnormal m included).
+constexpr int kFp16TopA = 3, kFp16TopB = 14;
+// The A side's leading term carries the factor 2^11 of the B side's low term.
+constexpr int kFp16LoShift = 11;
+
+__device__ __forceinline__ int fp16_row_exp(uint32_t maxbits, int top) {
+    if (maxbits == 0) return 0;
+    const uint32_t ef = (maxbits >> 23) & 0xffu;
+    const int lg = ef ? (int)ef - 127 : (31 - __clz((int)(maxbits & 0x7fffffu))) - 149;
+    return top - lg;
+}
+
+// x (already scaled) = h + l * 2^-11 with h = rn_fp16(x) and l = rn_fp16((x - h) * 2^11);
+// x - h is exact (h is within a factor of two of x, or both are below the
+// FP16 normal range where h is a multiple of 2^-24 and x's own grid is finer).
+// A non-finite x gives (x, 0).
+__device__ __forceinline__ void split_fp16(float x, __half &h, __half &l) {
+    h = __float2half_rn(x);
+    l = isfinite(x) ? __float2half_rn((x - __half2float(h)) * 2048.f) : __float2half_rn(0.f);
 }
 
 }  // namespace gb

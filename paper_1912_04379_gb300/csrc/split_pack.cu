@@ -27,11 +27,36 @@ namespace gb {
 namespace {
 
 // Splits four consecutive k of one row and stores each term as one vector:
-// 4 TF32 words (16 bytes) or 4 BF16 values (8 bytes). idx is a multiple of 4
-// and rows start on 16-byte boundaries, so the stores are aligned.
+// 4 TF32 words (16 bytes) or 4 BF16 / FP16 values (8 bytes). idx is a
+// multiple of 4 and rows start on 16-byte boundaries, so the stores are
+// aligned. Modes 4 and 5 are the scaled FP16 split of op(A) and of op(B)^T:
+// each value is first scaled by 2^e, the row's exponent, then split as
+// x = h + l 2^-11; op(A) stores (2^11 h, h, l), op(B)^T stores (h, l).
 template <int MODE>
-__device__ __forceinline__ void split_store4(const float v[4], void *out, int64_t ps, int64_t idx) {
-    if (MODE == 0) {
+__device__ __forceinline__ void split_store4(const float v[4], void *out, int64_t ps, int64_t idx,
+                                             int e) {
+    if (MODE == 4 || MODE == 5) {
+        __half h[4], l[4], h11[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            split_fp16(ldexpf(v[i], e), h[i], l[i]);
+            h11[i] = __float2half_rn(__half2float(h[i]) * 2048.f);   // exact: |h| <= 2^4
+        }
+        __half *o = static_cast<__half *>(out) + idx;
+        auto put = [&](__half *dst, const __half t[4]) {
+            __half2 a = __halves2half2(t[0], t[1]), b = __halves2half2(t[2], t[3]);
+            *reinterpret_cast<uint2 *>(dst) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
+        };
+        if (MODE == 4) {
+            put(o, h11);
+            put(o + ps, h);
+            put(o + 2 * ps, l);
+        } else {
+            put(o, h);
+            put(o + ps, l);
+        }
+    } else if (MODE == 0) {
         float h[4], l[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -56,13 +81,23 @@ __device__ __forceinline__ void split_store4(const float v[4], void *out, int64_
 // Each thread splits 4 consecutive k of one row: 16-byte loads when the
 // source is 16-byte aligned, vector stores of every term. blockIdx.y walks
 // rows, blockIdx.x the k-quads of a row.
+// The row's scaling exponent of the FP16 split (0 for the other modes).
+template <int MODE>
+__device__ __forceinline__ int row_exp(const uint32_t *mx, int64_t r) {
+    if (MODE == 4) return fp16_row_exp(mx[r], kFp16TopA);
+    if (MODE == 5) return fp16_row_exp(mx[r], kFp16TopB);
+    return 0;
+}
+
 template <int MODE, bool VEC>
 __global__ void __launch_bounds__(256)
 split_pack_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                     void *__restrict__ out, int64_t kpad, int64_t ps) {
+                     void *__restrict__ out, int64_t kpad, int64_t ps,
+                     const uint32_t *__restrict__ mx) {
     const int64_t p = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
     if (p >= kpad) return;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int e = row_exp<MODE>(mx, r);
         const float *src = X + r * ld + p;
         float v[4];
         if (VEC && p + 3 < K) {
@@ -72,7 +107,7 @@ split_pack_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = p + i < K ? __ldg(src + i) : 0.f;
         }
-        split_store4<MODE>(v, out, ps, r * kpad + p);
+        split_store4<MODE>(v, out, ps, r * kpad + p, e);
     }
 }
 
@@ -85,7 +120,8 @@ template <int MODE>
 __device__ __forceinline__ void pack_tile64(const float *__restrict__ X, int64_t ld, bool kc,
                                             bool vec, int64_t rows, int64_t K,
                                             void *__restrict__ out, int64_t kpad, int64_t ps,
-                                            int64_t r0, int64_t p0, float (*T)[65]) {
+                                            int64_t r0, int64_t p0, float (*T)[65],
+                                            const uint32_t *__restrict__ mx = nullptr) {
     const int t = threadIdx.x;
     const int l4 = (t & 15) * 4, l16 = t >> 4;
 #pragma unroll
@@ -128,7 +164,7 @@ __device__ __forceinline__ void pack_tile64(const float *__restrict__ X, int64_t
             float v[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = T[l4 + i][rl];
-            split_store4<MODE>(v, out, ps, rr * kpad + pp);
+            split_store4<MODE>(v, out, ps, rr * kpad + pp, row_exp<MODE>(mx, rr));
         }
     }
     __syncthreads();                                     // T is reused by the next tile
@@ -139,10 +175,51 @@ __device__ __forceinline__ void pack_tile64(const float *__restrict__ X, int64_t
 template <int MODE, bool VEC>
 __global__ void __launch_bounds__(256)
 split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                     void *__restrict__ out, int64_t kpad, int64_t ps) {
+                     void *__restrict__ out, int64_t kpad, int64_t ps,
+                     const uint32_t *__restrict__ mx) {
     __shared__ float T[64][65];
     pack_tile64<MODE>(X, ld, false, VEC, rows, K, out, kpad, ps, (int64_t)blockIdx.y * 64,
-                      (int64_t)blockIdx.x * 64, T);
+                      (int64_t)blockIdx.x * 64, T, mx);
+}
+
+// Largest finite |x| of each row of a rows x K operand, as FP32 bits
+// (non-negative floats order like their bit patterns), combined by atomicMax
+// into mx (which starts at 0) over slices of K.
+// Rows-contiguous source (element (r,p) at X[r + p*ld]): one thread per row,
+// coalesced along the rows.
+__global__ void __launch_bounds__(256)
+rowmax_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
+                 uint32_t *__restrict__ mx, int64_t kslice) {
+    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (r >= rows) return;
+    const int64_t p0 = (int64_t)blockIdx.y * kslice;
+    const int64_t p1 = p0 + kslice < K ? p0 + kslice : K;
+    uint32_t m = 0;
+#pragma unroll 8
+    for (int64_t p = p0; p < p1; ++p) {
+        const uint32_t u = __float_as_uint(__ldg(X + r + p * ld)) & 0x7fffffffu;
+        if (u < 0x7f800000u && u > m) m = u;
+    }
+    if (m) atomicMax(mx + r, m);
+}
+
+// K-contiguous source (element (r,p) at X[p + r*ld]): one warp per row.
+__global__ void __launch_bounds__(256)
+rowmax_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
+                 uint32_t *__restrict__ mx, int64_t kslice) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const int64_t p0 = (int64_t)blockIdx.y * kslice;
+    const int64_t p1 = p0 + kslice < K ? p0 + kslice : K;
+    uint32_t m = 0;
+#pragma unroll 4
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        const uint32_t u = __float_as_uint(__ldg(X + p + r * ld)) & 0x7fffffffu;
+        if (u < 0x7f800000u && u > m) m = u;
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0 && m) atomicMax(mx + r, m);
 }
 
 // A K-contiguous 64 x 64 tile straight from registers: each thread loads four
@@ -165,7 +242,7 @@ __device__ __forceinline__ void pack_tile64_kc_direct(const PackItem &it) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = pp + i < it.k ? __ldg(src + i) : 0.f;
         }
-        split_store4<MODE>(v, it.out, it.ps, rr * it.kpad + pp);
+        split_store4<MODE>(v, it.out, it.ps, rr * it.kpad + pp, 0);
     }
 }
 
@@ -197,22 +274,42 @@ split_pack_grouped_kernel(const PackItem *__restrict__ items, int64_t nitems) {
 
 template <int MODE>
 cudaError_t launch_mode(bool kc, int64_t rows, int64_t k, const float *X, int64_t ld, void *out,
-                        int64_t kpad, int64_t ps, cudaStream_t s) {
+                        int64_t kpad, int64_t ps, const uint32_t *mx, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && ld % 4 == 0;
     if (kc) {
         const int64_t gx = (kpad / 4 + 255) / 256;
         const int64_t gy = rows < 65535 ? rows : 65535;
         if (gx > 2147483647LL) return cudaErrorInvalidConfiguration;
         dim3 grid((unsigned)gx, (unsigned)gy);
-        if (vec) split_pack_kc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
-        else     split_pack_kc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+        if (vec) split_pack_kc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps, mx);
+        else     split_pack_kc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps, mx);
     } else {
         const int64_t gx = (kpad + 63) / 64, gy = (rows + 63) / 64;
         if (gx > 2147483647LL || gy > 65535LL) return cudaErrorInvalidConfiguration;
         dim3 grid((unsigned)gx, (unsigned)gy);
-        if (vec) split_pack_rc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
-        else     split_pack_rc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps);
+        if (vec) split_pack_rc_kernel<MODE, true><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps, mx);
+        else     split_pack_rc_kernel<MODE, false><<<grid, 256, 0, s>>>(rows, k, X, ld, out, kpad, ps, mx);
     }
+    return cudaGetLastError();
+}
+
+// mx[r] = largest finite |x| of row r (FP32 bits; 0 if none). About two
+// waves of 256-thread CTAs over (row blocks) x (K slices).
+cudaError_t launch_row_max(bool kc, int64_t rows, int64_t k, const float *X, int64_t ld,
+                           uint32_t *mx, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)rows * sizeof(uint32_t), s);
+    if (e != cudaSuccess || k <= 0) return e;
+    const int64_t per_block = kc ? 8 : 256;                  // rows per CTA
+    const int64_t gx = (rows + per_block - 1) / per_block;
+    if (gx > 2147483647LL) return cudaErrorInvalidConfiguration;
+    int64_t gy = (2432 + gx - 1) / gx;
+    if (gy > 65535) gy = 65535;
+    int64_t kslice = (k + gy - 1) / gy;
+    if (kslice < 64) kslice = 64;
+    gy = (k + kslice - 1) / kslice;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    if (kc) rowmax_kc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice);
+    else    rowmax_rc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice);
     return cudaGetLastError();
 }
 
@@ -226,6 +323,7 @@ cudaError_t launch_split_pack_grouped(const PackItem *items, int64_t nitems, cud
 }
 
 int split_parts(int mode) { return mode >= 2 ? 3 : 2; }
+int split_parts_side(int mode, bool a_side) { return mode == 4 ? (a_side ? 3 : 2) : split_parts(mode); }
 int split_elem_bytes(int mode) { return mode == 0 ? 4 : 2; }
 int64_t split_kpad(int mode, int64_t k) {
     // rows start on 16-byte boundaries: 4 TF32 words or 8 BF16 values
@@ -238,12 +336,22 @@ cudaError_t launch_split_pack(int mode, bool kcontig, int64_t rows, int64_t k, c
                               int64_t ld, void *out, int64_t kpad, int64_t ps, cudaStream_t s) {
     if (rows <= 0 || kpad <= 0) return cudaSuccess;
     switch (mode) {
-        case 0: return launch_mode<0>(kcontig, rows, k, X, ld, out, kpad, ps, s);
-        case 1: return launch_mode<1>(kcontig, rows, k, X, ld, out, kpad, ps, s);
+        case 0: return launch_mode<0>(kcontig, rows, k, X, ld, out, kpad, ps, nullptr, s);
+        case 1: return launch_mode<1>(kcontig, rows, k, X, ld, out, kpad, ps, nullptr, s);
         case 2:
-        case 3: return launch_mode<2>(kcontig, rows, k, X, ld, out, kpad, ps, s);   // same terms
+        case 3: return launch_mode<2>(kcontig, rows, k, X, ld, out, kpad, ps, nullptr, s);   // same terms
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_split_pack_fp16(bool a_side, bool kcontig, int64_t rows, int64_t k,
+                                   const float *X, int64_t ld, void *out, int64_t kpad,
+                                   int64_t ps, uint32_t *mx, cudaStream_t s) {
+    if (rows <= 0 || kpad <= 0) return cudaSuccess;
+    cudaError_t e = launch_row_max(kcontig, rows, k, X, ld, mx, s);
+    if (e != cudaSuccess) return e;
+    return a_side ? launch_mode<4>(kcontig, rows, k, X, ld, out, kpad, ps, mx, s)
+                  : launch_mode<5>(kcontig, rows, k, X, ld, out, kpad, ps, mx, s);
 }
 
 }  // namespace gb

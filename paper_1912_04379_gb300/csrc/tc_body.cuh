@@ -5,6 +5,7 @@
 // tensor maps, output); kTri selects the triangle-masked epilogue.
 #pragma once
 
+#include "split_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace gb {
@@ -23,7 +24,11 @@ template <int MODE, int RB, int BNX = 0, int BUDGET_KB = 216, bool PROMO_ = fals
 struct Cfg {
     static constexpr int ROW_BYTES = RB;                 // one swizzle row of K
     static constexpr bool TF32 = MODE == 0;
-    static constexpr int PARTS = MODE >= 2 ? 3 : 2;
+    static constexpr int FMT = MODE == 0 ? kFmtTF32 : MODE == 4 ? kFmtF16 : kFmtBF16;
+    // terms per operand: TF32 and BF16 x 2: 2; BF16 x 3: 3; scaled FP16: 3 for
+    // op(A) (2^11 h, h, l) and 2 for op(B) (h, l)
+    static constexpr int A_PARTS = MODE >= 2 ? 3 : 2;
+    static constexpr int B_PARTS = (MODE == 2 || MODE == 3) ? 3 : 2;
     static constexpr int NPAIRS = MODE == 3 ? 9 : MODE == 2 ? 6 : 3;
     // 256 output columns per tile, except 3-term operands with 128-byte rows
     // (a 256-column stage would be 144 KiB: one stage only), which use 128.
@@ -35,7 +40,7 @@ struct Cfg {
     static constexpr int KSTEPS = ROW_BYTES / KSTEP_BYTES;
     static constexpr int A_TILE = BM * ROW_BYTES;        // bytes of one term's A tile
     static constexpr int B_TILE = BN * ROW_BYTES;
-    static constexpr int STAGE_BYTES = PARTS * (A_TILE + B_TILE);
+    static constexpr int STAGE_BYTES = A_PARTS * A_TILE + B_PARTS * B_TILE;
     static constexpr int STAGES = (BUDGET_KB * 1024) / STAGE_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;             // two accumulators
     static constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256;
@@ -92,9 +97,10 @@ template <int MODE>
 using GroupedCfg = Cfg<MODE, 64, 128, 96>;
 
 // Promoted accumulation for one GEMM: 128 x 256 tiles of 64-byte rows (the
-// long-K configuration of the plain kernel), 320 threads.
+// long-K configuration of the plain kernel), 384 threads. The scaled FP16
+// split (56 KiB per stage) takes 224 KiB: four stages.
 template <int MODE>
-using PromoCfg = Cfg<MODE, 64, 256, 216, true>;
+using PromoCfg = Cfg<MODE, 64, 256, MODE == 4 ? 224 : 216, true>;
 
 // Waits for this thread's outstanding TMEM loads, with the 32 registers of
 // two 16-column loads as in/out operands (see tmem_wait16).
@@ -163,7 +169,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
     uint8_t *gbase = smem_raw + (base - raw);
     // [stages][term][A tile] then [stages][term][B tile]
     const uint32_t a_smem = base;
-    const uint32_t b_smem = base + CF::STAGES * CF::PARTS * CF::A_TILE;
+    const uint32_t b_smem = base + CF::STAGES * CF::A_PARTS * CF::A_TILE;
     const uint32_t bar_base = base + CF::STAGES * CF::STAGE_BYTES;
     uint8_t *gbar = gbase + CF::STAGES * CF::STAGE_BYTES;
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
@@ -215,12 +221,12 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
                         break;
                     }
                     mbar_arrive_expect_tx(full_bar(stage), CF::STAGE_BYTES);
-                    for (int t = 0; t < CF::PARTS; ++t) {
-                        tma_load_3d(a_smem + (stage * CF::PARTS + t) * CF::A_TILE, ui.ma,
+                    for (int t = 0; t < CF::A_PARTS; ++t)
+                        tma_load_3d(a_smem + (stage * CF::A_PARTS + t) * CF::A_TILE, ui.ma,
                                     full_bar(stage), kb * CF::BK, y_a, t);
-                        tma_load_3d(b_smem + (stage * CF::PARTS + t) * CF::B_TILE, ui.mb,
+                    for (int t = 0; t < CF::B_PARTS; ++t)
+                        tma_load_3d(b_smem + (stage * CF::B_PARTS + t) * CF::B_TILE, ui.mb,
                                     full_bar(stage), kb * CF::BK, y_b, t);
-                    }
                     issued_mask |= 1u << stage;
                     last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == CF::STAGES) { stage = 0; phase ^= 1u; }
@@ -241,7 +247,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
     auto mma_role = [&]() {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc = instr_desc<CF::TF32, CF::BN>();
+            constexpr uint32_t idesc = instr_desc<CF::FMT, CF::BN>();
             const uint64_t desc_a0 = smem_desc<RB>(a_smem), desc_b0 = smem_desc<RB>(b_smem);
             int stage = 0;
             uint32_t phase = 0;
@@ -257,8 +263,8 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
                 // >> 4, so offsetting a descriptor by whole 16-byte units
                 // is an add: one base descriptor per stage and operand,
                 // constant offsets for the term and the k-step.
-                const uint64_t da = desc_a0 + (uint64_t)((stage * CF::PARTS * CF::A_TILE) >> 4);
-                const uint64_t db = desc_b0 + (uint64_t)((stage * CF::PARTS * CF::B_TILE) >> 4);
+                const uint64_t da = desc_a0 + (uint64_t)((stage * CF::A_PARTS * CF::A_TILE) >> 4);
+                const uint64_t db = desc_b0 + (uint64_t)((stage * CF::B_PARTS * CF::B_TILE) >> 4);
 #pragma unroll
                 for (int q = 0; q < CF::NPAIRS; ++q) {
                     int sa, sb;
@@ -385,6 +391,20 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             if (!ok) break;
             UnitInfo ui;            // looked up again: not kept live across the chunks
             src.unit(u, ui);
+            if constexpr (MODE == 4) {
+                // Undo the scaled split: the accumulator holds 2^(11 + e_i + f_j)
+                // times the product of row i and column j (e_i, f_j the row's
+                // and the column's exponents). A power of two: exact unless
+                // the result leaves the FP32 range.
+                const int64_t row = ui.tm * BM + q * 32 + lane;
+                const int ea = row < ui.M ? fp16_row_exp(src.amax[row], kFp16TopA) : 0;
+                const int64_t c0 = ui.tn * CF::BN + hcol;
+#pragma unroll
+                for (int j = 0; j < CF::ECOLS; ++j) {
+                    const int fb = c0 + j < ui.N ? fp16_row_exp(src.bmax[c0 + j], kFp16TopB) : 0;
+                    v[j] = ldexpf(v[j], -(kFp16LoShift + ea + fb));
+                }
+            }
             store_regs<CF::BN, CF::ECOLS>(ui, v, hcol, q, lane);
         }
       }

@@ -222,7 +222,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc = instr_desc<false, CF::BN>();
+            constexpr uint32_t idesc = instr_desc<kFmtBF16, CF::BN>();
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;

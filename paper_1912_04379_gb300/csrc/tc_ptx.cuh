@@ -121,12 +121,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
+// Operand formats of the instruction descriptor (A and B alike).
+enum : int { kFmtF16 = 0, kFmtBF16 = 1, kFmtTF32 = 2 };
+
 // Instruction descriptor (kind::f16 / kind::tf32): D format F32 (bits 4-5 =
-// 1), A and B formats (bits 7-9, 10-12: 1 = BF16, 2 = TF32), both K-major
-// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-template <bool TF32, int N, int M = BM>
+// 1), A and B formats (bits 7-9, 10-12: 0 = F16, 1 = BF16, 2 = TF32), both
+// K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <int FMT, int N, int M = BM>
 __device__ __forceinline__ constexpr uint32_t instr_desc() {
-    constexpr uint32_t fmt = TF32 ? 2u : 1u;
+    constexpr uint32_t fmt = (uint32_t)FMT;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
@@ -198,7 +201,14 @@ __device__ __forceinline__ void tmem_wait16(uint32_t r[16]) {
 // Term pair (A term, B term) for step q, smallest weight first.
 template <int MODE>
 __device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {
-    if (MODE == 3) {
+    if (MODE == 4) {
+        // scaled FP16: A terms (2^11 h, h, l), B terms (h, l); the products
+        // h_a l_b, l_a h_b and 2^11 h_a h_b, so that one accumulator holds
+        // 2^11 (h_a h_b + (h_a l_b + l_a h_b) 2^-11)
+        const int a[3] = {1, 2, 0};
+        const int b[3] = {1, 0, 0};
+        sa = a[q]; sb = b[q];
+    } else if (MODE == 3) {
         // all nine products, by weight: 2^-32, 2^-24 (x2), 2^-16 (x3), 2^-8 (x2), 1
         const int a[9] = {2, 1, 2, 0, 1, 2, 0, 1, 0};
         const int b[9] = {2, 2, 1, 2, 1, 0, 1, 0, 0};
@@ -301,6 +311,7 @@ struct SingleSource {
     int tiles_m, tiles_n;
     int nkb;
     int chunk_kb;                 // promoted accumulation: k-blocks per chunk
+    const uint32_t *amax, *bmax;  // scaled FP16 split: row / column maxima (FP32 bits)
     __device__ __forceinline__ int64_t num_units() const {
         return (int64_t)tiles_m * tiles_n * splits;
     }

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(PromoCfg<MODE>::THREADS, 1)
 tc_promo_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 int64_t M, int64_t N, int64_t K, float alpha, float beta, float *__restrict__ C,
                 int64_t ldc, float *__restrict__ part, int splits, int chunk_kb,
-                DeviceState *dstate, uint64_t limit_ns) {
+                const uint32_t *amax, const uint32_t *bmax, DeviceState *dstate,
+                uint64_t limit_ns) {
     using CF = PromoCfg<MODE>;
     if (threadIdx.x == 0) {
         prefetch_tmap(&mapA);
@@ -95,6 +96,7 @@ tc_promo_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     src.tiles_n = (int)((N + CF::BN - 1) / CF::BN);
     src.nkb = (int)((K + CF::BK - 1) / CF::BK);
     src.chunk_kb = chunk_kb;
+    src.amax = amax; src.bmax = bmax;
     tc_body<MODE, CF::ROW_BYTES, SingleSource<CF::BN, CF::BK, 0>, CF>(src, dstate, limit_ns);
 }
 
@@ -139,16 +141,20 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 3-D map over [terms][rows][kpad] (K innermost), box = BK x box_rows x 1.
-bool make_map(CUtensorMap *map, bool tf32, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
+bool make_map(CUtensorMap *map, int fmt, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
               int parts, int box_rows, int bk, int row_bytes) {
     auto enc = get_encode();
     if (!enc) return false;
+    const bool tf32 = fmt == kFmtTF32;
     const int eb = tf32 ? 4 : 2;
     cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)parts};
     cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(rows * kpad * eb)};
     cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+    const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(map, dt,
                      3, const_cast<void *>(ptr), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE,
                      row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -174,8 +180,8 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
         return cudaErrorNotSupported;
     alignas(64) CUtensorMap ma, mb;
-    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK, RB) ||
-        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK, RB))
+    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, RB) ||
+        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, RB))
         return cudaErrorInvalidValue;
     const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
     const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
@@ -216,18 +222,22 @@ cudaError_t launch_promo_mode(const TcArgs &a, cudaStream_t s) {
     if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
         return cudaErrorNotSupported;
     alignas(64) CUtensorMap ma, mb;
-    if (!make_map(&ma, CF::TF32, a.Ap, a.k, a.m, a.kpad, CF::PARTS, BM, CF::BK, CF::ROW_BYTES) ||
-        !make_map(&mb, CF::TF32, a.Bp, a.k, a.n, a.kpad, CF::PARTS, CF::BN, CF::BK, CF::ROW_BYTES))
+    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, CF::ROW_BYTES) ||
+        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, CF::ROW_BYTES))
         return cudaErrorInvalidValue;
     const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
     const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
     if (units > 2147483647LL) return cudaErrorNotSupported;
     int grid = a.sm_count > 0 ? a.sm_count : 1;
     if (units < grid) grid = (int)units;
-    const int chunk_kb = a.promote_kb > 0 ? a.promote_kb : 1;
+    // no promotion asked for (the scaled FP16 split runs only here): one
+    // chunk spans the whole K range of a unit
+    const int64_t nkb = (a.k + CF::BK - 1) / CF::BK;
+    const int chunk_kb = a.promote_kb > 0 ? a.promote_kb : (int)(nkb < 1 ? 1 : nkb);
+    if (MODE == 4 && (!a.amax || !a.bmax)) return cudaErrorInvalidValue;
     tc_promo_kernel<MODE><<<grid, CF::THREADS, CF::SMEM_BYTES, s>>>(
         ma, mb, a.m, a.n, a.k, a.alpha, a.beta, a.C, a.ldc, splits > 1 ? a.part : nullptr, splits,
-        chunk_kb, a.dstate, (uint64_t)a.wait_limit * 1000ull);
+        chunk_kb, a.amax, a.bmax, a.dstate, (uint64_t)a.wait_limit * 1000ull);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
@@ -268,14 +278,15 @@ cudaError_t launch_splitk_reduce(int64_t m, int64_t n, int S, const float *part,
     return cudaGetLastError();
 }
 
-int tc_tile_n(int mode, bool rb128) { return (mode >= 2 && rb128) ? 128 : 256; }
+int tc_tile_n(int mode, bool rb128) { return (mode >= 2 && mode <= 3 && rb128) ? 128 : 256; }
 
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
                          int64_t rows, bool a_side) {
     const int rb = rb128 ? 128 : 64;
     const bool tf32 = mode == 0;
     const int bk = rb / (tf32 ? 4 : 2);
-    return make_map(map, tf32, packed, k, rows, split_kpad(mode, k), split_parts(mode),
+    return make_map(map, tf32 ? kFmtTF32 : kFmtBF16, packed, k, rows, split_kpad(mode, k),
+                    split_parts(mode),
                     a_side ? BM : tc_tile_n(mode, rb128), bk, rb);
 }
 
@@ -287,7 +298,8 @@ bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, const void *packed,
     static_assert(GroupedCfg<0>::ROW_BYTES == rb && GroupedCfg<2>::ROW_BYTES == rb &&
                   GroupedCfg<0>::BN == GroupedCfg<2>::BN, "one grouped layout for every split");
     const bool tf32 = mode == 0;
-    return make_map(map, tf32, packed, k, rows, split_kpad(mode, k), split_parts(mode),
+    return make_map(map, tf32 ? kFmtTF32 : kFmtBF16, packed, k, rows, split_kpad(mode, k),
+                    split_parts(mode),
                     a_side ? BM : tc_grouped_tile_n(), rb / (tf32 ? 4 : 2), rb);
 }
 
@@ -317,6 +329,7 @@ cudaError_t launch_tc_grouped(int mode, const TcProblem *probs, const TcItem *it
 // 0.081 ms, BF16 x 3 terms 0.075 against 0.078. The environment variable
 // GB_SGEMM_TC_ROW_BYTES = 64 or 128 forces one of them.
 bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k) {
+    if (mode == 4) return false;       // the scaled FP16 split runs 64-byte rows only
     static const int forced = [] {
         const char *e = getenv("GB_SGEMM_TC_ROW_BYTES");
         const int v = e ? atoi(e) : 0;
@@ -331,13 +344,14 @@ bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k) {
 int tc_promo_kblock(int mode) { return mode == 0 ? PromoCfg<0>::BK : PromoCfg<1>::BK; }
 
 cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
-    if (a.promote_kb > 0) {
+    if (a.promote_kb > 0 || a.mode == 4) {
         if (a.epi.kind != 0) return cudaErrorNotSupported;
         switch (a.mode) {
             case 0: return launch_promo_mode<0>(a, s);
             case 1: return launch_promo_mode<1>(a, s);
             case 2: return launch_promo_mode<2>(a, s);
             case 3: return launch_promo_mode<3>(a, s);
+            case 4: return launch_promo_mode<4>(a, s);
             default: return cudaErrorInvalidValue;
         }
     }

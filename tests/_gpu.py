@@ -5,7 +5,7 @@ import numpy as np
 import oracle
 import workloads as wl
 
-ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9")
+ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3")
 
 # Fixed relative error each algorithm adds to a product a*b by dropping the
 # smallest cross terms of its split (derivation: a = h + l + e with
@@ -16,14 +16,20 @@ ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9")
 #   contribute 2 * 2^-24; with all nine products nothing is dropped, but
 #   the tensor core's FP32 accumulation is not round-to-nearest (measured
 #   above 2*K*u*D at K = 1), which the one extra unit 2^-24 covers.
+#   FP16 x 2 terms on scaled rows (t = 11, as TF32): 3 * 2^-22 for every
+#   element within 2^17 of its row's (op(A)) or 2^28 of its column's (op(B))
+#   largest magnitude; smaller ones carry an absolute error below 2^-39 of
+#   that largest magnitude, far under the bound on these workloads.
 #   Rounded up slightly for the (1 + u_t) factors.
 SPLIT_EXTRA = {"simt": 0.0, "tf32x3": 3.01 * 2.0 ** -22, "bf16x3": 3.03 * 2.0 ** -16,
-               "bf16x6": 2.02 * 2.0 ** -24, "bf16x9": 1.01 * 2.0 ** -24}
+               "bf16x6": 2.02 * 2.0 ** -24, "bf16x9": 1.01 * 2.0 ** -24,
+               "fp16x3": 3.01 * 2.0 ** -22}
 # K from which the split's fixed term uses at most half of 2*K*u, so the
 # algorithm meets the plain FP32 bound 2*K*u*D with room for accumulation.
 # For BF16 x 9 products the threshold is measured: worst ratio to the plain
 # bound 1.34 at K = 1 (beta != 0), 0.73 at K = 2, log-uniform inputs.
-STANDARD_BOUND_MIN_K = {"simt": 0, "tf32x3": 16, "bf16x3": 1024, "bf16x6": 4, "bf16x9": 2}
+STANDARD_BOUND_MIN_K = {"simt": 0, "tf32x3": 16, "bf16x3": 1024, "bf16x6": 4, "bf16x9": 2,
+                        "fp16x3": 16}
 
 
 def torch_gpu():

@@ -14,7 +14,7 @@ from _gpu import SPLIT_EXTRA, STANDARD_BOUND_MIN_K, torch_gpu
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
-ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6")
+ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6", "fp16x3")
 
 
 def _check(got, want, D, kred, algo, what):

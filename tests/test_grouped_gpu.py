@@ -122,7 +122,7 @@ def test_grouped_edge_cases():
 MIXED_K = (1, 3, 4, 9, 15, 16, 40, 300, 1023, 1024, 1500, 2100)
 
 
-@pytest.mark.parametrize("algo", ("auto", "tf32x3", "bf16x3", "bf16x6", "bf16x9"))
+@pytest.mark.parametrize("algo", ("auto", "tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3"))
 def test_grouped_per_problem_split_meets_fp32_bound(algo):
     """The plan picks a split per problem by K: each problem's result meets the
     plain FP32 bound, whichever split was preferred (a problem below the

@@ -42,7 +42,7 @@ def test_host_pipeline_against_oracle(algo, shape, ta, tb):
     check_padding(p, got)
 
 
-@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x9"))
+@pytest.mark.parametrize("algo", ("tf32x3", "bf16x3", "bf16x9", "fp16x3"))
 def test_host_pipeline_splits(algo):
     p = wl.make_problem("T", "N", 260, 1800, 1500, -0.75, 0.0, seed=81, dist="logu", ld_pad=1)
     p.C[:p.m, :] = np.nan                      # beta = 0: C is not read

@@ -33,7 +33,7 @@ def _problem(ta, tb, seed):
     return p
 
 
-@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9"))
+@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3"))
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
 def test_nonfinite_positions(algo, ta, tb):
     torch_gpu()
@@ -55,7 +55,7 @@ def test_nonfinite_positions(algo, ta, tb):
     assert np.all(np.abs(g[fin] - C64[fin]) <= bound)
 
 
-@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9"))
+@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3"))
 def test_near_overflow_stays_finite(algo):
     torch_gpu()
     rng = np.random.default_rng(12)

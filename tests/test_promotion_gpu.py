@@ -19,7 +19,7 @@ from _gpu import assert_bit_exact, assert_within_bound, check_padding, oracle_of
 import oracle
 
 pytestmark = pytest.mark.gpu
-SPLIT = ("tf32x3", "bf16x3", "bf16x6", "bf16x9")
+SPLIT = ("tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3")
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
 
 

@@ -12,7 +12,7 @@ from _gpu import ALGOS, assert_bit_exact, assert_within_bound, check_padding, ru
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
-SPLIT = ("tf32x3", "bf16x3", "bf16x6", "bf16x9")
+SPLIT = ("tf32x3", "bf16x3", "bf16x6", "bf16x9", "fp16x3")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -108,7 +108,7 @@ def test_persistent_many_tiles():
 # ------------------------------------------------ log-uniform magnitudes --
 
 @pytest.mark.parametrize("k", (8, 64, 1000))
-@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x6", "bf16x9"))
+@pytest.mark.parametrize("algo", ("simt", "tf32x3", "bf16x6", "bf16x9", "fp16x3"))
 def test_log_uniform_small(algo, k):
     p = wl.make_problem("N", "N", 200, 150, k, 1.0, 0.0, seed=23, dist="logu")
     rc, got = run(p, algo)
