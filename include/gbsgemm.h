@@ -94,6 +94,17 @@ enum {
  *             BF16X9 2^-24 (nothing is dropped, but the tensor core's FP32
  *             accumulation is not round-to-nearest: at K = 1 the error
  *             was measured at 1.34 x 2*K*u*D),
+ *  FP16X3     (2*max(K,1)*u + 3*2^-22)*D + |alpha|*2^-34*(2^(la_i - 3)*sum_p |b_pj|
+ *             + 2^(lb_j - 14)*sum_p |a_ip|), la_i = floor(log2 max_p |a_ip|) and
+ *             lb_j = floor(log2 max_p |b_pj|) (finite entries; a = op(A),
+ *             b = op(B)): the last term is what entries far below their
+ *             row's or column's largest magnitude lose (from about 2^-17 of
+ *             it for op(A), 2^-28 for op(B), down to nothing below 2^-40).
+ *             It is negligible when no such entries dominate an element's
+ *             sum (M = N = K = 8192 with magnitudes 2^U(-20,20): largest
+ *             error 0.0004 of the plain bound), but with few widely spread
+ *             entries (K = 8, the same magnitudes) it can exceed the plain
+ *             bound many times over. AUTO never picks FP16X3.
  *  so a split meets the plain SIMT bound once K >= 16 (TF32X3), 1024
  *  (BF16X3), 4 (BF16X6) or 2 (BF16X9, measured: at most 0.73 x the bound
  *  at K = 2); AUTO only picks an algorithm above its threshold. The BF16 three-term split is exact for

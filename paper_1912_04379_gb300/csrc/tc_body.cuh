@@ -58,7 +58,7 @@ struct Cfg {
     // registers the promoted kernel must be launched with (per thread) so
     // that the split fits: 128 * REG_LOW + 256 * REG_HIGH <= THREADS * this
     static constexpr int REG_LAUNCH_MIN = (128 * REG_LOW + 256 * REG_HIGH + THREADS - 1) / THREADS;
-    static_assert(!PROMO || (ECOLS % 32 == 0 && ECOLS <= 128), "promoted epilogue columns");
+    static_assert(!PROMO || (ECOLS % 64 == 0 && ECOLS <= 128), "promoted epilogue columns");
     static_assert(!PROMO || THREADS == 384, "promoted kernel: three warpgroups");
     static_assert(STAGES >= 2, "need at least two stages");
     static_assert(SMEM_BYTES <= 232448, "opt-in shared memory per block");
@@ -112,6 +112,16 @@ __device__ __forceinline__ void tmem_wait32(uint32_t a[16], uint32_t b[16]) {
                    "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
                    "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
                    "+r"(b[14]), "+r"(b[15])
+                 :
+                 : "memory");
+}
+
+// Waits for this thread's outstanding TMEM loads, with the 64 registers of
+// four 16-column loads as in/out operands (see tmem_wait16).
+__device__ __forceinline__ void tmem_wait64(uint32_t a[16], uint32_t b[16], uint32_t c[16],
+                                            uint32_t d[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]), "+r"(c[8]), "+r"(c[9]), "+r"(c[10]), "+r"(c[11]), "+r"(c[12]), "+r"(c[13]), "+r"(c[14]), "+r"(c[15]), "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), "+r"(d[8]), "+r"(d[9]), "+r"(d[10]), "+r"(d[11]), "+r"(d[12]), "+r"(d[13]), "+r"(d[14]), "+r"(d[15])
                  :
                  : "memory");
 }
@@ -373,15 +383,25 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) +
                                        (uint32_t)(acc * CF::BN + hcol);
+                // 64 columns in flight per TMEM round trip (two per chunk):
+                // the fold has to keep pace with the MMAs of the next chunk.
 #pragma unroll
-                for (int c = 0; c < CF::ECOLS; c += 16) {
-                    uint32_t ra[16];
+                for (int c = 0; c < CF::ECOLS; c += 64) {
+                    uint32_t ra[16], rb[16], rc[16], rd[16];
                     tmem_ld16(taddr + (uint32_t)c, ra);
-                    tmem_wait16(ra);
+                    tmem_ld16(taddr + (uint32_t)(c + 16), rb);
+                    tmem_ld16(taddr + (uint32_t)(c + 32), rc);
+                    tmem_ld16(taddr + (uint32_t)(c + 48), rd);
+                    tmem_wait64(ra, rb, rc, rd);
                     // the chunks are summed in order, each addition rounded
                     // to nearest (0 + x = x for the first)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[c + j] = __fadd_rn(v[c + j], __uint_as_float(ra[j]));
+                    for (int j = 0; j < 16; ++j) {
+                        v[c + j] = __fadd_rn(v[c + j], __uint_as_float(ra[j]));
+                        v[c + 16 + j] = __fadd_rn(v[c + 16 + j], __uint_as_float(rb[j]));
+                        v[c + 32 + j] = __fadd_rn(v[c + 32 + j], __uint_as_float(rc[j]));
+                        v[c + 48 + j] = __fadd_rn(v[c + 48 + j], __uint_as_float(rd[j]));
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();

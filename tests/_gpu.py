@@ -65,14 +65,68 @@ def check_padding(p, got):
         assert np.all(got[p.m:, :] == wl.CANARY), "kernel wrote into the padding rows of C"
 
 
+def op_arrays(p):
+    """op(A) (M x K) and op(B) (K x N) of a problem as float64 arrays."""
+    A = p.A[:p.m, :p.k] if p.ta == "N" else p.A[:p.k, :p.m].T
+    B = p.B[:p.k, :p.n] if p.tb == "N" else p.B[:p.n, :p.k].T
+    return A.astype(np.float64), B.astype(np.float64)
+
+
+def fp16x3_floor(p, cols=None):
+    """The absolute term of the scaled FP16 split's bound, per element (i, j):
+        |alpha| 2^-34 (2^(lg a_i - 3) sum_p |b_pj| + 2^(lg b_j - 14) sum_p |a_ip|)
+    with lg a_i = floor(log2 max_p |a_ip|) and lg b_j = floor(log2 max_p |b_pj|)
+    over finite entries. Derivation: a row of op(A) is scaled so that its
+    largest magnitude lies in [2^3, 2^4) and an element x of it is kept as
+    h + l 2^-11 with h, l in FP16; each rounding to FP16 errs by at most
+    2^-11 of its value or half the subnormal spacing 2^-25, so
+    |x - h - l 2^-11| <= 2^-22 |x| + 2^-36 in scaled units, i.e. 2^-36 2^-e_i
+    = 2^(lg a_i - 3 - 36) absolutely; likewise 2^(lg b_j - 14 - 36) for op(B)
+    (columns to [2^14, 2^15)). Each such absolute error meets the other
+    operand's magnitudes in the products; 2^-34 covers both roundings of the
+    split and the (1 + 2^-22) factors with room. The relative 2^-22 parts make
+    the 3 * 2^-22 of SPLIT_EXTRA."""
+    A, B = op_arrays(p)
+    if cols is not None:
+        B = B[:, cols]
+
+    def lg(x, axis):
+        m = np.max(np.where(np.isfinite(x), np.abs(x), 0.0), axis=axis)
+        e = np.frexp(m)[1] - 1                    # floor(log2 m) for m > 0
+        return np.where(m > 0, e, 0)
+
+    la, lb = lg(A, 1), lg(B, 0)
+    Sa = np.sum(np.where(np.isfinite(A), np.abs(A), 0.0), axis=1)
+    Sb = np.sum(np.where(np.isfinite(B), np.abs(B), 0.0), axis=0)
+    return abs(float(p.alpha)) * 2.0 ** -34 * (np.ldexp(1.0, la - 3)[:, None] * Sb[None, :]
+                                             + np.ldexp(1.0, lb - 14)[None, :] * Sa[:, None])
+
+
 def assert_within_bound(p, got, cols=None, algo="simt"):
-    """The algorithm's own bound (2*max(K,1)*u + extra_algo)*D always, and the
-    plain FP32 bound 2*max(K,1)*u*D when K >= STANDARD_BOUND_MIN_K[algo]."""
+    """The algorithm's own bound (2*max(K,1)*u + extra_algo)*D always (for the
+    scaled FP16 split plus its absolute term, fp16x3_floor), and the plain
+    FP32 bound 2*max(K,1)*u*D when K >= STANDARD_BOUND_MIN_K[algo] (for the
+    scaled FP16 split on the elements whose absolute term is at most a
+    quarter of the plain bound)."""
     C64, D = oracle_of(p, cols)
     sub = got[:p.m, :] if cols is None else got[:p.m, cols]
+    std = oracle.err_report(sub, C64, D, p.k)
+    if algo == "fp16x3":
+        F = fp16x3_floor(p, cols)
+        c = sub.astype(np.float64)
+        fin = np.isfinite(c) & np.isfinite(C64)
+        assert np.array_equal(fin, np.isfinite(C64)), "fp16x3: non-finite where the oracle is finite"
+        diff = np.abs(c[fin] - C64[fin])
+        own = oracle.bound(D[fin], p.k, SPLIT_EXTRA[algo]) + F[fin]
+        assert np.all(diff <= own), \
+            f"fp16x3: {int(np.count_nonzero(diff > own))} elements over its own bound"
+        if p.k >= STANDARD_BOUND_MIN_K[algo]:
+            plain = oracle.bound(D[fin], p.k)
+            small = F[fin] <= 0.25 * plain
+            assert np.all(diff[small] <= plain[small]), "fp16x3: error over the FP32 bound"
+        return std
     rep = oracle.err_report(sub, C64, D, p.k, extra=SPLIT_EXTRA[algo])
     assert rep["max_ratio"] <= 1.0, f"{algo}: error over its own bound: {rep}"
-    std = oracle.err_report(sub, C64, D, p.k)
     if p.k >= STANDARD_BOUND_MIN_K[algo]:
         assert std["max_ratio"] <= 1.0, f"{algo}: error over the FP32 bound: {std}"
     return std
