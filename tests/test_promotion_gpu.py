@@ -139,18 +139,20 @@ def test_promotion_applies_to_pack_and_compute(handles):
 
 
 def test_promoted_bounded_wait_expires_cleanly(handles):
-    """A 1 microsecond wait limit makes the promoted kernel's waits run out:
-    the status is reported, and the context still runs a correct GEMM."""
+    """A 1 microsecond wait limit makes the promoted kernel's waits run out
+    (chunks of 8192: the epilogue waits far longer than that for each): the
+    status is reported, and the context still runs a correct GEMM."""
     import paper_1912_04379_gb300 as gb
     from paper_1912_04379_gb300 import _lib
     h = gb.Handle()
-    h.set_promotion(32)
+    h.set_promotion(8192)
     h.set_wait_limit(1)
-    p = wl.make_problem("N", "N", 1024, 1024, 8192, 1.0, 0.0, seed=13)
+    p = wl.make_problem("N", "N", 2048, 2048, 16384, 1.0, 0.0, seed=13)
     run(p, "bf16x6", handle=h)
     rc, site = h.device_error()
     assert rc == _lib.GB_ERR_TIMEOUT and site > 0
     h.set_wait_limit(2000000)
+    h.set_promotion(32)
     q = wl.make_problem("N", "N", 200, 300, 500, 1.0, 0.0, seed=14)
     rc, got = run(q, "bf16x6", handle=h)
     assert rc == 0
