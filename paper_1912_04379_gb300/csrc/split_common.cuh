@@ -88,6 +88,18 @@ __device__ __forceinline__ int fp16_row_exp(uint32_t maxbits, int top) {
     return top - lg;
 }
 
+// v * 2^-E. For a normal v whose result stays normal this only moves the
+// exponent field (exact); zeros, subnormals, infinities, NaNs and results
+// leaving the normal range go through ldexpf.
+__device__ __forceinline__ float scale_pow2(float v, int E) {
+    const uint32_t u = __float_as_uint(v);
+    const int ex = (int)((u >> 23) & 0xffu);
+    const int ne = ex - E;
+    if (ex != 0 && ex != 255 && ne >= 1 && ne <= 254)
+        return __uint_as_float((u & 0x807fffffu) | ((uint32_t)ne << 23));
+    return ldexpf(v, -E);
+}
+
 // x (already scaled) = h + l * 2^-11 with h = rn_fp16(x) and l = rn_fp16((x - h) * 2^11);
 // x - h is exact (h is within a factor of two of x, or both are below the
 // FP16 normal range where h is a multiple of 2^-24 and x's own grid is finer).

@@ -39,7 +39,7 @@ __device__ __forceinline__ void split_store4(const float v[4], void *out, int64_
         __half h[4], l[4], h11[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            split_fp16(ldexpf(v[i], e), h[i], l[i]);
+            split_fp16(scale_pow2(v[i], -e), h[i], l[i]);
             h11[i] = __float2half_rn(__half2float(h[i]) * 2048.f);   // exact: |h| <= 2^4
         }
         __half *o = static_cast<__half *>(out) + idx;

@@ -422,7 +422,7 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
 #pragma unroll
                 for (int j = 0; j < CF::ECOLS; ++j) {
                     const int fb = c0 + j < ui.N ? fp16_row_exp(src.bmax[c0 + j], kFp16TopB) : 0;
-                    v[j] = ldexpf(v[j], -(kFp16LoShift + ea + fb));
+                    v[j] = scale_pow2(v[j], kFp16LoShift + ea + fb);
                 }
             }
             store_regs<CF::BN, CF::ECOLS>(ui, v, hcol, q, lane);
