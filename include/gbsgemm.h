@@ -73,9 +73,10 @@ enum {
  *                       every FP32 product a*b is formed exactly (each BF16
  *                       x BF16 product is exact in FP32); only the FP32
  *                       accumulation rounds. 1.5x the tensor work of BF16X6.
- *  GB_ALGO_SPLIT_FP16X3 each row of op(A) and each column of op(B) is first
- *                       scaled by a power of two (from its largest finite
- *                       magnitude, so that the FP16 terms stay in range), then
+ *  GB_ALGO_SPLIT_FP16X3 each row of op(A) and each block of 256 columns of
+ *                       op(B) is first scaled by a power of two (from its
+ *                       largest finite magnitude, so that the FP16 terms stay
+ *                       in range), then
  *                       split as x = h + l*2^-11, h and l FP16 (11 significant
  *                       bits each, round to nearest even); h*h + h*l + l*h on
  *                       the tensor cores (kind::f16) in one FP32 accumulator,
@@ -95,11 +96,12 @@ enum {
  *             accumulation is not round-to-nearest: at K = 1 the error
  *             was measured at 1.34 x 2*K*u*D),
  *  FP16X3     (2*max(K,1)*u + 3*2^-22)*D + |alpha|*2^-34*(2^(la_i - 3)*sum_p |b_pj|
- *             + 2^(lb_j - 14)*sum_p |a_ip|), la_i = floor(log2 max_p |a_ip|) and
- *             lb_j = floor(log2 max_p |b_pj|) (finite entries; a = op(A),
- *             b = op(B)): the last term is what entries far below their
- *             row's or column's largest magnitude lose (from about 2^-17 of
- *             it for op(A), 2^-28 for op(B), down to nothing below 2^-40).
+ *             + 2^(lb_J - 14)*sum_p |a_ip|), la_i = floor(log2 max_p |a_ip|) and
+ *             lb_J = floor(log2 of the largest |b_pl| over the block of 256
+ *             columns l holding j) (finite entries; a = op(A), b = op(B)):
+ *             the last term is what entries far below their row's or column
+ *             block's largest magnitude lose (from about 2^-17 of it for
+ *             op(A), 2^-28 for op(B), down to nothing below 2^-40).
  *             It is negligible when no such entries dominate an element's
  *             sum (M = N = K = 8192 with magnitudes 2^U(-20,20): largest
  *             error 0.0004 of the plain bound), but with few widely spread

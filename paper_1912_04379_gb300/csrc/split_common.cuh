@@ -72,12 +72,17 @@ __device__ __forceinline__ void split2_bf16(float a0, float a1, uint32_t w[PARTS
 }
 
 // ---------------------------------------------- scaled FP16 split (FP16X3) --
-// Each row of op(A) and each column of op(B) is scaled by a power of two
-// 2^e chosen from its largest finite magnitude m (kept as FP32 bits, 0 when
-// the row has no nonzero finite entry): A rows to [2^3, 2^4), B columns to
-// [2^14, 2^15), so that every FP16 term below is finite. e = top - floor(log2 m),
-// with floor(log2 m) read off the FP32 encoding (subnormal m included).
+// Each row of op(A), and each block of kFp16ColBlock consecutive columns of
+// op(B), is scaled by a power of two 2^e chosen from its largest finite
+// magnitude m (kept as FP32 bits, 0 when there is no nonzero finite entry):
+// A rows to [2^3, 2^4), B column blocks to [2^14, 2^15), so that every FP16
+// term below is finite. e = top - floor(log2 m), with floor(log2 m) read off
+// the FP32 encoding (subnormal m included). A column block is the tensor-core
+// tile's width, so the epilogue undoes a tile's scaling with one factor per
+// row.
 constexpr int kFp16TopA = 3, kFp16TopB = 14;
+constexpr int kFp16ColBlockLog2 = 8;
+constexpr int kFp16ColBlock = 1 << kFp16ColBlockLog2;
 // The A side's leading term carries the factor 2^11 of the B side's low term.
 constexpr int kFp16LoShift = 11;
 
@@ -88,16 +93,26 @@ __device__ __forceinline__ int fp16_row_exp(uint32_t maxbits, int top) {
     return top - lg;
 }
 
+// Whether v * 2^-E is exact by moving v's exponent field alone: v normal
+// and the result normal.
+__device__ __forceinline__ bool pow2_scale_in_range(float v, int E) {
+    const int ex = (int)((__float_as_uint(v) >> 23) & 0xffu);
+    const int ne = ex - E;
+    return ex != 0 && ex != 255 && ne >= 1 && ne <= 254;
+}
+
+static __device__ __noinline__ float ldexp_out_of_line(float v, int n) { return ldexpf(v, n); }
+
 // v * 2^-E. For a normal v whose result stays normal this only moves the
 // exponent field (exact); zeros, subnormals, infinities, NaNs and results
-// leaving the normal range go through ldexpf.
+// leaving the normal range go through ldexpf (out of line: rare).
 __device__ __forceinline__ float scale_pow2(float v, int E) {
-    const uint32_t u = __float_as_uint(v);
-    const int ex = (int)((u >> 23) & 0xffu);
-    const int ne = ex - E;
-    if (ex != 0 && ex != 255 && ne >= 1 && ne <= 254)
+    if (pow2_scale_in_range(v, E)) {
+        const uint32_t u = __float_as_uint(v);
+        const int ne = (int)((u >> 23) & 0xffu) - E;
         return __uint_as_float((u & 0x807fffffu) | ((uint32_t)ne << 23));
-    return ldexpf(v, -E);
+    }
+    return ldexp_out_of_line(v, -E);
 }
 
 // x (already scaled) = h + l * 2^-11 with h = rn_fp16(x) and l = rn_fp16((x - h) * 2^11);

@@ -85,7 +85,7 @@ __device__ __forceinline__ void split_store4(const float v[4], void *out, int64_
 template <int MODE>
 __device__ __forceinline__ int row_exp(const uint32_t *mx, int64_t r) {
     if (MODE == 4) return fp16_row_exp(mx[r], kFp16TopA);
-    if (MODE == 5) return fp16_row_exp(mx[r], kFp16TopB);
+    if (MODE == 5) return fp16_row_exp(mx[r >> kFp16ColBlockLog2], kFp16TopB);
     return 0;
 }
 
@@ -184,12 +184,13 @@ split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
 
 // Largest finite |x| of each row of a rows x K operand, as FP32 bits
 // (non-negative floats order like their bit patterns), combined by atomicMax
-// into mx (which starts at 0) over slices of K.
+// into mx[r >> shift] (which starts at 0) over slices of K; shift > 0 takes
+// the maximum over blocks of 2^shift rows.
 // Rows-contiguous source (element (r,p) at X[r + p*ld]): one thread per row,
 // coalesced along the rows.
 __global__ void __launch_bounds__(256)
 rowmax_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                 uint32_t *__restrict__ mx, int64_t kslice) {
+                 uint32_t *__restrict__ mx, int64_t kslice, int shift) {
     const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (r >= rows) return;
     const int64_t p0 = (int64_t)blockIdx.y * kslice;
@@ -200,13 +201,13 @@ rowmax_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t l
         const uint32_t u = __float_as_uint(__ldg(X + r + p * ld)) & 0x7fffffffu;
         if (u < 0x7f800000u && u > m) m = u;
     }
-    if (m) atomicMax(mx + r, m);
+    if (m) atomicMax(mx + (r >> shift), m);
 }
 
 // K-contiguous source (element (r,p) at X[p + r*ld]): one warp per row.
 __global__ void __launch_bounds__(256)
 rowmax_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
-                 uint32_t *__restrict__ mx, int64_t kslice) {
+                 uint32_t *__restrict__ mx, int64_t kslice, int shift) {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
@@ -219,7 +220,7 @@ rowmax_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t l
         if (u < 0x7f800000u && u > m) m = u;
     }
     m = __reduce_max_sync(0xffffffffu, m);
-    if (lane == 0 && m) atomicMax(mx + r, m);
+    if (lane == 0 && m) atomicMax(mx + (r >> shift), m);
 }
 
 // A K-contiguous 64 x 64 tile straight from registers: each thread loads four
@@ -293,11 +294,13 @@ cudaError_t launch_mode(bool kc, int64_t rows, int64_t k, const float *X, int64_
     return cudaGetLastError();
 }
 
-// mx[r] = largest finite |x| of row r (FP32 bits; 0 if none). About two
-// waves of 256-thread CTAs over (row blocks) x (K slices).
+// mx[r >> shift] = largest finite |x| of the rows r of a block of 2^shift
+// (FP32 bits; 0 if none). About two waves of 256-thread CTAs over (row
+// blocks) x (K slices).
 cudaError_t launch_row_max(bool kc, int64_t rows, int64_t k, const float *X, int64_t ld,
-                           uint32_t *mx, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)rows * sizeof(uint32_t), s);
+                           uint32_t *mx, int shift, cudaStream_t s) {
+    const int64_t nmx = ((rows - 1) >> shift) + 1;
+    cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)nmx * sizeof(uint32_t), s);
     if (e != cudaSuccess || k <= 0) return e;
     const int64_t per_block = kc ? 8 : 256;                  // rows per CTA
     const int64_t gx = (rows + per_block - 1) / per_block;
@@ -308,8 +311,8 @@ cudaError_t launch_row_max(bool kc, int64_t rows, int64_t k, const float *X, int
     if (kslice < 64) kslice = 64;
     gy = (k + kslice - 1) / kslice;
     dim3 grid((unsigned)gx, (unsigned)gy);
-    if (kc) rowmax_kc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice);
-    else    rowmax_rc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice);
+    if (kc) rowmax_kc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice, shift);
+    else    rowmax_rc_kernel<<<grid, 256, 0, s>>>(rows, k, X, ld, mx, kslice, shift);
     return cudaGetLastError();
 }
 
@@ -348,7 +351,8 @@ cudaError_t launch_split_pack_fp16(bool a_side, bool kcontig, int64_t rows, int6
                                    const float *X, int64_t ld, void *out, int64_t kpad,
                                    int64_t ps, uint32_t *mx, cudaStream_t s) {
     if (rows <= 0 || kpad <= 0) return cudaSuccess;
-    cudaError_t e = launch_row_max(kcontig, rows, k, X, ld, mx, s);
+    // op(A): one maximum per row; op(B)^T: one per block of kFp16ColBlock rows
+    cudaError_t e = launch_row_max(kcontig, rows, k, X, ld, mx, a_side ? 0 : kFp16ColBlockLog2, s);
     if (e != cudaSuccess) return e;
     return a_side ? launch_mode<4>(kcontig, rows, k, X, ld, out, kpad, ps, mx, s)
                   : launch_mode<5>(kcontig, rows, k, X, ld, out, kpad, ps, mx, s);

@@ -128,14 +128,14 @@ __device__ __forceinline__ void tmem_wait64(uint32_t a[16], uint32_t b[16], uint
 
 // Stores one epilogue warp's part of a unit's result from registers: row
 // tm*128 + 32q + lane, the EC columns from tn*BN + hcol, value v[j] for
-// column j. C <- alpha*v + beta*C (C not read when beta == 0), or the raw
-// sum for a split-K partial. Same arithmetic as store_tile.
+// column j. C <- a*v + beta*C (C not read when beta == 0), or a*v for a
+// split-K partial; a is alpha (1 for a partial), times an exact power of two
+// for the scaled FP16 split. Same arithmetic as store_tile.
 template <int BN, int EC>
 __device__ __forceinline__ void store_regs(const UnitInfo &ui, const float (&v)[EC], int hcol,
-                                           int q, int lane) {
+                                           int q, int lane, float a) {
     const int64_t M = ui.M, N = ui.N, ldd = ui.ldd;
     const bool part = ui.raw;
-    const float a = part ? 1.f : ui.alpha;
     const float beta = part ? 0.f : ui.beta;
     const int64_t row = ui.tm * BM + q * 32 + lane;
     const int64_t col0 = ui.tn * BN + hcol;
@@ -411,21 +411,26 @@ __device__ __forceinline__ void tc_body(const Src &src, DeviceState *dstate, uin
             if (!ok) break;
             UnitInfo ui;            // looked up again: not kept live across the chunks
             src.unit(u, ui);
+            float a = ui.raw ? 1.f : ui.alpha;
             if constexpr (MODE == 4) {
-                // Undo the scaled split: the accumulator holds 2^(11 + e_i + f_j)
-                // times the product of row i and column j (e_i, f_j the row's
-                // and the column's exponents). A power of two: exact unless
-                // the result leaves the FP32 range.
+                // Undo the scaled split: the accumulator holds 2^(11 + e_i + f)
+                // times the product (e_i the row's exponent, f the tile's
+                // column block's). When a * 2^-(11 + e_i + f) is exact the
+                // factor joins a (one rounding, as a * (v 2^-E) would give);
+                // otherwise each value is scaled first, exactly unless it
+                // leaves the FP32 range.
+                static_assert(CF::BN == kFp16ColBlock, "one column block per tile");
                 const int64_t row = ui.tm * BM + q * 32 + lane;
                 const int ea = row < ui.M ? fp16_row_exp(src.amax[row], kFp16TopA) : 0;
-                const int64_t c0 = ui.tn * CF::BN + hcol;
+                const int E = kFp16LoShift + ea + fp16_row_exp(src.bmax[ui.tn], kFp16TopB);
+                if (pow2_scale_in_range(a, E)) {
+                    a = scale_pow2(a, E);
+                } else {
 #pragma unroll
-                for (int j = 0; j < CF::ECOLS; ++j) {
-                    const int fb = c0 + j < ui.N ? fp16_row_exp(src.bmax[c0 + j], kFp16TopB) : 0;
-                    v[j] = scale_pow2(v[j], kFp16LoShift + ea + fb);
+                    for (int j = 0; j < CF::ECOLS; ++j) v[j] = scale_pow2(v[j], E);
                 }
             }
-            store_regs<CF::BN, CF::ECOLS>(ui, v, hcol, q, lane);
+            store_regs<CF::BN, CF::ECOLS>(ui, v, hcol, q, lane, a);
         }
       }
     };

@@ -74,30 +74,36 @@ def op_arrays(p):
 
 def fp16x3_floor(p, cols=None):
     """The absolute term of the scaled FP16 split's bound, per element (i, j):
-        |alpha| 2^-34 (2^(lg a_i - 3) sum_p |b_pj| + 2^(lg b_j - 14) sum_p |a_ip|)
-    with lg a_i = floor(log2 max_p |a_ip|) and lg b_j = floor(log2 max_p |b_pj|)
-    over finite entries. Derivation: a row of op(A) is scaled so that its
-    largest magnitude lies in [2^3, 2^4) and an element x of it is kept as
-    h + l 2^-11 with h, l in FP16; each rounding to FP16 errs by at most
-    2^-11 of its value or half the subnormal spacing 2^-25, so
-    |x - h - l 2^-11| <= 2^-22 |x| + 2^-36 in scaled units, i.e. 2^-36 2^-e_i
-    = 2^(lg a_i - 3 - 36) absolutely; likewise 2^(lg b_j - 14 - 36) for op(B)
-    (columns to [2^14, 2^15)). Each such absolute error meets the other
-    operand's magnitudes in the products; 2^-34 covers both roundings of the
-    split and the (1 + 2^-22) factors with room. The relative 2^-22 parts make
-    the 3 * 2^-22 of SPLIT_EXTRA."""
+        |alpha| 2^-34 (2^(lg a_i - 3) sum_p |b_pj| + 2^(lg b_J - 14) sum_p |a_ip|)
+    with lg a_i = floor(log2 max_p |a_ip|) over row i of op(A), and lg b_J the
+    same over the block of 256 columns of op(B) holding column j (finite
+    entries). Derivation: a row of op(A) is scaled so that its largest
+    magnitude lies in [2^3, 2^4) and an element x of it is kept as h + l 2^-11
+    with h, l in FP16; each rounding to FP16 errs by at most 2^-11 of its value
+    or half the subnormal spacing 2^-25, so |x - h - l 2^-11| <= 2^-22 |x| +
+    2^-36 in scaled units, i.e. 2^-36 2^-e_i = 2^(lg a_i - 3 - 36) absolutely;
+    likewise 2^(lg b_J - 14 - 36) for op(B) (column blocks to [2^14, 2^15)).
+    Each such absolute error meets the other operand's magnitudes in the
+    products; 2^-34 covers both roundings of the split and the (1 + 2^-22)
+    factors with room. The relative 2^-22 parts make the 3 * 2^-22 of
+    SPLIT_EXTRA."""
     A, B = op_arrays(p)
+    absA = np.where(np.isfinite(A), np.abs(A), 0.0)
+    absB = np.where(np.isfinite(B), np.abs(B), 0.0)
+
+    def lg(m):
+        return np.where(m > 0, np.frexp(m)[1] - 1, 0)   # floor(log2 m) for m > 0
+
+    la = lg(absA.max(axis=1))
+    colmax = absB.max(axis=0)
+    blk = np.arange(p.n) // 256
+    blockmax = np.zeros(blk[-1] + 1 if p.n else 0)
+    np.maximum.at(blockmax, blk, colmax)
+    lb = lg(blockmax[blk])
+    Sa = absA.sum(axis=1)
+    Sb = absB.sum(axis=0)
     if cols is not None:
-        B = B[:, cols]
-
-    def lg(x, axis):
-        m = np.max(np.where(np.isfinite(x), np.abs(x), 0.0), axis=axis)
-        e = np.frexp(m)[1] - 1                    # floor(log2 m) for m > 0
-        return np.where(m > 0, e, 0)
-
-    la, lb = lg(A, 1), lg(B, 0)
-    Sa = np.sum(np.where(np.isfinite(A), np.abs(A), 0.0), axis=1)
-    Sb = np.sum(np.where(np.isfinite(B), np.abs(B), 0.0), axis=0)
+        lb, Sb = lb[cols], Sb[cols]
     return abs(float(p.alpha)) * 2.0 ** -34 * (np.ldexp(1.0, la - 3)[:, None] * Sb[None, :]
                                              + np.ldexp(1.0, lb - 14)[None, :] * Sa[:, None])
 

@@ -1,10 +1,11 @@
 """GPU checks specific to the scaled FP16 split (GB_ALGO_SPLIT_FP16X3).
 
-Each row of op(A) and each column of op(B) is scaled by a power of two
-chosen from its largest finite magnitude before the FP16 split, and the
-epilogue undoes it. Scaling a row (or column) by 2^s therefore changes
-nothing but the exponent the kernel picks: the result scales by exactly 2^s,
-bit for bit, as long as it stays in the normal FP32 range. The per-element
+Each row of op(A) and each block of 256 columns of op(B) is scaled by a
+power of two chosen from its largest finite magnitude before the FP16
+split, and the epilogue undoes it. Scaling a row (or a column block) by 2^s
+therefore changes nothing but the exponent the kernel picks: the result
+scales by exactly 2^s, bit for bit, as long as it stays in the normal FP32
+range. The per-element
 bound against the FP64 oracle is checked on rows and columns whose
 magnitudes differ by up to 2^120, on empty (all-zero) rows, through the
 pack-once path, and with and without promoted accumulation.
@@ -48,11 +49,11 @@ def _scale_op_cols(X, trans, cols, t):
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 def test_power_of_two_row_and_column_scaling_is_exact(h, ta, tb, promote):
     h.set_promotion(promote)
-    m, n, k = 300, 270, 1500
+    m, n, k = 300, 600, 1500
     base = wl.make_problem(ta, tb, m, n, k, 1.0, 0.0, seed=61, ld_pad=3)
     rng = np.random.default_rng(62)
     s = rng.integers(-40, 41, m)
-    t = rng.integers(-40, 41, n)
+    t = np.repeat(rng.integers(-40, 41, 3), 256)[:n]     # one exponent per 256-column block
     scaled = wl.make_problem(ta, tb, m, n, k, 1.0, 0.0, seed=61, ld_pad=3)
     _scale_op_rows(scaled.A, ta, m, s)
     _scale_op_cols(scaled.B, tb, n, t)
