@@ -53,9 +53,10 @@ ARMS = (("simt", 0), ("bf16x3", 0), ("tf32x3", 0), ("bf16x6", 0), ("bf16x9", 0),
 
 def arm_name(algo, promote):
     return algo if not promote else f"{algo}+promote{promote}"
-# Per-launch DRAM traffic of the tensor-core kernel at 8192^3 bf16x3 from one
-# ncu capture, valid only for the kernel source it was taken on.
-TRAFFIC = {"source_sha": "992e0942fcbda8b9", "bytes": 2525554752}
+# Per-launch DRAM traffic of the headline tensor-core kernel at 8192^3 (fp16x3,
+# 128-element promoted chunks) from one ncu capture, valid only for the kernel
+# source it was taken on.
+TRAFFIC = {"source_sha": "ee24b9cbece09c23", "bytes": 2853016576 + 263062016}
 
 
 def env_int(name, default):
