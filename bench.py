@@ -77,6 +77,8 @@ def parse():
                     help="skip the grouped 2000-problem comparison")
     ap.add_argument("--no-shapes", action="store_true",
                     help="skip the per-shape table (K = 1024, 16384 and the skinny shapes)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 384^3 case, the padded-stride size sweep and the dense layer")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the training-step measurement of the fully connected network")
     ap.add_argument("--no-blas3", action="store_true",
@@ -452,13 +454,41 @@ def bench_grouped(gb, h, dev, stream, reps=10):
     (host-issued, and the same launches captured in one graph)."""
     import torch
     import workloads as wl
+    import numpy as np
+    import oracle
     probs = wl.grouped_problems(2000, seed=4)
     flops = float(sum(2 * p.m * p.n * p.k for p in probs))
     nbytes = float(sum(4 * (p.A.size + p.B.size + 2 * p.C.size) for p in probs))
     buf, tuples, views = gb.upload_problems(probs, device=dev)
+    buf0 = buf.clone()
+    offs = [(v.data_ptr() - buf.data_ptr()) // 4 for v in views]
+    t0 = time.perf_counter()
+    ref = [oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta, p.C,
+                        p.ldc) for p in probs]
+    oracle_s = time.perf_counter() - t0
     out = {"workload": "2000 problems, M,N,K = round(2^U(3,10)), trans N/T p=0.5, "
                        "alpha,beta ~ U[-2,2], entries U[-1,1] (seed 4)",
-           "gflop": flops / 1e9, "min_bytes": nbytes}
+           "gflop": flops / 1e9, "min_bytes": nbytes,
+           "cpu_oracle": {"seconds": oracle_s, "gflops": flops / oracle_s / 1e9,
+                          "sample": "every element of all 2000 problems"}}
+
+    def accuracy(plan):
+        """One run on the original C of every problem: max and median (over
+        the problems' medians) error / plain bound, elements over it."""
+        buf.copy_(buf0)
+        plan.run(stream=stream)
+        torch.cuda.synchronize()
+        host = buf.cpu().numpy()
+        mx, meds, nfail, count = 0.0, [], 0, 0
+        for p, (C64, D), o in zip(probs, ref, offs):
+            got = host[o:o + p.ldc * p.n].reshape(p.n, p.ldc).T[:p.m]
+            r = oracle.err_report(got, C64, D, p.k)
+            mx = max(mx, r["max_ratio"])
+            meds.append(r["median_ratio"])
+            nfail += r["n_fail"]
+            count += r["count"]
+        return {"max_ratio": mx, "median_of_problem_medians": float(np.median(meds)),
+                "n_fail": nfail, "elements": count, "within_plain_bound": nfail == 0}
 
     def timed(fn, n):
         fn()
@@ -482,7 +512,8 @@ def bench_grouped(gb, h, dev, stream, reps=10):
         torch.cuda.synchronize()
         ms = timed(g.replay, reps)
         out[f"grouped_{algo}"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-                                  "gbs": nbytes / (ms * 1e-3) / 1e9, "launches": plan_launches(plan)}
+                                  "gbs": nbytes / (ms * 1e-3) / 1e9, "launches": plan_launches(plan),
+                                  "accuracy": accuracy(plan)}
         plan.close()
 
     def one(t, strm=None):
@@ -612,43 +643,229 @@ def bench_blas3(gb, h, dev, stream, reps=5):
 
 
 def bench_shapes(gb, h, dev, stream, reps=10):
-    """gb_sgemm on the split-precision shapes (M=N=8192 with K = 1024, 16384;
-    skinny 8192x8192x64 and 64x8192x8192) per algorithm: TFLOP/s and, for the
-    memory-bound skinny shapes, HBM GB/s of the minimum traffic
-    4(MK + KN + MN) bytes against the measured HBM peak."""
+    """gb_sgemm on the other split-precision shapes (M=N=8192 with K = 1024,
+    16384; skinny 8192x8192x64 and 64x8192x8192), entries random sign x
+    2^U(-20,20) as the split workload specifies (drawn on the device, seed 2),
+    per algorithm: TFLOP/s, HBM GB/s of the minimum traffic 4(MK + KN + MN)
+    bytes against the measured HBM peak (the skinny shapes are memory bound),
+    and the max / median error over the plain bound on 8 sampled columns
+    (within_plain_bound false marks an arm outside 2*K*u*D there, e.g. BF16X3
+    at K = 64, whose split error needs K >= 1024)."""
+    import numpy as np
     import torch
+    import oracle
+    import workloads as wl
     peaks, _ = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     out = {}
+    arms = (("bf16x3", 0), ("tf32x3", 0), ("bf16x6", 0), ("bf16x9", 0), ("simt", 0),
+            ("fp16x3", 128), ("bf16x6", 64))
     for (m, n, k) in ((8192, 8192, 1024), (8192, 8192, 16384), (8192, 8192, 64), (64, 8192, 8192)):
         g = torch.Generator(device=dev).manual_seed(SEED)
-        A = (torch.rand((k, m), device=dev, generator=g) * 2 - 1).t()
-        B = (torch.rand((n, k), device=dev, generator=g) * 2 - 1).t()
+
+        def logu(rows, cols):
+            sign = torch.where(torch.rand((cols, rows), device=dev, generator=g) < 0.5, -1.0, 1.0)
+            mag = torch.exp2(torch.rand((cols, rows), device=dev, generator=g) * 40.0 - 20.0)
+            return (sign * mag).t()                    # column-major rows x cols
+        A = logu(m, k)
+        B = logu(k, n)
         C = gb.colmajor(m, n, device=dev)
+        cols = np.unique(np.linspace(0, n - 1, 8).round().astype(np.int64))
+        Ah = np.asfortranarray(A.cpu().numpy())
+        Bh = np.asfortranarray(B.cpu().numpy())
+        C64, D = oracle.sgemm("N", "N", m, n, k, 1.0, Ah, m, Bh, k, 0.0, None, m, cols=cols)
+        idx = torch.from_numpy(cols).to(dev)
         rows = {}
-        for algo in ("bf16x3", "tf32x3", "bf16x6", "bf16x9", "simt"):
+        for algo, promote in arms:
+            h.set_promotion(promote)
             ws_n = gb.workspace_size(algo, "N", "N", m, n, k)
             ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
 
             def f():
                 gb.sgemm_raw("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0,
                              C.data_ptr(), m, algo=algo, handle=h, workspace=ws)
-            f()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                f()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
+            ms = _timed_ms(f, stream, reps if algo != "simt" else 3)
             gbs = 4.0 * (m * k + k * n + m * n) / (ms * 1e-3) / 1e9
-            rows[algo] = {"ms": ms, "tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12,
-                          "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+            got = C.index_select(1, idx).cpu().numpy()
+            rep = oracle.err_report(got, C64, D, k)
+            rows[arm_name(algo, promote)] = {
+                "ms": ms, "tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "hbm_gbs": gbs,
+                "hbm_frac": gbs / hbm, "max_ratio": rep["max_ratio"],
+                "median_ratio": rep["median_ratio"], "within_plain_bound": rep["n_fail"] == 0}
             del ws
+        h.set_promotion(0)
         out[f"{m}x{n}x{k}"] = rows
-        del A, B, C
+        del A, B, C, Ah, Bh
     return out
+
+
+def _timed_ms(fn, stream, reps):
+    """Mean CUDA-event time of `reps` calls of fn after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _accuracy(p, got_full, cols=None):
+    """Max / median error / plain bound and the oracle's time on the columns
+    `cols` (all when None) of problem p; got_full is C's storage (Fortran)."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta,
+                          p.C, p.ldc, cols=cols)
+    dt = time.perf_counter() - t0
+    sub = got_full[:p.m, :p.n] if cols is None else got_full[:p.m, cols]
+    rep = oracle.err_report(sub, C64, D, p.k)
+    ncols = p.n if cols is None else len(cols)
+    return {"max_ratio": rep["max_ratio"], "median_ratio": rep["median_ratio"],
+            "n_fail": rep["n_fail"], "elements": rep["count"],
+            "within_plain_bound": rep["n_fail"] == 0,
+            "cpu_oracle": {"seconds": dt, "columns": int(ncols),
+                           "gflops": 2.0 * p.m * p.k * ncols / max(dt, 1e-9) / 1e9}}
+
+
+def _run_problem(gb, h, p, algo, dev, stream, reps, promote=0):
+    """Upload p, time gb_sgemm (C restored between calls is not needed: the
+    timed calls overwrite C with alpha*AB + beta*C_prev; the checked result
+    comes from one call on the original C). Returns (ms, C storage)."""
+    import numpy as np
+    import torch
+    h.set_promotion(promote)
+    _, A = gb.from_fortran(p.A, device=dev)
+    _, B = gb.from_fortran(p.B, device=dev)
+    Cfull, _ = gb.from_fortran(p.C, device=dev)
+    C0 = Cfull.clone()
+    ws_n = gb.workspace_size(algo, p.ta, p.tb, p.m, p.n, p.k)
+    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+
+    def f():
+        gb.sgemm_raw(p.ta, p.tb, p.m, p.n, p.k, p.alpha, A.data_ptr(), p.lda, B.data_ptr(),
+                     p.ldb, p.beta, Cfull.data_ptr(), p.ldc, algo=algo, handle=h, workspace=ws,
+                     stream=stream)
+    ms = _timed_ms(f, stream, reps)
+    Cfull.copy_(C0)
+    f()
+    torch.cuda.synchronize()
+    got = gb.to_fortran(Cfull)
+    h.set_promotion(0)
+    return ms, got
+
+
+def bench_configs(gb, h, dev, stream, headline=("fp16x3", 128)):
+    """The paper-shaped workloads besides the 8192^3 headline, each timed on
+    the GPU (CUDA events) with its accuracy against the FP64 oracle (max and
+    median error / plain bound 2*K*u*D, over all or sampled output columns)
+    and the oracle's own time on those columns:
+      plain 384^3 ('N','N', ld = 384, U[-1,1] seed 0, alpha 1, beta 0.5), and
+        its integer variant (entries in {-8..8}: every algorithm bit-exact);
+      the padded-stride sweep: n in {16, 100, 257, 512, 1000, 1023, 2048, 4096,
+        8192}, 4 transposes, ld = stored rows + 7, alpha 1.5, beta -0.5,
+        U[-1,1] seed 1, for SIMT, AUTO and the headline configuration (the
+        paper's size sweep with a stride larger than the row, Sec. 4);
+      the dense layer Y = X W (X 4096 x 1024, W 1024 x 4096, N(0, 1/1024),
+        seed 3) forward and backward through the autograd Function."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    out = {}
+    # ---- 384^3
+    rows = {}
+    for integer in (False, True):
+        p = wl.plain_384(integer=integer)
+        for algo, promote in (("simt", 0), ("auto", 0), headline):
+            name = arm_name(algo, promote) + ("_int" if integer else "")
+            ms, got = _run_problem(gb, h, p, algo, dev, stream, 20, promote)
+            row = {"us": ms * 1e3, "gflops": p.flops / (ms * 1e-3) / 1e9}
+            row.update(_accuracy(p, got))
+            if integer:
+                C64, _ = __import__("oracle").sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A,
+                                                    p.lda, p.B, p.ldb, p.beta, p.C, p.ldc)
+                row["bit_exact"] = bool(np.array_equal(got[:p.m], C64.astype(np.float32)))
+            rows[name] = row
+    out["plain_384"] = {"workload": "M=N=K=384, 'N','N', ld=384, U[-1,1] (seed 0), alpha=1, "
+                                    "beta=0.5; _int: entries in {-8..8}", "rows": rows}
+    # ---- the padded-stride sweep
+    sweep = {}
+    for n in wl.SWEEP_SIZES:
+        for ta, tb in (("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")):
+            p = wl.sweep_case(n, ta, tb)
+            cols = None if n <= 1023 else np.unique(np.linspace(0, n - 1, 16).round().astype(np.int64))
+            for algo, promote in (("simt", 0), ("auto", 0), headline):
+                reps = max(2, min(50, int(2e9 / max(p.flops, 1))))
+                if algo == "simt" and n >= 4096:
+                    reps = 2
+                ms, got = _run_problem(gb, h, p, algo, dev, stream, reps, promote)
+                row = {"ms": ms, "gflops": p.flops / (ms * 1e-3) / 1e9}
+                row.update(_accuracy(p, got, cols))
+                sweep[f"{n}_{ta}{tb}_{arm_name(algo, promote)}"] = row
+            del p
+    out["sweep"] = {"workload": "square n, 4 transposes, ld = stored rows + 7, alpha=1.5, "
+                                "beta=-0.5, U[-1,1] (seed 1); accuracy over all columns for "
+                                "n <= 1023, else 16 sampled columns", "rows": sweep}
+    out["dense_layer"] = bench_dense_layer(gb, dev, stream)
+    return out
+
+
+def bench_dense_layer(gb, dev, stream, reps=10):
+    """Y = X W (X 4096 x 1024, W 1024 x 4096 ~ N(0, 1/1024), upstream G ~ N(0,1),
+    seed 3), forward and backward (dX = G W^T, dW = X^T G) through the
+    autograd Function with AUTO (BF16X3 for all three products: K >= 1024).
+    Each product's accuracy is checked on 16 sampled output columns of its
+    column-major form against the oracle."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1912_04379_gb300 import autograd as ga
+    X, W, G = wl.dense_layer()
+    batch, d_in = X.shape
+    d_out = W.shape[1]
+    Xd = torch.from_numpy(X).to(dev).requires_grad_(True)
+    Wd = torch.from_numpy(W).to(dev).requires_grad_(True)
+    Gd = torch.from_numpy(G).to(dev)
+
+    def fwd_bwd():
+        Xd.grad = None
+        Wd.grad = None
+        Y = ga.linear(Xd, Wd, algo="auto")
+        Y.backward(Gd)
+        return Y
+
+    def fwd():
+        with torch.no_grad():
+            return ga.linear(Xd, Wd, algo="auto")
+
+    flops_fwd = 2.0 * batch * d_in * d_out
+    ms = _timed_ms(fwd_bwd, stream, reps)
+    ms_fwd = _timed_ms(fwd, stream, reps)
+    Y = fwd_bwd()
+    torch.cuda.synchronize()
+    Yt = Y.detach().cpu().numpy().T                  # column-major d_out x batch
+    dXt = Xd.grad.cpu().numpy().T                    # d_in x batch
+    dWt = Wd.grad.cpu().numpy().T                    # d_out x d_in
+    cols = lambda n: np.unique(np.linspace(0, n - 1, 16).round().astype(np.int64))
+    P = wl.Problem
+    checks = {
+        # Y^T = W^T X^T
+        "Y": (P("N", "N", d_out, batch, d_in, 1.0, 0.0, W.T, d_out, X.T, d_in, None, d_out), Yt),
+        # dX^T = W G^T
+        "dX": (P("T", "N", d_in, batch, d_out, 1.0, 0.0, W.T, d_out, G.T, d_out, None, d_in), dXt),
+        # dW^T = G^T X
+        "dW": (P("N", "T", d_out, d_in, batch, 1.0, 0.0, G.T, d_out, X.T, d_in, None, d_out), dWt),
+    }
+    acc = {name: _accuracy(p, got, cols(p.n)) for name, (p, got) in checks.items()}
+    return {"workload": "Y = X W, X 4096x1024, W 1024x4096 ~ N(0,1/1024), G ~ N(0,1) (seed 3); "
+                        "forward + backward through the autograd Function, algo auto",
+            "forward_backward_ms": ms, "forward_backward_tflops": 3 * flops_fwd / (ms * 1e-3) / 1e12,
+            "forward_ms": ms_fwd, "forward_tflops": flops_fwd / (ms_fwd * 1e-3) / 1e12,
+            "accuracy": acc}
 
 
 def plan_launches(plan):
@@ -859,10 +1076,22 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": C_h.numel() * 4,
            "transfers_only_ms": link_ms}
 
-    grouped = None if args.no_grouped else bench_grouped(gb, h, dev, stream)
-    shapes = None if args.no_shapes else bench_shapes(gb, h, dev, stream)
-    mlp = None if args.no_mlp else bench_mlp(gb, h, dev, stream)
-    blas3 = None if args.no_blas3 else bench_blas3(gb, h, dev, stream)
+    def section(skip, fn, *a):
+        """A secondary measurement; a failure in it is recorded in its place
+        instead of ending the run (the headline above is already measured)."""
+        if skip:
+            return None
+        try:
+            return fn(*a)
+        except Exception as e:                       # noqa: BLE001 - recorded, not hidden
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    h.set_promotion(0)           # the sections below set what they need
+    configs = section(args.no_configs, bench_configs, gb, h, dev, stream, (ALGO, PROMOTE))
+    grouped = section(args.no_grouped, bench_grouped, gb, h, dev, stream)
+    shapes = section(args.no_shapes, bench_shapes, gb, h, dev, stream)
+    mlp = section(args.no_mlp, bench_mlp, gb, h, dev, stream)
+    blas3 = section(args.no_blas3, bench_blas3, gb, h, dev, stream)
     measured = measure_rooflines(gb, h, dev, stream)
 
     peaks, peak_kind = load_peaks()
@@ -903,6 +1132,25 @@ def run_ours(args, rank, world, local_rank):
             row["ceiling_tflops"] = ceilings[row["algo"]]
             row["frac"] = row["value"] / ceilings[row["algo"]]
 
+    def resolved(algo, k):
+        """The algorithm a row ran: AUTO resolves by K as the library does
+        (BF16X3 for K >= 1024, BF16X6 for 4 <= K < 1024, else SIMT)."""
+        if algo != "auto":
+            return algo
+        return "bf16x3" if k >= 1024 else "bf16x6" if k >= 4 else "simt"
+
+    if configs and "error" not in configs:
+        for sect, kdim in (("plain_384", lambda name: 384), ("sweep", lambda name: int(name.split("_")[0]))):
+            for name, row in configs[sect]["rows"].items():
+                algo = name.split("+")[0].split("_")[-1] if sect == "sweep" else name.split("+")[0].split("_")[0]
+                r = resolved(algo, kdim(name))
+                row["algo_run"] = r
+                row["ceiling_tflops"] = ceilings[r]
+                row["roofline_frac"] = row["gflops"] / 1e3 / ceilings[r]
+        dl = configs["dense_layer"]
+        dl["ceiling_tflops"] = ceilings["bf16x3"]
+        dl["roofline_frac"] = dl["forward_backward_tflops"] / ceilings["bf16x3"]
+
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -914,7 +1162,7 @@ def run_ours(args, rank, world, local_rank):
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "gpu_launches": 5 * args.steps, "e2e": e2e, "roofline": roofline,
             "pack": pack, "arms": arms, "measured_rooflines": measured, "grouped": grouped,
-            "shapes": shapes, "mlp": mlp, "blas3": blas3, "clocks": clocks,
+            "shapes": shapes, "configs": configs, "mlp": mlp, "blas3": blas3, "clocks": clocks,
             "source_sha": sha}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
