@@ -368,11 +368,28 @@ def measure_rooflines(gb, h, dev, stream):
     finally:
         torch.backends.cuda.matmul.allow_tf32 = old
     tf32 = 2.0 * n ** 3 * 5 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    # cuBLAS FP32 (TF32 off): a yardstick for the SIMT arm, never on the product path
+    old32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        c = a @ b
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            c = a @ b
+        e1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old32
+    fp32_cublas = 2.0 * n ** 3 * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
     del a, b, c
     return {"fp32_simt_tflops": fp32, "fp32_simt_nominal_tflops": nominal,
-            "tf32_tensor_tflops": tf32, "sms": props.multi_processor_count,
+            "tf32_tensor_tflops": tf32, "fp32_cublas_tflops": fp32_cublas,
+            "sms": props.multi_processor_count,
             "how": "FP32: gb_measure_ffma (8 blocks x 256 threads per SM, 128 FMA per thread "
-                   "per iteration); TF32: torch.matmul 8192^3 with TF32 allowed (cuBLAS)"}
+                   "per iteration); TF32: torch.matmul 8192^3 with TF32 allowed (cuBLAS); "
+                   "fp32_cublas: torch.matmul 8192^3 with TF32 off (cuBLAS SGEMM, a "
+                   "yardstick for the SIMT arm, not used by the library)"}
 
 
 def _lib_check(rc):
