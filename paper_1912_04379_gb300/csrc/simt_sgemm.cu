@@ -26,6 +26,23 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8;
 constexpr int NT = 256;
 constexpr int LDS = BM + 4;   // padded shared row (floats); conflict-free transposed stores
+constexpr int LDSB = 2 * BN + 8;   // B panel row: every value stored twice (see below)
+
+// Two IEEE FP32 fused multiply-adds, round to nearest, in one instruction
+// (sm_100 family): d.lo += a.lo * b.lo, d.hi += a.hi * b.hi. Each lane
+// rounds exactly as fmaf does, so results equal the scalar form bit for bit.
+__device__ __forceinline__ void ffma2(unsigned long long &d, unsigned long long a,
+                                      unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+    return v;
+}
 
 // Loads this thread's four elements of a 128 x 8 panel of op(X), where op(X)
 // is (rows x K) and the panel starts at (r0, k0). KC: the stored matrix is
@@ -106,6 +123,37 @@ __device__ __forceinline__ void store_panel(float *__restrict__ S, int t, const 
     }
 }
 
+// store_panel for the op(B)^T panel, each value written twice (adjacent):
+// a 16-byte load then yields two (b_j, b_j) pairs, the operand that
+// multiplies a pair of rows of op(A) in ffma2.
+template <bool KC, bool VEC>
+__device__ __forceinline__ void store_panel_dup(float *__restrict__ S, int t, const float v[4]) {
+    if (!KC) {
+        const int p = t >> 5;
+        if (VEC) {
+            float *d = S + p * LDSB + 2 * ((t & 31) * 4);
+            *reinterpret_cast<float4 *>(d) = make_float4(v[0], v[0], v[1], v[1]);
+            *reinterpret_cast<float4 *>(d + 4) = make_float4(v[2], v[2], v[3], v[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                *reinterpret_cast<float2 *>(S + p * LDSB + 2 * ((t & 31) + 32 * e)) = make_float2(v[e], v[e]);
+        }
+    } else {
+        if (VEC) {
+            const int r = t >> 1, p = (t & 1) * 4;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                *reinterpret_cast<float2 *>(S + (p + e) * LDSB + 2 * r) = make_float2(v[e], v[e]);
+        } else {
+            const int p = t & 7;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                *reinterpret_cast<float2 *>(S + p * LDSB + 2 * ((t >> 3) + 32 * e)) = make_float2(v[e], v[e]);
+        }
+    }
+}
+
 template <bool TA, bool TB, bool VA, bool VB, bool VC>
 __global__ void __launch_bounds__(NT, 2)
 simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
@@ -118,18 +166,20 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
     constexpr bool AKC = TA;
     constexpr bool BKC = !TB;
     __shared__ __align__(16) float As[2][BK * LDS];
-    __shared__ __align__(16) float Bs[2][BK * LDS];
+    __shared__ __align__(16) float Bs[2][BK * LDSB];
 
     const int t = threadIdx.x;
     const int tx = t & 15, ty = t >> 4;
     const int64_t m0 = (int64_t)blockIdx.x * BM;
     const int64_t n0 = (int64_t)blockIdx.y * BN;
 
-    float acc[8][8];
+    // acc2[ip][j]: rows (2ip, 2ip + 1) of the thread's 8 (tx*4 + 0..3,
+    // 64 + tx*4 + 0..3), column j of its 8, as one FP32 pair
+    unsigned long long acc2[4][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 8; ++j) acc2[i][j] = 0ull;
 
     const int64_t nk = (K + BK - 1) / BK;
     float ra[4], rb[4];
@@ -137,7 +187,7 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         load_panel<AKC, VA>(A, lda, M, K, m0, 0, t, ra);
         load_panel<BKC, VB>(B, ldb, N, K, n0, 0, t, rb);
         store_panel<AKC, VA>(As[0], t, ra);
-        store_panel<BKC, VB>(Bs[0], t, rb);
+        store_panel_dup<BKC, VB>(Bs[0], t, rb);
     }
     __syncthreads();
 
@@ -152,27 +202,35 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         const float *bs = Bs[cur];
 #pragma unroll
         for (int p = 0; p < BK; ++p) {
-            float a[8], b[8];
-            const float4 a0 = *reinterpret_cast<const float4 *>(as + p * LDS + tx * 4);
-            const float4 a1 = *reinterpret_cast<const float4 *>(as + p * LDS + 64 + tx * 4);
-            const float4 b0 = *reinterpret_cast<const float4 *>(bs + p * LDS + ty * 4);
-            const float4 b1 = *reinterpret_cast<const float4 *>(bs + p * LDS + 64 + ty * 4);
-            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-            a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
-            b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+            // a pairs straight from two 16-byte loads; b as (b_j, b_j) pairs
+            // from the duplicated panel (four 16-byte loads)
+            const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(as + p * LDS + tx * 4);
+            const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(as + p * LDS + 64 + tx * 4);
+            const float *bp = bs + p * LDSB;
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (ty * 4));
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (ty * 4) + 4);
+            const ulonglong2 b2 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (64 + ty * 4));
+            const ulonglong2 b3 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (64 + ty * 4) + 4);
+            const unsigned long long a[4] = {a0.x, a0.y, a1.x, a1.y};
+            const unsigned long long b[8] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y, b3.x, b3.y};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) ffma2(acc2[i][j], a[i], b[j]);
         }
         if (more) {
             store_panel<AKC, VA>(As[cur ^ 1], t, ra);
-            store_panel<BKC, VB>(Bs[cur ^ 1], t, rb);
+            store_panel_dup<BKC, VB>(Bs[cur ^ 1], t, rb);
         }
         __syncthreads();
         cur ^= 1;
     }
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) unpack2(acc2[i][j], acc[2 * i][j], acc[2 * i + 1][j]);
 
     // Epilogue: thread rows {tx*4 + 0..3, 64 + tx*4 + 0..3}, columns
     // {ty*4 + 0..3, 64 + ty*4 + 0..3}; a warp writes 64 consecutive floats of
