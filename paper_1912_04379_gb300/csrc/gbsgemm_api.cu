@@ -160,6 +160,66 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
 }
 
+}  // namespace
+
+size_t gb::packed_operand_bytes(int mode, bool a_side, int64_t mn, int64_t k) {
+    return packed_bytes(mode, a_side, mn, k);
+}
+
+// The product of a row range of a packed op(A) and a column range of a
+// packed op(B) (see internal.h).
+int gb::compute_packed_view(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k,
+                            float alpha, const void *Ap, int64_t a_rows, int64_t a_row0,
+                            const void *Bp, int64_t b_rows, int64_t b_row0, float beta, float *C,
+                            int64_t ldc, cudaStream_t s) {
+    if (mode == 4 && (b_row0 % 256) != 0) return GB_ERR_ARG;   // one scaling block per tile
+    const int64_t kpad = split_kpad(mode, k);
+    const int64_t eb = split_elem_bytes(mode);
+    TcArgs t{};
+    t.mode = mode;
+    t.m = m; t.n = n; t.k = k; t.kpad = kpad;
+    t.alpha = alpha; t.beta = beta;
+    t.Ap = static_cast<const char *>(Ap) + a_row0 * kpad * eb;
+    t.Bp = static_cast<const char *>(Bp) + b_row0 * kpad * eb;
+    t.a_part_stride = a_rows * kpad; t.b_part_stride = b_rows * kpad;
+    t.C = C; t.ldc = ldc;
+    t.splits = 1;
+    t.dstate = h->dstate;
+    t.wait_limit = h->wait_limit;
+    t.sm_count = h->sm_count;
+    if (mode == 4) {
+        t.amax = packed_max(const_cast<void *>(Ap), mode, true, a_rows, k) + a_row0;
+        t.bmax = packed_max(const_cast<void *>(Bp), mode, false, b_rows, k) + b_row0 / 256;
+    }
+    if (h->promote_k > 0) {
+        const int64_t bk = tc_promo_kblock(mode);
+        const int64_t kb = (h->promote_k + bk - 1) / bk;
+        t.promote_kb = (int)(kb < 1 ? 1 : kb > (1 << 24) ? (1 << 24) : kb);
+    }
+    cudaError_t e = launch_tc_sgemm(t, s);
+    return e == cudaSuccess ? GB_OK : (e == cudaErrorNotSupported ? GB_ERR_UNSUPPORTED : GB_ERR_CUDA);
+}
+
+// Splits and packs rows [row0, row0 + rows) of op(X) into their place in a
+// packed operand of total_rows rows (terms total_rows * kpad apart); for the
+// scaled FP16 split also their row maxima.
+cudaError_t gb::pack_operand_rows(int mode, bool a_side, bool trans, int64_t rows, int64_t k,
+                                  const float *X, int64_t ldx, void *packed, int64_t total_rows,
+                                  int64_t row0, cudaStream_t s) {
+    const int64_t kpad = split_kpad(mode, k);
+    const bool kcontig = a_side ? trans : !trans;
+    char *out = static_cast<char *>(packed) + row0 * kpad * split_elem_bytes(mode);
+    if (mode == 4) {
+        if (!a_side && (row0 % 256) != 0) return cudaErrorInvalidValue;
+        uint32_t *mx = packed_max(packed, mode, a_side, total_rows, k) + (a_side ? row0 : row0 / 256);
+        return launch_split_pack_fp16(a_side, kcontig, rows, k, X, ldx, out, kpad,
+                                      total_rows * kpad, mx, s);
+    }
+    return launch_split_pack(mode, kcontig, rows, k, X, ldx, out, kpad, total_rows * kpad, s);
+}
+
+namespace {
+
 int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_t n, int64_t k,
                float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
                float *C, int64_t ldc, void *ws, size_t ws_bytes, cudaStream_t s) {

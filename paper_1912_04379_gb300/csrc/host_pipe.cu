@@ -12,6 +12,16 @@
 // pipeline starts after the work already enqueued on the caller's stream and
 // the caller's stream waits for its last download, so the call is ordered on
 // that stream like any other, and returns without waiting.
+//
+// For the split algorithms with M and N of at least 2048 a 2-D blocked
+// pipeline replaces it, so that no GEMM waits for all of op(A): op(A) is cut
+// into row blocks A_s and op(B) into column blocks B_s (multiples of 256,
+// about an eighth of each), uploaded in the order A_0, B_0, A_1, B_1, ...
+// and each split and packed once, in place, into whole packed operands.
+// When pair s has arrived, the output blocks (r, j) with max(r, j) = s can
+// be computed: two GEMMs on views of the packed operands (A_s times B_0..s,
+// and A_0..s-1 times B_s), and those blocks (one row strip and one column
+// strip of C) download at once, while pair s + 1 uploads.
 #include <stdint.h>
 
 #include "internal.h"
@@ -92,6 +102,133 @@ bool pipe_ready(gb_handle_t h) {
     return true;
 }
 
+// ---------------------------------------------- 2-D blocked pipeline --
+// Row blocks of op(A) and column blocks of op(B): multiples of 256 (the
+// scaled FP16 split scales op(B) per 256 columns), about an eighth of the
+// dimension and at least 1024.
+int64_t block_2d(int64_t x) {
+    int64_t b = (x + 7) / 8;
+    b = (b + 255) / 256 * 256;
+    return b < 1024 ? 1024 : b;
+}
+
+bool use_2d(int mode, int64_t m, int64_t n, bool compute) {
+    return compute && mode >= 0 && m >= 2048 && n >= 2048;
+}
+
+struct Grid2 {
+    int mode;
+    int64_t mb, nb;           // rows of an op(A) block, columns of an op(B) block
+    int ra, cb;               // number of op(A) and op(B) blocks
+    size_t a_dev, b_dev, a_pack, b_pack, c_dev, total;
+};
+
+void grid2(int mode, int64_t m, int64_t n, int64_t k, Grid2 *G) {
+    G->mode = mode;
+    G->mb = block_2d(m);
+    G->nb = block_2d(n);
+    G->ra = (int)((m + G->mb - 1) / G->mb);
+    G->cb = (int)((n + G->nb - 1) / G->nb);
+    size_t off = 0;
+    G->a_dev = off; off += round_up((size_t)m * (size_t)k * 4, 256);      // op(A) as stored
+    G->b_dev = off; off += round_up((size_t)k * (size_t)n * 4, 256);      // op(B) as stored
+    G->a_pack = off; off += round_up(packed_operand_bytes(mode, true, m, k), 256);
+    G->b_pack = off; off += round_up(packed_operand_bytes(mode, false, n, k), 256);
+    G->c_dev = off; off += round_up((size_t)m * (size_t)n * 4, 256);     // C, ld = M
+    G->total = off;
+}
+
+int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n, int64_t k,
+           float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+           float *C, int64_t ldc, char *ws, cudaStream_t user) {
+    cudaStream_t sin = h->pipe_stream[0], scomp = h->pipe_stream[1], sout = h->pipe_stream[2];
+    cudaEvent_t *ev = h->pipe_event + 8;             // [0] start, then 3 per pair
+    const int pairs = G.ra > G.cb ? G.ra : G.cb;
+    if (1 + 3 * pairs > kPipeEvents - 8) return GB_ERR_UNSUPPORTED;
+    const bool ta_t = is_t(ta), tb_t = is_t(tb);
+    // device copies keep the stored layout: op(A) rows are stored columns
+    // when transposed (ld K), else stored rows (ld M); likewise for op(B)
+    const int64_t lda_d = ta_t ? k : m, ldb_d = tb_t ? n : k;
+    float *Ad = reinterpret_cast<float *>(ws + G.a_dev);
+    float *Bd = reinterpret_cast<float *>(ws + G.b_dev);
+    void *Ap = ws + G.a_pack, *Bp = ws + G.b_pack;
+    float *Cd = reinterpret_cast<float *>(ws + G.c_dev);
+    const bool read_c = beta != 0.f;
+#define GB_TRY(x) do { if ((x) != cudaSuccess) return GB_ERR_CUDA; } while (0)
+    GB_TRY(cudaEventRecord(ev[0], user));
+    for (int i = 0; i < 3; ++i) GB_TRY(cudaStreamWaitEvent(h->pipe_stream[i], ev[0], 0));
+    // the C strips of pair s: rows [r0, r1) x columns [0, c1) and rows [0, r0) x [c0, c1)
+    auto strips = [&](int s, int64_t &r0, int64_t &r1, int64_t &c0, int64_t &c1) {
+        r0 = s < G.ra ? s * G.mb : m;
+        r1 = s < G.ra ? (r0 + G.mb < m ? r0 + G.mb : m) : m;
+        c0 = s < G.cb ? s * G.nb : n;
+        c1 = s < G.cb ? (c0 + G.nb < n ? c0 + G.nb : n) : n;
+    };
+    auto copy_c = [&](bool up, int64_t i0, int64_t i1, int64_t j0, int64_t j1, cudaStream_t st) {
+        if (i1 <= i0 || j1 <= j0) return cudaSuccess;
+        return up ? cudaMemcpy2DAsync(Cd + i0 + j0 * m, (size_t)m * 4, C + i0 + j0 * ldc,
+                                      (size_t)ldc * 4, (size_t)(i1 - i0) * 4, (size_t)(j1 - j0),
+                                      cudaMemcpyHostToDevice, st)
+                  : cudaMemcpy2DAsync(C + i0 + j0 * ldc, (size_t)ldc * 4, Cd + i0 + j0 * m,
+                                      (size_t)m * 4, (size_t)(i1 - i0) * 4, (size_t)(j1 - j0),
+                                      cudaMemcpyDeviceToHost, st);
+    };
+    for (int s = 0; s < pairs; ++s) {
+        cudaEvent_t ev_a = ev[1 + 3 * s], ev_b = ev[2 + 3 * s], ev_c = ev[3 + 3 * s];
+        int64_t r0, r1, c0, c1;
+        strips(s, r0, r1, c0, c1);
+        // ---- upload A_s, then B_s (and the C strips when beta != 0)
+        if (s < G.ra) {
+            if (!ta_t)       // rows r0..r1 of the m x k stored A
+                GB_TRY(cudaMemcpy2DAsync(Ad + r0, (size_t)m * 4, A + r0, (size_t)lda * 4,
+                                         (size_t)(r1 - r0) * 4, (size_t)k, cudaMemcpyHostToDevice, sin));
+            else             // columns r0..r1 of the k x m stored A
+                GB_TRY(cudaMemcpy2DAsync(Ad + r0 * k, (size_t)k * 4, A + r0 * lda, (size_t)lda * 4,
+                                         (size_t)k * 4, (size_t)(r1 - r0), cudaMemcpyHostToDevice, sin));
+        }
+        GB_TRY(cudaEventRecord(ev_a, sin));
+        if (s < G.cb) {
+            if (!tb_t)       // columns c0..c1 of the k x n stored B
+                GB_TRY(cudaMemcpy2DAsync(Bd + c0 * k, (size_t)k * 4, B + c0 * ldb, (size_t)ldb * 4,
+                                         (size_t)k * 4, (size_t)(c1 - c0), cudaMemcpyHostToDevice, sin));
+            else             // rows c0..c1 of the n x k stored B
+                GB_TRY(cudaMemcpy2DAsync(Bd + c0, (size_t)n * 4, B + c0, (size_t)ldb * 4,
+                                         (size_t)(c1 - c0) * 4, (size_t)k, cudaMemcpyHostToDevice, sin));
+        }
+        if (read_c) {
+            GB_TRY(copy_c(true, r0, r1, 0, c1, sin));
+            GB_TRY(copy_c(true, 0, r0, c0, c1, sin));
+        }
+        GB_TRY(cudaEventRecord(ev_b, sin));
+        // ---- pack A_s and B_s in place, then the two GEMMs of the L
+        int rc = GB_OK;
+        GB_TRY(cudaStreamWaitEvent(scomp, ev_a, 0));
+        if (s < G.ra)
+            GB_TRY(pack_operand_rows(G.mode, true, ta_t, r1 - r0, k, ta_t ? Ad + r0 * k : Ad + r0,
+                                     lda_d, Ap, m, r0, scomp));
+        GB_TRY(cudaStreamWaitEvent(scomp, ev_b, 0));
+        if (s < G.cb)
+            GB_TRY(pack_operand_rows(G.mode, false, tb_t, c1 - c0, k, tb_t ? Bd + c0 : Bd + c0 * k,
+                                     ldb_d, Bp, n, c0, scomp));
+        if (r1 > r0 && c1 > 0)       // A_s x B_0 .. B_s
+            rc = compute_packed_view(h, G.mode, r1 - r0, c1, k, alpha, Ap, m, r0, Bp, n, 0, beta,
+                                     Cd + r0, m, scomp);
+        if (!rc && r0 > 0 && c1 > c0)   // A_0 .. A_s-1 x B_s
+            rc = compute_packed_view(h, G.mode, r0, c1 - c0, k, alpha, Ap, m, 0, Bp, n, c0, beta,
+                                     Cd + c0 * m, m, scomp);
+        if (rc) return rc;
+        GB_TRY(cudaEventRecord(ev_c, scomp));
+        // ---- download the finished strips
+        GB_TRY(cudaStreamWaitEvent(sout, ev_c, 0));
+        GB_TRY(copy_c(false, r0, r1, 0, c1, sout));
+        GB_TRY(copy_c(false, 0, r0, c0, c1, sout));
+    }
+    GB_TRY(cudaEventRecord(ev[1], sout));    // reused: every wait on it was enqueued above
+    GB_TRY(cudaStreamWaitEvent(user, ev[1], 0));
+#undef GB_TRY
+    return GB_OK;
+}
+
 }  // namespace
 
 void destroy_pipe(gb_handle_t h) {
@@ -116,6 +253,11 @@ GB_API int gb_sgemm_host_workspace_size(gb_algo_t algo, char ta, char tb, int64_
     rc = layout(algo, ta, tb, m, n, k, 1.f, &L);
     if (rc) return rc;
     *bytes = L.total;
+    if (use_2d(L.mode, m, n, L.compute)) {
+        Grid2 G;
+        grid2(L.mode, m, n, k, &G);
+        *bytes = G.total;
+    }
     return GB_OK;
 }
 
@@ -141,6 +283,12 @@ GB_API int gb_sgemm_host(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_
     if (ws_bytes < full || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
         return GB_ERR_WORKSPACE;
     if (!pipe_ready(h)) return GB_ERR_CUDA;
+    if (use_2d(L.mode, m, n, L.compute)) {
+        Grid2 G;
+        grid2(L.mode, m, n, k, &G);
+        return run_2d(h, G, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      static_cast<char *>(workspace), static_cast<cudaStream_t>(stream));
+    }
 
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     cudaStream_t sin = h->pipe_stream[0], scomp = h->pipe_stream[1], sout = h->pipe_stream[2];

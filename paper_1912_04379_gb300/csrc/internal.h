@@ -47,7 +47,7 @@ struct gb_handle_s {
     // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
     bool pipe_ready;
     cudaStream_t pipe_stream[3];
-    cudaEvent_t pipe_event[8];
+    cudaEvent_t pipe_event[40];
     // grouped runs: a side stream for the SIMT part, forked from and joined
     // to the caller's stream (created when a plan has both parts)
     bool side_ready;
@@ -61,7 +61,7 @@ struct gb_handle_s {
 namespace gb {
 
 constexpr int kHandleMagic = 0x6b5e3a21;
-constexpr int kPipeEvents = 8;
+constexpr int kPipeEvents = 40;   // 8 for the column-block pipeline, 32 for the 2-D one
 void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events
 void destroy_side(gb_handle_t h);     // releases the grouped runs' side stream and events
 // Device address of gb_sgemm_noalloc's static scratch array on the current
@@ -232,6 +232,22 @@ int sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_
               float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
               float *C, int64_t ldc, const EpiOp &op, void *ws, size_t ws_bytes, cudaStream_t s,
               bool *fused);
+
+// C <- alpha op(A)[a_row0 .. a_row0+m) op(B)[:, b_row0 .. b_row0+n) + beta C,
+// from whole packed operands of a_rows rows (op(A)) and b_rows columns
+// (op(B)), as gb_sgemm_pack laid them out; no split-K. Mode 4 needs b_row0 a
+// multiple of 256 (its column-block scaling). Returns a GB_* status.
+int compute_packed_view(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, float alpha,
+                        const void *Ap, int64_t a_rows, int64_t a_row0, const void *Bp,
+                        int64_t b_rows, int64_t b_row0, float beta, float *C, int64_t ldc,
+                        cudaStream_t s);
+// Split + pack rows [row0, row0+rows) of op(X) (a_side) or op(B)^T into the
+// packed operand of total_rows rows at `packed` (layout of gb_sgemm_pack).
+cudaError_t pack_operand_rows(int mode, bool a_side, bool trans, int64_t rows, int64_t k,
+                              const float *X, int64_t ldx, void *packed, int64_t total_rows,
+                              int64_t row0, cudaStream_t s);
+// Bytes of one packed operand (gb_sgemm_pack_size's value).
+size_t packed_operand_bytes(int mode, bool a_side, int64_t mn, int64_t k);
 
 // AUTO's choice for a given K, and the split mode of an algorithm (-1: SIMT).
 gb_algo_t resolve_algo(gb_algo_t algo, int64_t k);

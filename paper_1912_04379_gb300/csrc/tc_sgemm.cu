@@ -141,14 +141,17 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 3-D map over [terms][rows][kpad] (K innermost), box = BK x box_rows x 1.
+// term_stride: elements between terms (0: rows * kpad, a whole packed
+// operand; larger when the rows are a range of a bigger packed operand).
 bool make_map(CUtensorMap *map, int fmt, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
-              int parts, int box_rows, int bk, int row_bytes) {
+              int parts, int box_rows, int bk, int row_bytes, int64_t term_stride = 0) {
     auto enc = get_encode();
     if (!enc) return false;
     const bool tf32 = fmt == kFmtTF32;
     const int eb = tf32 ? 4 : 2;
     cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)parts};
-    cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(rows * kpad * eb)};
+    const int64_t ts = term_stride > 0 ? term_stride : rows * kpad;
+    cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(ts * eb)};
     cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -180,8 +183,10 @@ cudaError_t launch_mode(const TcArgs &a, cudaStream_t s) {
     if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
         return cudaErrorNotSupported;
     alignas(64) CUtensorMap ma, mb;
-    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, RB) ||
-        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, RB))
+    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, RB,
+                  a.a_part_stride) ||
+        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, RB,
+                  a.b_part_stride))
         return cudaErrorInvalidValue;
     const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
     const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;
@@ -222,8 +227,10 @@ cudaError_t launch_promo_mode(const TcArgs &a, cudaStream_t s) {
     if (a.m > 2147483647LL || a.n > 2147483647LL || a.k > 2147483647LL)
         return cudaErrorNotSupported;
     alignas(64) CUtensorMap ma, mb;
-    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, CF::ROW_BYTES) ||
-        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, CF::ROW_BYTES))
+    if (!make_map(&ma, CF::FMT, a.Ap, a.k, a.m, a.kpad, CF::A_PARTS, BM, CF::BK, CF::ROW_BYTES,
+                  a.a_part_stride) ||
+        !make_map(&mb, CF::FMT, a.Bp, a.k, a.n, a.kpad, CF::B_PARTS, CF::BN, CF::BK, CF::ROW_BYTES,
+                  a.b_part_stride))
         return cudaErrorInvalidValue;
     const int splits = a.part ? (a.splits > 1 ? a.splits : 1) : 1;
     const int64_t units = ((a.m + BM - 1) / BM) * ((a.n + CF::BN - 1) / CF::BN) * splits;

@@ -94,3 +94,48 @@ def test_host_pipeline_argument_errors():
     assert gb.sgemm_host_raw("X", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4, check=False) == -1
     assert gb.sgemm_host_raw("N", "N", 4, 4, 4, 1.0, 0, 3, 0, 4, 0.0, 0, 4, check=False) == -8
     assert gb.sgemm_host_raw("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 3, check=False) == -13
+
+
+# ---- the 2-D blocked pipeline (split algorithms, M and N >= 2048): op(A) row
+# blocks and op(B) column blocks of 1024 (ragged last ones), unequal counts
+
+SHAPES_2D = [(2100, 2300, 700), (4100, 2048, 300), (2048, 5000, 1500)]
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("shape", SHAPES_2D, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("algo", ("bf16x6", "fp16x3", "auto"))
+def test_host_pipeline_2d_against_oracle(algo, shape, ta, tb):
+    m, n, k = shape
+    p = wl.make_problem(ta, tb, m, n, k, 1.25, -0.5, seed=m + 3 * n + k, ld_pad=3)
+    got = _run_host(p, algo)
+    if algo == "auto":
+        algo = "bf16x3" if k >= 1024 else "bf16x6"
+    # every block boundary of C and its neighbours, plus a spread of columns
+    cols = np.unique(np.r_[0, 1, np.arange(1023, n, 1024), np.arange(1024, n, 1024),
+                           np.linspace(0, n - 1, 24).round().astype(int), n - 1])
+    cols = cols[cols < n]
+    assert_within_bound(p, got, cols=cols, algo=algo)
+    check_padding(p, got)
+
+
+@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6", "fp16x3"))
+def test_host_pipeline_2d_equals_device_gemm(algo):
+    """K > 2048: the blocked GEMMs run the same kernel configuration as one
+    gb_sgemm over the whole shape (which has enough tiles not to split K),
+    and an output element's arithmetic does not depend on its tile, so the
+    results agree bit for bit; beta = 0 with NaN in C (not read)."""
+    torch = torch_gpu()
+    import paper_1912_04379_gb300 as gb
+    from _gpu import run
+    p = wl.make_problem("N", "T", 2100, 2300, 2500, 1.0, 0.0, seed=86, dist="logu", ld_pad=1)
+    p.C[:p.m, :] = np.nan
+    got = _run_host(p, algo)
+    _, want = run(p, algo)
+    assert np.array_equal(got[:p.m], want[:p.m])
+    check_padding(p, got)
+
+
+def test_host_pipeline_2d_integer_bit_exact_beta():
+    p = wl.make_problem("T", "N", 3000, 2200, 900, 1.0, -0.5, seed=87, dist="int", ld_pad=2)
+    assert_bit_exact(p, _run_host(p, "bf16x6"))
