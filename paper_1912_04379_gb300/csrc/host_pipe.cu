@@ -20,8 +20,10 @@
 // and each split and packed once, in place, into whole packed operands.
 // When pair s has arrived, the output blocks (r, j) with max(r, j) = s can
 // be computed: two GEMMs on views of the packed operands (A_s times B_0..s,
-// and A_0..s-1 times B_s), and those blocks (one row strip and one column
-// strip of C) download at once, while pair s + 1 uploads.
+// and A_0..s-1 times B_s), each on its own stream so that one's last,
+// partial wave of tiles overlaps the other, and those blocks (one row strip
+// and one column strip of C) download as each GEMM finishes, while pair s + 1
+// uploads and, on a fifth stream, is split and packed.
 #include <stdint.h>
 
 #include "internal.h"
@@ -92,7 +94,7 @@ int check_args(char ta, char tb, int64_t m, int64_t n, int64_t k, int64_t lda, i
 // The handle's pipeline streams and events, created on first use.
 bool pipe_ready(gb_handle_t h) {
     if (h->pipe_ready) return true;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < kPipeStreams; ++i)
         if (cudaStreamCreateWithFlags(&h->pipe_stream[i], cudaStreamNonBlocking) != cudaSuccess)
             return false;
     for (int i = 0; i < kPipeEvents; ++i)
@@ -141,10 +143,11 @@ void grid2(int mode, int64_t m, int64_t n, int64_t k, Grid2 *G) {
 int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n, int64_t k,
            float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
            float *C, int64_t ldc, char *ws, cudaStream_t user) {
-    cudaStream_t sin = h->pipe_stream[0], scomp = h->pipe_stream[1], sout = h->pipe_stream[2];
-    cudaEvent_t *ev = h->pipe_event + 8;             // [0] start, then 3 per pair
+    cudaStream_t sin = h->pipe_stream[0], sg1 = h->pipe_stream[1], sout = h->pipe_stream[2];
+    cudaStream_t spack = h->pipe_stream[3], sg2 = h->pipe_stream[4];
+    cudaEvent_t *ev = h->pipe_event + 8;             // [0] start, then 5 per pair, then the end
     const int pairs = G.ra > G.cb ? G.ra : G.cb;
-    if (1 + 3 * pairs > kPipeEvents - 8) return GB_ERR_UNSUPPORTED;
+    if (2 + 5 * pairs > kPipeEvents - 8) return GB_ERR_UNSUPPORTED;
     const bool ta_t = is_t(ta), tb_t = is_t(tb);
     // device copies keep the stored layout: op(A) rows are stored columns
     // when transposed (ld K), else stored rows (ld M); likewise for op(B)
@@ -156,7 +159,7 @@ int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n
     const bool read_c = beta != 0.f;
 #define GB_TRY(x) do { if ((x) != cudaSuccess) return GB_ERR_CUDA; } while (0)
     GB_TRY(cudaEventRecord(ev[0], user));
-    for (int i = 0; i < 3; ++i) GB_TRY(cudaStreamWaitEvent(h->pipe_stream[i], ev[0], 0));
+    for (int i = 0; i < 5; ++i) GB_TRY(cudaStreamWaitEvent(h->pipe_stream[i], ev[0], 0));
     // the C strips of pair s: rows [r0, r1) x columns [0, c1) and rows [0, r0) x [c0, c1)
     auto strips = [&](int s, int64_t &r0, int64_t &r1, int64_t &c0, int64_t &c1) {
         r0 = s < G.ra ? s * G.mb : m;
@@ -174,7 +177,8 @@ int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n
                                       cudaMemcpyDeviceToHost, st);
     };
     for (int s = 0; s < pairs; ++s) {
-        cudaEvent_t ev_a = ev[1 + 3 * s], ev_b = ev[2 + 3 * s], ev_c = ev[3 + 3 * s];
+        cudaEvent_t ev_a = ev[1 + 5 * s], ev_b = ev[2 + 5 * s], ev_p = ev[3 + 5 * s];
+        cudaEvent_t ev_g1 = ev[4 + 5 * s], ev_g2 = ev[5 + 5 * s];
         int64_t r0, r1, c0, c1;
         strips(s, r0, r1, c0, c1);
         // ---- upload A_s, then B_s (and the C strips when beta != 0)
@@ -200,31 +204,39 @@ int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n
             GB_TRY(copy_c(true, 0, r0, c0, c1, sin));
         }
         GB_TRY(cudaEventRecord(ev_b, sin));
-        // ---- pack A_s and B_s in place, then the two GEMMs of the L
-        int rc = GB_OK;
-        GB_TRY(cudaStreamWaitEvent(scomp, ev_a, 0));
+        // ---- split and pack A_s and B_s in place (their own stream)
+        GB_TRY(cudaStreamWaitEvent(spack, ev_a, 0));
         if (s < G.ra)
             GB_TRY(pack_operand_rows(G.mode, true, ta_t, r1 - r0, k, ta_t ? Ad + r0 * k : Ad + r0,
-                                     lda_d, Ap, m, r0, scomp));
-        GB_TRY(cudaStreamWaitEvent(scomp, ev_b, 0));
+                                     lda_d, Ap, m, r0, spack));
+        GB_TRY(cudaStreamWaitEvent(spack, ev_b, 0));
         if (s < G.cb)
             GB_TRY(pack_operand_rows(G.mode, false, tb_t, c1 - c0, k, tb_t ? Bd + c0 : Bd + c0 * k,
-                                     ldb_d, Bp, n, c0, scomp));
+                                     ldb_d, Bp, n, c0, spack));
+        GB_TRY(cudaEventRecord(ev_p, spack));
+        // ---- the two GEMMs of the L, on two streams (packs of pairs <= s done)
+        int rc = GB_OK;
+        GB_TRY(cudaStreamWaitEvent(sg1, ev_p, 0));
         if (r1 > r0 && c1 > 0)       // A_s x B_0 .. B_s
             rc = compute_packed_view(h, G.mode, r1 - r0, c1, k, alpha, Ap, m, r0, Bp, n, 0, beta,
-                                     Cd + r0, m, scomp);
-        if (!rc && r0 > 0 && c1 > c0)   // A_0 .. A_s-1 x B_s
-            rc = compute_packed_view(h, G.mode, r0, c1 - c0, k, alpha, Ap, m, 0, Bp, n, c0, beta,
-                                     Cd + c0 * m, m, scomp);
+                                     Cd + r0, m, sg1);
         if (rc) return rc;
-        GB_TRY(cudaEventRecord(ev_c, scomp));
-        // ---- download the finished strips
-        GB_TRY(cudaStreamWaitEvent(sout, ev_c, 0));
+        GB_TRY(cudaEventRecord(ev_g1, sg1));
+        GB_TRY(cudaStreamWaitEvent(sg2, ev_p, 0));
+        if (r0 > 0 && c1 > c0)       // A_0 .. A_s-1 x B_s
+            rc = compute_packed_view(h, G.mode, r0, c1 - c0, k, alpha, Ap, m, 0, Bp, n, c0, beta,
+                                     Cd + c0 * m, m, sg2);
+        if (rc) return rc;
+        GB_TRY(cudaEventRecord(ev_g2, sg2));
+        // ---- download each strip when its GEMM is done
+        GB_TRY(cudaStreamWaitEvent(sout, ev_g1, 0));
         GB_TRY(copy_c(false, r0, r1, 0, c1, sout));
+        GB_TRY(cudaStreamWaitEvent(sout, ev_g2, 0));
         GB_TRY(copy_c(false, 0, r0, c0, c1, sout));
     }
-    GB_TRY(cudaEventRecord(ev[1], sout));    // reused: every wait on it was enqueued above
-    GB_TRY(cudaStreamWaitEvent(user, ev[1], 0));
+    cudaEvent_t ev_end = ev[1 + 5 * pairs];
+    GB_TRY(cudaEventRecord(ev_end, sout));
+    GB_TRY(cudaStreamWaitEvent(user, ev_end, 0));
 #undef GB_TRY
     return GB_OK;
 }
@@ -233,7 +245,7 @@ int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n
 
 void destroy_pipe(gb_handle_t h) {
     if (!h->pipe_ready) return;
-    for (int i = 0; i < 3; ++i) cudaStreamDestroy(h->pipe_stream[i]);
+    for (int i = 0; i < kPipeStreams; ++i) cudaStreamDestroy(h->pipe_stream[i]);
     for (int i = 0; i < kPipeEvents; ++i) cudaEventDestroy(h->pipe_event[i]);
     h->pipe_ready = false;
 }

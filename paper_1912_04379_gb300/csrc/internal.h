@@ -46,8 +46,8 @@ struct gb_handle_s {
     int64_t promote_k;          // promoted accumulation: chunk length in K (0 = off)
     // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
     bool pipe_ready;
-    cudaStream_t pipe_stream[3];
-    cudaEvent_t pipe_event[40];
+    cudaStream_t pipe_stream[6];   // copy-in, compute, copy-out, then pack and a second GEMM stream
+    cudaEvent_t pipe_event[56];
     // grouped runs: a side stream for the SIMT part, forked from and joined
     // to the caller's stream (created when a plan has both parts)
     bool side_ready;
@@ -61,7 +61,8 @@ struct gb_handle_s {
 namespace gb {
 
 constexpr int kHandleMagic = 0x6b5e3a21;
-constexpr int kPipeEvents = 40;   // 8 for the column-block pipeline, 32 for the 2-D one
+constexpr int kPipeStreams = 6;
+constexpr int kPipeEvents = 56;   // 8 for the column-block pipeline, 48 for the 2-D one
 void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events
 void destroy_side(gb_handle_t h);     // releases the grouped runs' side stream and events
 // Device address of gb_sgemm_noalloc's static scratch array on the current
