@@ -244,9 +244,10 @@ struct gb_grouped_plan_s {
     gb::GItem *d_items;
     // tensor-core part: packed operands, tensor maps, problems, tiles and
     // pack tiles, all in device memory owned by the plan. Tiles are grouped
-    // by split mode (one launch per mode present), LPT order within a mode.
+    // by (split mode, kernel configuration): one launch per segment present,
+    // segment mode * kGroupedConfigVariants + configuration, LPT order within.
     int64_t tc_nitems, tc_npack;
-    int64_t tc_seg_off[4], tc_seg_n[4];
+    int64_t tc_seg_off[4 * gb::kGroupedConfigVariants], tc_seg_n[4 * gb::kGroupedConfigVariants];
     void *tc_packed;
     CUtensorMap *tc_maps;
     gb::TcProblem *tc_probs;
@@ -303,6 +304,10 @@ bool upload(T **dptr, const std::vector<T> &v) {
            cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
+// Routing values of a size class: 0 = SIMT 64 x 64 tiles, 1 = SIMT 128 x 128
+// tiles, 2 + v = tensor cores in grouped configuration v.
+constexpr int kChoices = 2 + gb::kGroupedConfigVariants;
+
 // Builds a plan for validated problems; choice[c] routes size class c.
 // Returns a GB status; on error frees everything it allocated.
 // pref: preferred split mode of the tensor-core problems (kPrefAuto: by K).
@@ -312,12 +317,17 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
     std::vector<GProblem> probs;
     std::vector<GItem> items;
     std::vector<double> work;
-    struct TcPending { size_t prob; size_t off_a, off_b; int mode; };
+    struct TcPending { size_t prob; size_t off_a, off_b; int mode, v; };
     std::vector<TcPending> tcs;
     size_t packed_bytes = 0;
-    auto route = [&](const gb_gemm_problem_t &p, bool scale_only) {
+    auto route_choice = [&](const gb_gemm_problem_t &p, bool scale_only) {
         return (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
                                        : choice[size_class(p.m, p.n, p.k)];
+    };
+    // 0 / 1: SIMT tiles, 2: tensor cores (configuration route_choice - 2)
+    auto route = [&](const gb_gemm_problem_t &p, bool scale_only) {
+        const int c = route_choice(p, scale_only);
+        return c >= 2 ? 2 : c;
     };
     // Under AUTO, the BF16 x 2 terms problems (K >= 1024) get a launch of
     // their own only if they fill at least one round of the persistent grid;
@@ -330,7 +340,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             const bool so = p.alpha == 0.f || p.k == 0;
             if (p.m == 0 || p.n == 0 || so || route(p, so) != 2 || tc_mode_for(pref, p.k) != 1)
                 continue;
-            const int64_t bn1 = tc_grouped_tile_n();
+            const int64_t bn1 = tc_grouped_tile_n(route_choice(p, so) - 2);
             x2_tiles += ((p.m + 127) / 128) * ((p.n + bn1 - 1) / bn1);
         }
         x2_own_launch = x2_tiles >= 2 * h->sm_count;   // one round: two CTAs per SM
@@ -345,7 +355,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             if (mode == 1 && !x2_own_launch) mode = 2;
             const size_t kpad = (size_t)split_kpad(mode, p.k);
             const size_t per = (size_t)split_parts(mode) * kpad * (size_t)split_elem_bytes(mode);
-            TcPending t{i, packed_bytes, 0, mode};
+            TcPending t{i, packed_bytes, 0, mode, route_choice(p, scale_only) - 2};
             packed_bytes += round_up(per * (size_t)p.m, 1024);
             t.off_b = packed_bytes;
             packed_bytes += round_up(per * (size_t)p.n, 1024);
@@ -404,12 +414,12 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
         char *base = static_cast<char *>(pl->tc_packed);
         for (size_t j = 0; ok && j < tcs.size(); ++j) {
             const gb_gemm_problem_t &p = ps[tcs[j].prob];
-            const int mode = tcs[j].mode;
-            const int bn = tc_grouped_tile_n();
+            const int mode = tcs[j].mode, v = tcs[j].v;
+            const int bn = tc_grouped_tile_n(v);
             const int64_t kpad = split_kpad(mode, p.k);
             char *pa = base + tcs[j].off_a, *pb = base + tcs[j].off_b;
-            ok = tc_make_grouped_operand_map(&maps[2 * j], mode, pa, p.k, p.m, true) &&
-                 tc_make_grouped_operand_map(&maps[2 * j + 1], mode, pb, p.k, p.n, false);
+            ok = tc_make_grouped_operand_map(&maps[2 * j], mode, v, pa, p.k, p.m, true) &&
+                 tc_make_grouped_operand_map(&maps[2 * j + 1], mode, v, pb, p.k, p.n, false);
             TcProblem &t = tprobs[j];
             t.mapA = pl->tc_maps + 2 * j;
             t.mapB = pl->tc_maps + 2 * j + 1;
@@ -420,8 +430,8 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             for (int tm = 0; tm < tiles_m; ++tm)
                 for (int tn = 0; tn < tiles_n; ++tn) {
                     titems.push_back(TcItem{(int)j, tm, tn, 0});
-                    twork.push_back((double)p.k);
-                    tmode.push_back(mode);
+                    twork.push_back((double)p.k * bn);
+                    tmode.push_back(mode * kGroupedConfigVariants + v);   // segment
                 }
             // pack tiles of op(A) (M x K, K-contiguous iff A is transposed) and
             // op(B)^T (N x K, K-contiguous iff B is not transposed)
@@ -455,7 +465,8 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
             tsorted[i] = titems[tord[i]];
             ++pl->tc_seg_n[tmode[tord[i]]];
         }
-        for (int md = 1; md < 4; ++md) pl->tc_seg_off[md] = pl->tc_seg_off[md - 1] + pl->tc_seg_n[md - 1];
+        for (int sg = 1; sg < 4 * kGroupedConfigVariants; ++sg)
+            pl->tc_seg_off[sg] = pl->tc_seg_off[sg - 1] + pl->tc_seg_n[sg - 1];
         ok = ok &&
              cudaMemcpy(pl->tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -490,10 +501,11 @@ int run_plan(gb_grouped_plan_s *plan, void *workspace, cudaStream_t s) {
     if (plan->tc_nitems > 0) {
         if (launch_split_pack_grouped(plan->tc_pack, plan->tc_npack, s) != cudaSuccess)
             return GB_ERR_CUDA;
-        for (int md = 0; md < 4; ++md) {
-            if (plan->tc_seg_n[md] == 0) continue;
-            if (launch_tc_grouped(md, plan->tc_probs, plan->tc_items + plan->tc_seg_off[md],
-                                  plan->tc_seg_n[md], plan->h->sm_count, plan->h->dstate,
+        for (int sg = 0; sg < 4 * kGroupedConfigVariants; ++sg) {
+            if (plan->tc_seg_n[sg] == 0) continue;
+            if (launch_tc_grouped(sg / kGroupedConfigVariants, sg % kGroupedConfigVariants,
+                                  plan->tc_probs, plan->tc_items + plan->tc_seg_off[sg],
+                                  plan->tc_seg_n[sg], plan->h->sm_count, plan->h->dstate,
                                   plan->h->wait_limit, s) != cudaSuccess)
                 return GB_ERR_CUDA;
         }
@@ -584,7 +596,9 @@ int time_choice(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps
 
 // Autotuner: for each size class, time a synthetic group of square problems
 // of the class's middle size (geometric mean 2^(c+3.5)) under each candidate
-// (SIMT 64x64 tiles, SIMT 128x128 tiles, tensor cores) and keep the fastest.
+// (SIMT 64x64 tiles, SIMT 128x128 tiles, and the tensor cores in each of the
+// three grouped configurations: tile width, row width, stage count and CTAs
+// per SM, see tc_body.cuh) and keep the fastest.
 // A class timed alone does not see that its SIMT part and the tensor-core
 // part of a mixed group share the SMs (a SIMT CTA does not fit beside two
 // tensor-core CTAs), so the per-class choice is then checked on one mixed
@@ -614,7 +628,7 @@ int autotune(gb_handle_t h, int dev) {
         const std::vector<gb_gemm_problem_t> ps = synthetic(buf, g, d, 0);
         float best = 1e30f;
         int best_ch = 1;
-        for (int ch = 0; ch < 3 && rc == GB_OK; ++ch) {
+        for (int ch = 0; ch < kChoices && rc == GB_OK; ++ch) {
             int choice[kClasses];
             for (int q = 0; q < kClasses; ++q) choice[q] = ch;
             float ms = 1e30f;
@@ -627,7 +641,7 @@ int autotune(gb_handle_t h, int dev) {
     // The mixed check: 16 problems of each class's middle size (4 of the
     // largest), about 0.24 GB of scratch.
     bool any_simt = false;
-    for (int c = 0; c < kClasses; ++c) any_simt |= h->grouped_choice[c] != 2;
+    for (int c = 0; c < kClasses; ++c) any_simt |= h->grouped_choice[c] < 2;
     // a mixed plan runs its two parts concurrently only on the side stream
     if (rc == GB_OK && any_simt && !ensure_side(h)) rc = GB_ERR_CUDA;
     if (rc == GB_OK && any_simt) {
@@ -648,13 +662,13 @@ int autotune(gb_handle_t h, int dev) {
             int tuned[kClasses], all_tc[kClasses];
             for (int c = 0; c < kClasses; ++c) {
                 tuned[c] = h->grouped_choice[c];
-                all_tc[c] = 2;
+                all_tc[c] = tuned[c] >= 2 ? tuned[c] : 2;   // SIMT classes to configuration 0
             }
             float t_tuned = 1e30f, t_tc = 1e30f;
             rc = time_choice(h, dev, mix, tuned, ws, s, e0, e1, &t_tuned);
             if (rc == GB_OK) rc = time_choice(h, dev, mix, all_tc, ws, s, e0, e1, &t_tc);
             if (rc == GB_OK && t_tc < t_tuned)
-                for (int c = 0; c < kClasses; ++c) h->grouped_choice[c] = 2;
+                for (int c = 0; c < kClasses; ++c) h->grouped_choice[c] = all_tc[c];
         }
         for (float *b : bufs) cudaFree(b);
     }
@@ -709,9 +723,12 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
         for (int c = 0; c < kClasses; ++c) choice[c] = h->grouped_choice[c];
     } else {
         // SIMT: 64x64 tiles for the three smallest classes, else 128x128;
-        // a split algorithm: every problem with K >= 4 on the tensor cores
+        // a split algorithm: every problem with K >= 4 on the tensor cores,
+        // in the configuration the tuner chose for its class if the handle
+        // has tuned (or loaded) one, else configuration 0
         for (int c = 0; c < kClasses; ++c)
-            choice[c] = algo == GB_ALGO_SIMT ? (c < 3 ? 0 : 1) : 2;
+            choice[c] = algo == GB_ALGO_SIMT ? (c < 3 ? 0 : 1)
+                        : (h->grouped_tuned && h->grouped_choice[c] >= 2 ? h->grouped_choice[c] : 2);
     }
     // the scaled FP16 split has no grouped kernel: its problems take TF32X3,
     // whose per-product error is of the same order (3 * 2^-22)

@@ -39,7 +39,8 @@ struct gb_handle_s {
     int64_t wait_limit;
     gb::DeviceState *dstate;   // device memory
     // Grouped autotuner result, per size class of a problem (see grouped.cu):
-    // 0 = SIMT 64x64 tiles, 1 = SIMT 128x128 tiles, 2 = tensor cores (BF16 x 3).
+    // 0 = SIMT 64x64 tiles, 1 = SIMT 128x128 tiles, 2 + v = tensor cores in
+    // grouped configuration v.
     bool grouped_tuned;
     int grouped_choice[8];
     bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
@@ -202,10 +203,13 @@ bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k);
 bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *packed, int64_t k,
                          int64_t rows, bool a_side);
 // The grouped kernel's tile width (128 for every split) and operand maps.
-int tc_grouped_tile_n();
-bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, const void *packed, int64_t k,
+// Grouped configurations v = 0..kGroupedConfigVariants-1 (see tc_body.cuh).
+constexpr int kGroupedConfigVariants = 3;
+int tc_grouped_tile_n(int v);
+int tc_grouped_row_bytes(int v);
+bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, int v, const void *packed, int64_t k,
                                  int64_t rows, bool a_side);
-cudaError_t launch_tc_grouped(int mode, const TcProblem *probs, const TcItem *items,
+cudaError_t launch_tc_grouped(int mode, int v, const TcProblem *probs, const TcItem *items,
                               int64_t nitems, int sm_count, DeviceState *dstate,
                               int64_t wait_limit, cudaStream_t s);
 

@@ -89,12 +89,29 @@ struct GroupSource {
     }
 };
 
-// Grouped runs: 128 x 128 tiles of 64-byte rows in 96 KiB of stages, so that
-// two CTAs share an SM (two 256-column TMEM allocations, 2 x 99.6 KB of
-// shared memory): many small tiles are latency-bound, and a second CTA per
-// SM runs its own load / MMA / epilogue pipeline beside the first.
+// Grouped runs, three configurations the autotuner chooses between per size
+// class of a problem:
+//   V = 0: 128 x 128 tiles of 64-byte rows in 96 KiB of stages, so that two
+//          CTAs share an SM (two 256-column TMEM allocations, 2 x 99.6 KB of
+//          shared memory): many small tiles are latency-bound, and a second
+//          CTA per SM runs its own load / MMA / epilogue pipeline beside the
+//          first;
+//   V = 1: 128 x 256 tiles of 64-byte rows, 216 KiB of stages, one CTA per SM
+//          (the long-K configuration of one GEMM: half the operand re-reads
+//          per flop);
+//   V = 2: 128 x 128 tiles of 128-byte rows, 216 KiB of stages, one CTA per SM
+//          (twice the K per stage: fewer hand-offs per k).
+constexpr int kGroupedConfigs = 3;
+template <int MODE, int V>
+struct GroupedCfgV;
 template <int MODE>
-using GroupedCfg = Cfg<MODE, 64, 128, 96>;
+struct GroupedCfgV<MODE, 0> : Cfg<MODE, 64, 128, 96> { static constexpr int CTAS = 2; };
+template <int MODE>
+struct GroupedCfgV<MODE, 1> : Cfg<MODE, 64, 256, 216> { static constexpr int CTAS = 1; };
+template <int MODE>
+struct GroupedCfgV<MODE, 2> : Cfg<MODE, 128, 128, 216> { static constexpr int CTAS = 1; };
+template <int MODE>
+using GroupedCfg = GroupedCfgV<MODE, 0>;
 
 // Promoted accumulation for one GEMM: 128 x 256 tiles of 64-byte rows (the
 // long-K configuration of the plain kernel), 384 threads. The scaled FP16

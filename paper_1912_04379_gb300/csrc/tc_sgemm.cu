@@ -100,11 +100,11 @@ tc_promo_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     tc_body<MODE, CF::ROW_BYTES, SingleSource<CF::BN, CF::BK, 0>, CF>(src, dstate, limit_ns);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NUM_THREADS, 2)
+template <int MODE, int V>
+__global__ void __launch_bounds__(NUM_THREADS, GroupedCfgV<MODE, V>::CTAS)
 tc_grouped_kernel(const TcProblem *__restrict__ probs, const TcItem *__restrict__ items,
                   int64_t nitems, DeviceState *dstate, uint64_t limit_ns) {
-    using CF = GroupedCfg<MODE>;
+    using CF = GroupedCfgV<MODE, V>;
     GroupSource<CF::BN, CF::BK> src{probs, items, nitems};
     tc_body<MODE, CF::ROW_BYTES, GroupSource<CF::BN, CF::BK>, CF>(src, dstate, limit_ns);
 }
@@ -250,27 +250,40 @@ cudaError_t launch_promo_mode(const TcArgs &a, cudaStream_t s) {
     return launch_splitk_reduce(a.m, a.n, splits, a.part, a.alpha, a.beta, a.C, a.ldc, s);
 }
 
-template <int MODE>
+template <int MODE, int V>
 cudaError_t launch_grouped_mode(const TcProblem *probs, const TcItem *items, int64_t nitems,
                                 int sm_count, DeviceState *dstate, int64_t wait_limit,
                                 cudaStream_t s) {
-    using CF = GroupedCfg<MODE>;
+    using CF = GroupedCfgV<MODE, V>;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MODE>,
+        cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MODE, V>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
-    int grid = sm_count > 0 ? 2 * sm_count : 1;           // two CTAs per SM
+    int grid = sm_count > 0 ? CF::CTAS * sm_count : 1;    // persistent: CTAS per SM
     if (nitems < grid) grid = (int)nitems;
-    tc_grouped_kernel<MODE><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
+    tc_grouped_kernel<MODE, V><<<grid, NUM_THREADS, CF::SMEM_BYTES, s>>>(
         probs, items, nitems, dstate, (uint64_t)wait_limit * 1000ull);
     return cudaGetLastError();
+}
+
+template <int V>
+cudaError_t launch_grouped_v(int mode, const TcProblem *probs, const TcItem *items,
+                             int64_t nitems, int sm_count, DeviceState *dstate,
+                             int64_t wait_limit, cudaStream_t s) {
+    switch (mode) {
+        case 0: return launch_grouped_mode<0, V>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 1: return launch_grouped_mode<1, V>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 2: return launch_grouped_mode<2, V>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 3: return launch_grouped_mode<3, V>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -297,28 +310,36 @@ bool tc_make_operand_map(CUtensorMap *map, int mode, bool rb128, const void *pac
                     a_side ? BM : tc_tile_n(mode, rb128), bk, rb);
 }
 
-int tc_grouped_tile_n() { return GroupedCfg<1>::BN; }
-
-bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, const void *packed, int64_t k,
-                                 int64_t rows, bool a_side) {
-    constexpr int rb = GroupedCfg<1>::ROW_BYTES;
-    static_assert(GroupedCfg<0>::ROW_BYTES == rb && GroupedCfg<2>::ROW_BYTES == rb &&
-                  GroupedCfg<0>::BN == GroupedCfg<2>::BN, "one grouped layout for every split");
-    const bool tf32 = mode == 0;
-    return make_map(map, tf32 ? kFmtTF32 : kFmtBF16, packed, k, rows, split_kpad(mode, k),
-                    split_parts(mode),
-                    a_side ? BM : tc_grouped_tile_n(), rb / (tf32 ? 4 : 2), rb);
+// Tile width and row width of grouped configuration v (the same for every
+// split mode: the configurations differ in shape, not in terms).
+int tc_grouped_tile_n(int v) {
+    static_assert(GroupedCfgV<0, 0>::BN == GroupedCfgV<2, 0>::BN &&
+                  GroupedCfgV<0, 1>::BN == GroupedCfgV<2, 1>::BN &&
+                  GroupedCfgV<0, 2>::BN == GroupedCfgV<2, 2>::BN, "tile width by configuration");
+    return v == 1 ? GroupedCfgV<1, 1>::BN : v == 2 ? GroupedCfgV<1, 2>::BN : GroupedCfgV<1, 0>::BN;
+}
+int tc_grouped_row_bytes(int v) {
+    return v == 1 ? GroupedCfgV<1, 1>::ROW_BYTES : v == 2 ? GroupedCfgV<1, 2>::ROW_BYTES
+                                                         : GroupedCfgV<1, 0>::ROW_BYTES;
 }
 
-cudaError_t launch_tc_grouped(int mode, const TcProblem *probs, const TcItem *items,
+bool tc_make_grouped_operand_map(CUtensorMap *map, int mode, int v, const void *packed,
+                                 int64_t k, int64_t rows, bool a_side) {
+    const int rb = tc_grouped_row_bytes(v);
+    const bool tf32 = mode == 0;
+    return make_map(map, tf32 ? kFmtTF32 : kFmtBF16, packed, k, rows, split_kpad(mode, k),
+                    split_parts(mode), a_side ? BM : tc_grouped_tile_n(v), rb / (tf32 ? 4 : 2),
+                    rb);
+}
+
+cudaError_t launch_tc_grouped(int mode, int v, const TcProblem *probs, const TcItem *items,
                               int64_t nitems, int sm_count, DeviceState *dstate,
                               int64_t wait_limit, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    switch (mode) {
-        case 0: return launch_grouped_mode<0>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 1: return launch_grouped_mode<1>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 2: return launch_grouped_mode<2>(probs, items, nitems, sm_count, dstate, wait_limit, s);
-        case 3: return launch_grouped_mode<3>(probs, items, nitems, sm_count, dstate, wait_limit, s);
+    switch (v) {
+        case 0: return launch_grouped_v<0>(mode, probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 1: return launch_grouped_v<1>(mode, probs, items, nitems, sm_count, dstate, wait_limit, s);
+        case 2: return launch_grouped_v<2>(mode, probs, items, nitems, sm_count, dstate, wait_limit, s);
         default: return cudaErrorInvalidValue;
     }
 }
