@@ -367,6 +367,66 @@ GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 GB_API int gb_set_promotion(gb_handle_t h, int64_t k_chunk);
 GB_API int gb_get_promotion(gb_handle_t h, int64_t *k_chunk);
 
+/* ---------------------------------------------------------------------
+ * Autotuning and its cache (the paper chose its block sizes
+ * experimentally, Sec. 3; here the library measures its own choices).
+ *
+ * gb_tune_grouped runs the grouped autotuner now: for each size class of a
+ * problem (floor(log2) of the geometric mean of M, N, K, 8 classes from 8
+ * to 1024) it times synthetic groups under SIMT with 64 x 64 tiles, SIMT
+ * with 128 x 128 tiles, and the tensor cores in each grouped kernel
+ * configuration (0: 128 x 128 tiles, 64-byte rows, two CTAs per SM; 1:
+ * 128 x 256 tiles, 64-byte rows, one CTA per SM; 2: 128 x 128 tiles,
+ * 128-byte rows, one CTA per SM; the stage count follows from each), keeps
+ * the fastest per class, then checks the result on one mixed group. AUTO
+ * plans run it on first use if the handle has no result yet; split-algorithm
+ * plans use its configurations when present. Synchronises; allocates and
+ * frees scratch memory.
+ *
+ * gb_tune_sgemm times gb_sgemm's tensor-core kernel for this algorithm and
+ * shape with 64-byte and with 128-byte shared-memory rows (scratch inputs of
+ * that shape) and records the faster for the shape's bucket (the split mode
+ * and floor(log2) of M, N and K); later gb_sgemm calls of that bucket use it
+ * instead of the built-in rule (the environment variable
+ * GB_SGEMM_TC_ROW_BYTES still overrides both). Synchronises; allocates and
+ * frees scratch memory. GB_ERR_UNSUPPORTED for SIMT or when the table is
+ * full.
+ *
+ * The results form a gb_tuning_t, keyed by the GPU's name, its SM count,
+ * the CUDA runtime version and the library version. gb_tuning_write and
+ * gb_tuning_read store and load one as a small JSON file (host only, no
+ * device needed; GB_ERR_ARG for a file that is missing or malformed).
+ * gb_get_tuning / gb_set_tuning copy a record out of or into a handle;
+ * gb_set_tuning returns GB_ERR_ARG when the record's key does not match the
+ * handle's device. When the environment variable GB_SGEMM_TUNING names a
+ * file, gb_create loads it if its key matches, and every tuning call that
+ * changes the handle's record writes it back there.
+ * ------------------------------------------------------------------- */
+#define GB_TUNING_MAX_GEMM 64
+typedef struct {
+    int mode;                  /* split mode: 0 TF32X3, 1 BF16X3, 2 BF16X6, 3 BF16X9, 4 FP16X3 */
+    int log2_m, log2_n, log2_k;
+    int row_bytes;             /* 64 or 128 */
+} gb_tuning_gemm_t;
+typedef struct {
+    char gpu_name[96];
+    int sm_count;
+    int cuda_runtime_version;
+    int library_version;
+    int grouped_valid;         /* 1 when grouped_route holds a tuned result */
+    int grouped_route[8];      /* per size class: 0 SIMT 64x64, 1 SIMT 128x128, 2 + v tensor cores, configuration v */
+    int n_gemm;                /* entries of gemm[] in use */
+    gb_tuning_gemm_t gemm[GB_TUNING_MAX_GEMM];
+} gb_tuning_t;
+
+GB_API int gb_tune_grouped(gb_handle_t h);
+GB_API int gb_tune_sgemm(gb_handle_t h, gb_algo_t algo, char transa, char transb, int64_t m,
+                         int64_t n, int64_t k);
+GB_API int gb_get_tuning(gb_handle_t h, gb_tuning_t *t);
+GB_API int gb_set_tuning(gb_handle_t h, const gb_tuning_t *t);
+GB_API int gb_tuning_write(const gb_tuning_t *t, const char *path);
+GB_API int gb_tuning_read(gb_tuning_t *t, const char *path);
+
 /* Device workspace bytes gb_sgemm_host needs for this problem. */
 GB_API int gb_sgemm_host_workspace_size(gb_algo_t algo, char transa, char transb, int64_t m,
                                         int64_t n, int64_t k, size_t *bytes);

@@ -52,6 +52,20 @@ class MlpDesc(ctypes.Structure):
 
 ACTIVATIONS = {"identity": 0, "tanh": 1}
 
+TUNING_MAX_GEMM = 64
+
+
+class TuningGemm(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("log2_m", c_int), ("log2_n", c_int), ("log2_k", c_int),
+                ("row_bytes", c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("gpu_name", ctypes.c_char * 96), ("sm_count", c_int),
+                ("cuda_runtime_version", c_int), ("library_version", c_int),
+                ("grouped_valid", c_int), ("grouped_route", c_int * 8), ("n_gemm", c_int),
+                ("gemm", TuningGemm * TUNING_MAX_GEMM)]
+
 SIGNATURES = {
     "gb_version": ([], c_int),
     "gb_status_string": ([c_int], ctypes.c_char_p),
@@ -85,6 +99,12 @@ SIGNATURES = {
     "gb_set_wait_limit": ([c_vp, c_i64], c_int),
     "gb_set_fused_split": ([c_vp, c_int], c_int),
     "gb_set_promotion": ([c_vp, c_i64], c_int),
+    "gb_tune_grouped": ([c_vp], c_int),
+    "gb_tune_sgemm": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64], c_int),
+    "gb_get_tuning": ([c_vp, ctypes.POINTER(Tuning)], c_int),
+    "gb_set_tuning": ([c_vp, ctypes.POINTER(Tuning)], c_int),
+    "gb_tuning_write": ([ctypes.POINTER(Tuning), ctypes.c_char_p], c_int),
+    "gb_tuning_read": ([ctypes.POINTER(Tuning), ctypes.c_char_p], c_int),
     "gb_get_promotion": ([c_vp, ctypes.POINTER(c_i64)], c_int),
     "gb_mlp_workspace_size": ([c_int, ctypes.POINTER(MlpDesc), c_int, ctypes.POINTER(c_size)],
                               c_int),

@@ -112,6 +112,24 @@ class Handle:
         _lib.check("gb_get_promotion", self.lib.gb_get_promotion(self.h, ctypes.byref(v)))
         return v.value
 
+    def tune_grouped(self):
+        """Run the grouped autotuner now (synchronises)."""
+        _lib.check("gb_tune_grouped", self.lib.gb_tune_grouped(self.h))
+
+    def tune_sgemm(self, algo, transa, transb, m, n, k):
+        """Measure the tensor-core row width for this shape bucket (synchronises)."""
+        _lib.check("gb_tune_sgemm", self.lib.gb_tune_sgemm(
+            self.h, _lib.ALGOS[algo], transa.encode(), transb.encode(), m, n, k))
+
+    def tuning(self):
+        """The handle's tuning record (a ctypes gb_tuning_t)."""
+        t = _lib.Tuning()
+        _lib.check("gb_get_tuning", self.lib.gb_get_tuning(self.h, ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, t):
+        _lib.check("gb_set_tuning", self.lib.gb_set_tuning(self.h, ctypes.byref(t)))
+
     def set_wait_limit(self, microseconds: int):
         _lib.check("gb_set_wait_limit", self.lib.gb_set_wait_limit(self.h, int(microseconds)))
 

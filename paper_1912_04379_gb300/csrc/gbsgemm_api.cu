@@ -146,6 +146,7 @@ int compute_packed(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, flo
     t.dstate = h->dstate;
     t.wait_limit = h->wait_limit;
     t.sm_count = h->sm_count;
+    t.row_bytes = h->rb_override ? h->rb_override : tuned_row_bytes(h, mode, m, n, k);
     if (epi) t.epi = *epi;
     if (mode == 4) {
         t.amax = packed_max(const_cast<void *>(Ap), mode, true, m, k);
@@ -371,6 +372,8 @@ GB_API int gb_create(gb_handle_t *out) {
     h->cc_minor = prop.minor;
     h->smem_optin = prop.sharedMemPerBlockOptin;
     h->wait_limit = 2000000;
+    strncpy(h->gpu_name, prop.name, sizeof(h->gpu_name) - 1);
+    if (cudaRuntimeGetVersion(&h->cuda_runtime_version) != cudaSuccess) h->cuda_runtime_version = 0;
     if (cudaMalloc(&h->dstate, sizeof(DeviceState)) != cudaSuccess ||
         cudaMemset(h->dstate, 0, sizeof(DeviceState)) != cudaSuccess) {
         delete h;
@@ -384,6 +387,7 @@ GB_API int gb_create(gb_handle_t *out) {
         delete h;
         return GB_ERR_CUDA;
     }
+    gb::tuning_autoload(h);
     *out = h;
     return GB_OK;
 }

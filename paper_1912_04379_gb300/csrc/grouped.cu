@@ -676,11 +676,26 @@ int autotune(gb_handle_t h, int dev) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
-    if (rc == GB_OK) h->grouped_tuned = true;
+    if (rc == GB_OK) {
+        h->grouped_tuned = true;
+        gb::tuning_autosave(h);
+    }
     return rc;
 }
 
 }  // namespace
+
+int gb::grouped_autotune(gb_handle_t h) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    if (dev != h->device) return GB_ERR_HANDLE;
+    return autotune(h, dev);
+}
+
+extern "C" GB_API int gb_tune_grouped(gb_handle_t h) {
+    if (!h || h->magic != gb::kHandleMagic) return GB_ERR_HANDLE;
+    return gb::grouped_autotune(h);
+}
 
 extern "C" {
 

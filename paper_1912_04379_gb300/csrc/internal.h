@@ -43,6 +43,13 @@ struct gb_handle_s {
     // grouped configuration v.
     bool grouped_tuned;
     int grouped_choice[8];
+    // the key of the tuning record, and the one-GEMM row widths measured per
+    // shape bucket (gb_tune_sgemm); rb_override forces a width while tuning
+    char gpu_name[96];
+    int cuda_runtime_version;
+    int n_gemm_rb;
+    gb_tuning_gemm_t gemm_rb[GB_TUNING_MAX_GEMM];
+    int rb_override;
     bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
     int64_t promote_k;          // promoted accumulation: chunk length in K (0 = off)
     // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
@@ -136,6 +143,7 @@ struct TcArgs {
     int promote_kb;             // > 0: promoted accumulation, k-blocks per chunk
     const uint32_t *amax;       // mode 4: largest |op(A)| per row (FP32 bits)
     const uint32_t *bmax;       // mode 4: largest |op(B)| per column
+    int row_bytes;              // 64 or 128: the tuned row width; 0: the built-in rule
 };
 // cudaErrorNotSupported: an epilogue operation with another mode or split-K,
 // or with promoted accumulation.
@@ -253,6 +261,13 @@ cudaError_t pack_operand_rows(int mode, bool a_side, bool trans, int64_t rows, i
                               int64_t row0, cudaStream_t s);
 // Bytes of one packed operand (gb_sgemm_pack_size's value).
 size_t packed_operand_bytes(int mode, bool a_side, int64_t mn, int64_t k);
+
+// Tuning (tuning.cu, grouped.cu): the row width recorded for a call's shape
+// bucket (0: none), the grouped autotuner, and the GB_SGEMM_TUNING cache.
+int tuned_row_bytes(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k);
+int grouped_autotune(gb_handle_t h);
+void tuning_autosave(gb_handle_t h);
+void tuning_autoload(gb_handle_t h);
 
 // AUTO's choice for a given K, and the split mode of an algorithm (-1: SIMT).
 gb_algo_t resolve_algo(gb_algo_t algo, int64_t k);

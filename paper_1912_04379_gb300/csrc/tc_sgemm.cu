@@ -344,6 +344,18 @@ cudaError_t launch_tc_grouped(int mode, int v, const TcProblem *probs, const TcI
     }
 }
 
+namespace {
+// The row width forced by GB_SGEMM_TC_ROW_BYTES (64 or 128), read once; 0 if none.
+int forced_row_bytes() {
+    static const int forced = [] {
+        const char *e = getenv("GB_SGEMM_TC_ROW_BYTES");
+        const int v = e ? atoi(e) : 0;
+        return (v == 64 || v == 128) ? v : 0;
+    }();
+    return forced;
+}
+}  // namespace
+
 // Shared-memory row width of a k-block for one GEMM. 64-byte rows (64-byte
 // swizzle; 2 terms: four 48 KiB stages; 3 terms: three 72 KiB stages with
 // 256-column tiles) measured faster than 128-byte rows (two 96 KiB stages;
@@ -358,12 +370,7 @@ cudaError_t launch_tc_grouped(int mode, int v, const TcProblem *probs, const TcI
 // GB_SGEMM_TC_ROW_BYTES = 64 or 128 forces one of them.
 bool tc_rb128(int mode, int64_t m, int64_t n, int64_t k) {
     if (mode == 4) return false;       // the scaled FP16 split runs 64-byte rows only
-    static const int forced = [] {
-        const char *e = getenv("GB_SGEMM_TC_ROW_BYTES");
-        const int v = e ? atoi(e) : 0;
-        return (v == 64 || v == 128) ? v : 0;
-    }();
-    if (forced) return forced == 128;
+    if (const int forced = forced_row_bytes()) return forced == 128;
     if (k <= 128) return true;
     if (k > 2048 || mode <= 1) return false;
     return ((m + BM - 1) / BM) * ((n + 255) / 256) < 1024;
@@ -383,7 +390,9 @@ cudaError_t launch_tc_sgemm(const TcArgs &a, cudaStream_t s) {
             default: return cudaErrorInvalidValue;
         }
     }
-    const bool rb128 = tc_rb128(a.mode, a.m, a.n, a.k);
+    // the environment's width, else the tuned one, else the rule
+    const bool rb128 = (forced_row_bytes() || a.row_bytes == 0) ? tc_rb128(a.mode, a.m, a.n, a.k)
+                                                                : a.row_bytes == 128;
     if (a.epi.kind != 0) {
         // fused elementwise operations: BF16 x 2 terms and x 3 terms (6 products)
         const int key = a.mode * 10 + a.epi.kind;
