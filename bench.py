@@ -533,6 +533,31 @@ def bench_grouped(gb, h, dev, stream, reps=10):
                                   "accuracy": accuracy(plan)}
         plan.close()
 
+    # the tuner's routing per size class (0 / 1: SIMT tiles, 2 + v: tensor
+    # cores in grouped configuration v), and BF16X6 plans with every class
+    # forced to each configuration for comparison
+    t = h.tuning()
+    out["tuned_routes"] = list(t.grouped_route) if t.grouped_valid else None
+    fixed = {}
+    for v in range(3):
+        f = h.tuning()
+        f.grouped_valid = 1
+        for c in range(8):
+            f.grouped_route[c] = 2 + v
+        h.set_tuning(f)
+        plan = gb.GroupedPlan(tuples, algo="bf16x6", handle=h)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.run(stream=s)
+        torch.cuda.synchronize()
+        fixed[f"config{v}"] = timed(g.replay, reps)
+        plan.close()
+    h.set_tuning(t)
+    out["bf16x6_fixed_config_ms"] = fixed
+
     def one(t, strm=None):
         ta, tb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc = t
         gb.sgemm_raw(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, algo="simt",

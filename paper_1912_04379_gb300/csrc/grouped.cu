@@ -603,8 +603,10 @@ int time_choice(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps
 // part of a mixed group share the SMs (a SIMT CTA does not fit beside two
 // tensor-core CTAs), so the per-class choice is then checked on one mixed
 // synthetic group (equal problem counts per class, as in a log-uniform
-// group): if routing its SIMT classes to the tensor cores too is faster,
-// they are. Runs once per handle, on a private stream, with scratch memory
+// group) against routing every class to the tensor cores, in the classes'
+// configurations or all in configuration 0 (a class timed alone favours
+// the one-CTA-per-SM configurations, which give up parallelism in a mixed
+// group): the fastest of the three routings is kept. Runs once per handle, on a private stream, with scratch memory
 // freed afterwards; the result is stored in the handle.
 int autotune(gb_handle_t h, int dev) {
     cudaStream_t s;
@@ -639,12 +641,13 @@ int autotune(gb_handle_t h, int dev) {
         h->grouped_choice[c] = best_ch;
     }
     // The mixed check: 16 problems of each class's middle size (4 of the
-    // largest), about 0.24 GB of scratch.
-    bool any_simt = false;
-    for (int c = 0; c < kClasses; ++c) any_simt |= h->grouped_choice[c] < 2;
+    // largest), about 0.24 GB of scratch. Needed unless every class already
+    // chose the tensor cores in configuration 0.
+    bool any_other = false;
+    for (int c = 0; c < kClasses; ++c) any_other |= h->grouped_choice[c] != 2;
     // a mixed plan runs its two parts concurrently only on the side stream
-    if (rc == GB_OK && any_simt && !ensure_side(h)) rc = GB_ERR_CUDA;
-    if (rc == GB_OK && any_simt) {
+    if (rc == GB_OK && any_other && !ensure_side(h)) rc = GB_ERR_CUDA;
+    if (rc == GB_OK && any_other) {
         std::vector<gb_gemm_problem_t> mix;
         std::vector<float *> bufs;
         for (int c = 0; c < kClasses && rc == GB_OK; ++c) {
@@ -659,16 +662,24 @@ int autotune(gb_handle_t h, int dev) {
             mix.insert(mix.end(), ps.begin(), ps.end());
         }
         if (rc == GB_OK) {
-            int tuned[kClasses], all_tc[kClasses];
+            // three routings of the mixed group: as tuned per class; every
+            // class on the tensor cores in its tuned configuration (SIMT
+            // classes in configuration 0); every class in configuration 0
+            int cand[3][kClasses];
             for (int c = 0; c < kClasses; ++c) {
-                tuned[c] = h->grouped_choice[c];
-                all_tc[c] = tuned[c] >= 2 ? tuned[c] : 2;   // SIMT classes to configuration 0
+                cand[0][c] = h->grouped_choice[c];
+                cand[1][c] = cand[0][c] >= 2 ? cand[0][c] : 2;
+                cand[2][c] = 2;
             }
-            float t_tuned = 1e30f, t_tc = 1e30f;
-            rc = time_choice(h, dev, mix, tuned, ws, s, e0, e1, &t_tuned);
-            if (rc == GB_OK) rc = time_choice(h, dev, mix, all_tc, ws, s, e0, e1, &t_tc);
-            if (rc == GB_OK && t_tc < t_tuned)
-                for (int c = 0; c < kClasses; ++c) h->grouped_choice[c] = all_tc[c];
+            float best_t = 1e30f;
+            int best = 0;
+            for (int i = 0; i < 3 && rc == GB_OK; ++i) {
+                float t = 1e30f;
+                rc = time_choice(h, dev, mix, cand[i], ws, s, e0, e1, &t);
+                if (t < best_t) { best_t = t; best = i; }
+            }
+            if (rc == GB_OK)
+                for (int c = 0; c < kClasses; ++c) h->grouped_choice[c] = cand[best][c];
         }
         for (float *b : bufs) cudaFree(b);
     }
