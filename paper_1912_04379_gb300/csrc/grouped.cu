@@ -640,26 +640,43 @@ int autotune(gb_handle_t h, int dev) {
         cudaFree(buf);
         h->grouped_choice[c] = best_ch;
     }
-    // The mixed check: 16 problems of each class's middle size (4 of the
-    // largest), about 0.24 GB of scratch. Needed unless every class already
-    // chose the tensor cores in configuration 0.
+    // The mixed check: 512 uneven problems with M, N and K each drawn
+    // log-uniformly from [8, 1024] (a fixed xorshift sequence), as grouped
+    // workloads of uneven sizes come, in about 0.5 GB of scratch. Needed
+    // unless every class already chose the tensor cores in configuration 0.
     bool any_other = false;
     for (int c = 0; c < kClasses; ++c) any_other |= h->grouped_choice[c] != 2;
     // a mixed plan runs its two parts concurrently only on the side stream
     if (rc == GB_OK && any_other && !ensure_side(h)) rc = GB_ERR_CUDA;
     if (rc == GB_OK && any_other) {
-        std::vector<gb_gemm_problem_t> mix;
+        std::vector<gb_gemm_problem_t> mix(512);
         std::vector<float *> bufs;
-        for (int c = 0; c < kClasses && rc == GB_OK; ++c) {
-            const int64_t d = (int64_t)llround(pow(2.0, c + 3.5));
-            const int64_t g = c == kClasses - 1 ? 4 : 16;
-            float *buf = nullptr;
-            const size_t bytes = (size_t)(3 * d * d) * g * sizeof(float);
-            if (cudaMalloc(&buf, bytes) != cudaSuccess) { rc = GB_ERR_CUDA; break; }
+        uint64_t x = 0x9e3779b97f4a7c15ull;
+        auto dim = [&]() {
+            x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+            const double u = (double)(x >> 11) / 9007199254740992.0;   // [0, 1)
+            return (int64_t)llround(pow(2.0, 3.0 + 7.0 * u));
+        };
+        size_t total = 0;
+        for (gb_gemm_problem_t &p : mix) {
+            p.m = dim(); p.n = dim(); p.k = dim();
+            total += (size_t)(p.m * p.k + p.k * p.n + p.m * p.n);
+        }
+        float *buf = nullptr;
+        if (cudaMalloc(&buf, total * sizeof(float)) != cudaSuccess) rc = GB_ERR_CUDA;
+        else {
             bufs.push_back(buf);
-            cudaMemsetAsync(buf, 0x3e, bytes, s);
-            const std::vector<gb_gemm_problem_t> ps = synthetic(buf, g, d, (int64_t)mix.size());
-            mix.insert(mix.end(), ps.begin(), ps.end());
+            cudaMemsetAsync(buf, 0x3e, total * sizeof(float), s);
+            size_t off = 0;
+            for (size_t i = 0; i < mix.size(); ++i) {
+                gb_gemm_problem_t &p = mix[i];
+                p.transa = (i & 1) ? 'T' : 'N';
+                p.transb = (i & 2) ? 'T' : 'N';
+                p.alpha = 1.f; p.beta = 0.f;
+                p.A = buf + off; p.lda = p.transa == 'T' ? p.k : p.m; off += (size_t)(p.m * p.k);
+                p.B = buf + off; p.ldb = p.transb == 'T' ? p.n : p.k; off += (size_t)(p.k * p.n);
+                p.C = buf + off; p.ldc = p.m; off += (size_t)(p.m * p.n);
+            }
         }
         if (rc == GB_OK) {
             // three routings of the mixed group: as tuned per class; every
