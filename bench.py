@@ -1176,10 +1176,10 @@ def run_ours(args, rank, world, local_rank):
 
     def resolved(algo, k):
         """The algorithm a row ran: AUTO resolves by K as the library does
-        (BF16X3 for K >= 1024, BF16X6 for 4 <= K < 1024, else SIMT)."""
+        (BF16X3 for K >= 1024, BF16X6 for 9 <= K < 1024, else SIMT)."""
         if algo != "auto":
             return algo
-        return "bf16x3" if k >= 1024 else "bf16x6" if k >= 4 else "simt"
+        return "bf16x3" if k >= 1024 else "bf16x6" if k >= 9 else "simt"
 
     if configs and "error" not in configs:
         for sect, kdim in (("plain_384", lambda name: 384), ("sweep", lambda name: int(name.split("_")[0]))):

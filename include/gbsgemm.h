@@ -87,15 +87,28 @@ enum {
  *                       K). Grouped runs and gb_ssyrk's triangle kernel take
  *                       SPLIT_TF32X3 for it.
  *  GB_ALGO_AUTO         the library picks: SPLIT_BF16X3 when K >= 1024,
- *                       SPLIT_BF16X6 when 4 <= K < 1024, else SIMT.
+ *                       SPLIT_BF16X6 when 9 <= K < 1024, else SIMT.
  * Error per element, D = |alpha||op(A)||op(B)| + |beta||C|, u = 2^-24:
  *  SIMT       |C - C_exact| <= 2*max(K,1)*u*D
- *  split x    (2*max(K,1)*u + e_x)*D with e_x the dropped cross terms:
- *             TF32X3 and FP16X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24 (x 1.01),
- *             BF16X9 2^-24 (nothing is dropped, but the tensor core's FP32
- *             accumulation is not round-to-nearest: at K = 1 the error
- *             was measured at 1.34 x 2*K*u*D),
- *  FP16X3     (2*max(K,1)*u + 3*2^-22)*D + |alpha|*2^-34*(2^(la_i - 3)*sum_p |b_pj|
+ *  split x    (2*max(K,1)*u + e_x + t_x)*D, with e_x the dropped cross terms
+ *             (TF32X3 and FP16X3 3*2^-22, BF16X3 3*2^-16, BF16X6 2*2^-24
+ *             x 1.01, BF16X9 0) and t_x the tensor cores' accumulation.
+ *             The PTX ISA leaves that accumulation's rounding unspecified
+ *             (it is not round-to-nearest: BF16X9, whose products are all
+ *             exact, measured 1.34 x 2*K*u*D at K = 1). The library assumes
+ *             a model: every MMA instruction adds its 16 exact products (8
+ *             for TF32) to the running sum with an error of at most one FP32
+ *             ulp (2u relative). An element then sees P*ceil(K/16) such steps
+ *             (P products per pair of terms: 3, 6 or 9; ceil(K/8) for TF32),
+ *             plus one rounding in the alpha/beta epilogue, so
+ *             (2*P*ceil(K/16) + 2)*u*D bounds accumulation and epilogue
+ *             together. Against the plain bound 2*K*u*D this leaves room for
+ *             the dropped terms once K >= 16 (TF32X3, FP16X3), 1024 (BF16X3,
+ *             its dropped terms within half the bound), 9 (BF16X6) or 10
+ *             (BF16X9); below that the model gives t_x = (2*P*ceil(K/16) +
+ *             2 - 2*K)*u (BF16X9 at most 18u). AUTO and the grouped
+ *             planner use a split only above its threshold.
+ *  FP16X3     additionally |alpha|*2^-34*(2^(la_i - 3)*sum_p |b_pj|
  *             + 2^(lb_J - 14)*sum_p |a_ip|), la_i = floor(log2 max_p |a_ip|) and
  *             lb_J = floor(log2 of the largest |b_pl| over the block of 256
  *             columns l holding j) (finite entries; a = op(A), b = op(B)):
@@ -107,11 +120,8 @@ enum {
  *             error 0.0004 of the plain bound), but with few widely spread
  *             entries (K = 8, the same magnitudes) it can exceed the plain
  *             bound many times over. AUTO never picks FP16X3.
- *  so a split meets the plain SIMT bound once K >= 16 (TF32X3), 1024
- *  (BF16X3), 4 (BF16X6) or 2 (BF16X9, measured: at most 0.73 x the bound
- *  at K = 2); AUTO only picks an algorithm above its threshold. The BF16 three-term split is exact for
- *  |a| >= 2^-110; smaller nonzero magnitudes lose bits below the BF16
- *  subnormal range. */
+ *  The BF16 three-term split is exact for |a| >= 2^-110; smaller nonzero
+ *  magnitudes lose bits below the BF16 subnormal range. */
 typedef enum {
     GB_ALGO_AUTO = -1,
     GB_ALGO_SIMT = 0,
@@ -277,10 +287,10 @@ typedef struct {
  *                K >= 1024 (if those fill at least one round of the
  *                persistent grid, else they join the next), else
  *                SPLIT_BF16X6;
- *  a split algo  the preferred split for every problem with K >= 4; a
+ *  a split algo  the preferred split for every problem with K >= 9; a
  *                problem whose K is below that split's threshold (see
  *                gb_algo_t) takes SPLIT_BF16X6 instead.
- * Problems with K < 4, alpha = 0 or K = 0 always run on the CUDA cores.
+ * Problems with K < 9, alpha = 0 or K = 0 always run on the CUDA cores.
  * The tensor-core problems of one split run in one persistent launch. */
 GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
                                  const gb_gemm_problem_t *host_problems,
@@ -517,7 +527,7 @@ GB_API int gb_ssyrk_workspace_size(gb_algo_t algo, char uplo, char trans, int64_
  * lda >= max(1, k)) for 'T' or 'C'; ldc >= max(1, n). C is not read when
  * beta = 0; A is not read when alpha = 0 or k = 0. Negative returns are
  * BLAS argument positions (1 uplo, 2 trans, 3 n, 4 k, 7 lda, 10 ldc).
- * With a split algorithm (AUTO: K >= 4) op(A) is split and packed once into
+ * With a split algorithm (AUTO: K >= 9) op(A) is split and packed once into
  * the workspace and the whole triangle runs in one tensor-core launch (the
  * algorithm's error bound per element, as for gb_sgemm). With SIMT, or when
  * alpha = 0 or K = 0, it recurses by halving: each level's off-diagonal

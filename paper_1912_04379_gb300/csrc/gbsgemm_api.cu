@@ -88,13 +88,15 @@ int gb::split_mode(gb_algo_t algo) {
 
 // AUTO picks the fastest algorithm whose worst-case error stays within the
 // FP32 bound 2*K*u*D for this K. Each split drops a fixed relative term per
-// product (BF16 x 2: 3*2^-16, BF16 x 3: 2*2^-24); requiring it to use at
-// most half of 2*K*u gives K >= 1024 for BF16 x 2 and K >= 4 for BF16 x 3
-// (which is also faster than TF32 x 2 at the same accuracy class).
+// product (BF16 x 2: 3*2^-16, BF16 x 3: 2*2^-24) and the tensor cores'
+// accumulation adds up to one ulp per MMA instruction; requiring the dropped
+// terms to use at most half of 2*K*u gives K >= 1024 for BF16 x 2, and the
+// accumulation model K >= 9 for BF16 x 3 (which is also faster than TF32 x 2
+// at the same accuracy class).
 gb_algo_t gb::resolve_algo(gb_algo_t algo, int64_t k) {
     if (algo != GB_ALGO_AUTO) return algo;
     if (k >= 1024) return GB_ALGO_SPLIT_BF16X3;
-    if (k >= 4) return GB_ALGO_SPLIT_BF16X6;
+    if (k >= kMinKBf16x6) return GB_ALGO_SPLIT_BF16X6;
     return GB_ALGO_SIMT;
 }
 

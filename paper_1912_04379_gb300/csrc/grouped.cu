@@ -261,17 +261,17 @@ constexpr int kPlanMagic = 0x47525031;
 constexpr int kClasses = 8;
 constexpr int kPrefAuto = -1;
 
-// Split mode of one tensor-core problem (K >= 4): the preferred mode when
-// its fixed per-product error leaves the FP32 bound 2*K*u*D room at this K
-// (TF32 x 2 terms from K >= 16, BF16 x 2 terms from K >= 1024), else BF16 x
-// 3 terms with 6 products, which holds from K >= 4. All 9 products (mode 3)
-// hold at every K. AUTO takes the cheapest mode that holds: BF16 x 2 terms
-// at K >= 1024, else BF16 x 3 terms.
+// Split mode of one tensor-core problem (K >= kMinKBf16x6): the preferred
+// mode when it meets the FP32 bound 2*K*u*D at this K (TF32 x 2 terms from
+// K >= 16, BF16 x 2 terms from K >= 1024, all 9 BF16 products from K >= 10),
+// else BF16 x 3 terms with 6 products, which holds from K >= 9. AUTO takes
+// the cheapest mode that holds: BF16 x 2 terms at K >= 1024, else BF16 x 3
+// terms.
 int tc_mode_for(int pref, int64_t k) {
     switch (pref) {
         case 0: return k >= 16 ? 0 : 2;
         case 2: return 2;
-        case 3: return 3;
+        case 3: return k >= gb::kMinKBf16x9 ? 3 : 2;
         default: return k >= 1024 ? 1 : 2;   // kPrefAuto and BF16 x 2 terms
     }
 }
@@ -321,7 +321,7 @@ int build_plan(gb_handle_t h, int dev, const std::vector<gb_gemm_problem_t> &ps,
     std::vector<TcPending> tcs;
     size_t packed_bytes = 0;
     auto route_choice = [&](const gb_gemm_problem_t &p, bool scale_only) {
-        return (scale_only || p.k < 4) ? (p.m < 96 || p.n < 96 ? 0 : 1)
+        return (scale_only || p.k < gb::kMinKBf16x6) ? (p.m < 96 || p.n < 96 ? 0 : 1)
                                        : choice[size_class(p.m, p.n, p.k)];
     };
     // 0 / 1: SIMT tiles, 2: tensor cores (configuration route_choice - 2)
@@ -766,7 +766,7 @@ GB_API int gb_sgemm_grouped_plan(gb_handle_t h, gb_algo_t algo, int64_t count,
         for (int c = 0; c < kClasses; ++c) choice[c] = h->grouped_choice[c];
     } else {
         // SIMT: 64x64 tiles for the three smallest classes, else 128x128;
-        // a split algorithm: every problem with K >= 4 on the tensor cores,
+        // a split algorithm: every problem with K >= 9 on the tensor cores,
         // in the configuration the tuner chose for its class if the handle
         // has tuned (or loaded) one, else configuration 0
         for (int c = 0; c < kClasses; ++c)

@@ -69,6 +69,15 @@ struct gb_handle_s {
 namespace gb {
 
 constexpr int kHandleMagic = 0x6b5e3a21;
+// Smallest K at which each split meets the plain FP32 bound 2*K*u*D under the
+// tensor-core accumulation model (each MMA instruction, 16 exact products or
+// 8 for TF32 plus the running sum, errs by at most one FP32 ulp; derivation in
+// gb_algo_t's comment in include/gbsgemm.h): BF16 x 3 terms with 6 products
+// from K = 9, with all 9 products from K = 10, TF32 x 2 from K = 16 (its
+// dropped terms), BF16 x 2 from K = 1024 (its dropped terms, using at most
+// half the bound).
+constexpr int64_t kMinKBf16x6 = 9;
+constexpr int64_t kMinKBf16x9 = 10;
 constexpr int kPipeStreams = 6;
 constexpr int kPipeEvents = 56;   // 8 for the column-block pipeline, 48 for the 2-D one
 void destroy_pipe(gb_handle_t h);     // releases gb_sgemm_host's streams and events

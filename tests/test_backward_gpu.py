@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from _gpu import SPLIT_EXTRA, STANDARD_BOUND_MIN_K, torch_gpu
+from _gpu import STANDARD_BOUND_MIN_K, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
@@ -18,7 +18,7 @@ ALGOS = ("simt", "tf32x3", "bf16x3", "bf16x6", "fp16x3")
 
 
 def _check(got, want, D, kred, algo, what):
-    for extra, must in ((SPLIT_EXTRA[algo], True),
+    for extra, must in ((split_extra(algo, kred), True),
                         (0.0, kred >= STANDARD_BOUND_MIN_K[algo])):
         if not must:
             continue

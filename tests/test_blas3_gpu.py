@@ -20,7 +20,7 @@ import pytest
 
 import workloads as wl
 from oracle import blas3
-from _gpu import SPLIT_EXTRA, torch_gpu
+from _gpu import auto_algo, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
@@ -30,7 +30,7 @@ COMBOS = list(itertools.product("LR", "LU", "NT", "NU"))
 def _resolve(algo, k):
     if algo != "auto":
         return algo
-    return "bf16x3" if k >= 1024 else ("bf16x6" if k >= 4 else "simt")
+    return auto_algo(k)
 
 
 def _dev(arr):
@@ -69,7 +69,7 @@ def test_ssyrk_against_oracle(algo, n, k, uplo, trans):
     got = gb.to_fortran(Cd)
     C64, D = blas3.ssyrk(uplo, trans, n, k, alpha, A, A.shape[0], beta, C, C.shape[0])
     mask = ~np.isnan(C64)
-    bound = (2 * max(k, 1) * U + SPLIT_EXTRA[_resolve(algo, k)]) * D
+    bound = (2 * max(k, 1) * U + split_extra(_resolve(algo, k), k)) * D
     err = np.abs(got[:n, :n] - C64)
     assert np.all(err[mask] <= bound[mask]), float(np.max(err[mask] / bound[mask]))
     assert np.all(np.isnan(got[:n, :n][~mask]))            # other triangle untouched
@@ -92,7 +92,7 @@ def test_ssyrk_tensor_core_algorithms(algo, n, k, uplo, trans):
     got = gb.to_fortran(Cd)
     C64, D = blas3.ssyrk(uplo, trans, n, k, -0.75, A, A.shape[0], 1.5, C, C.shape[0])
     mask = ~np.isnan(C64)
-    bound = (2 * max(k, 1) * U + SPLIT_EXTRA[algo]) * D
+    bound = (2 * max(k, 1) * U + split_extra(algo, k)) * D
     err = np.abs(got[:n, :n] - C64)
     assert np.all(err[mask] <= bound[mask]), float(np.max(err[mask] / bound[mask]))
     assert np.all(np.isnan(got[:n, :n][~mask]))
@@ -178,7 +178,7 @@ def _residual_check(side, uplo, trans, diag, m, n, alpha, A, B0, X, algo):
     absT = np.abs(T)
     mag = absT @ np.abs(Xd) if side == "L" else np.abs(Xd) @ absT
     depth = max(0, int(np.ceil(np.log2(max(s, 1) / 128))))
-    extra = SPLIT_EXTRA[_resolve(algo, 128)] if algo == "auto" else SPLIT_EXTRA[algo]
+    extra = split_extra(_resolve(algo, 128) if algo == "auto" else algo, 128)
     tol = ((2 * s + 2) * U + depth * extra) * mag + 2 * U * np.abs(alpha * B0[:m, :n]) + 1e-38
     assert np.all(np.abs(R) <= tol), float(np.max(np.abs(R) / tol))
 

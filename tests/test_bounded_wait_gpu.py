@@ -75,6 +75,6 @@ def test_wait_limit_in_the_triangle_and_grouped_kernels():
     C64, D = blas3.ssyrk("U", "N", 300, 700, 1.0, Ah, 300, 0.0, Ch, 300)
     got = gb.to_fortran(Cd)
     iu = np.triu_indices(300)
-    from _gpu import SPLIT_EXTRA
-    bound = (2 * 700 * 2.0 ** -24 + SPLIT_EXTRA["bf16x3"]) * D[iu]
+    from _gpu import split_extra
+    bound = (2 * 700 * 2.0 ** -24 + split_extra("bf16x3", 700)) * D[iu]
     assert np.all(np.abs(got[iu] - C64[iu]) <= bound)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from _gpu import ALGOS, SPLIT_EXTRA, assert_within_bound, check_padding, run, torch_gpu
+from _gpu import ALGOS, assert_within_bound, auto_algo, check_padding, run, torch_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +39,6 @@ def test_random_problem(case):
     assert rc == 0
     check = algo
     if algo == "auto":
-        check = "bf16x3" if k >= 1024 else ("bf16x6" if k >= 4 else "simt")
+        check = auto_algo(k)
     assert_within_bound(p, got, algo=check)
     check_padding(p, got)

@@ -11,11 +11,11 @@ pytestmark = pytest.mark.gpu
 
 
 def _check_problem(p, got_storage, cols=None, algo="simt"):
-    from _gpu import SPLIT_EXTRA, STANDARD_BOUND_MIN_K
+    from _gpu import STANDARD_BOUND_MIN_K, split_extra
     C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta,
                           p.C, p.ldc, cols=cols)
     sub = got_storage[:p.m, :] if cols is None else got_storage[:p.m, cols]
-    rep = oracle.err_report(sub, C64, D, p.k, extra=SPLIT_EXTRA[algo])
+    rep = oracle.err_report(sub, C64, D, p.k, extra=split_extra(algo, p.k))
     assert rep["max_ratio"] <= 1.0, (p.ta, p.tb, p.m, p.n, p.k, rep)
     if p.k >= STANDARD_BOUND_MIN_K[algo]:
         assert oracle.err_report(sub, C64, D, p.k)["max_ratio"] <= 1.0
@@ -118,7 +118,7 @@ def test_grouped_edge_cases():
 
 
 # K values on both sides of every split's threshold (16 for TF32 x 2 terms,
-# 1024 for BF16 x 2 terms, 4 for BF16 x 3 terms with 6 products).
+# 1024 for BF16 x 2 terms, 9 for BF16 x 3 terms with 6 products, 10 with 9).
 MIXED_K = (1, 3, 4, 9, 15, 16, 40, 300, 1023, 1024, 1500, 2100)
 
 
@@ -126,7 +126,7 @@ MIXED_K = (1, 3, 4, 9, 15, 16, 40, 300, 1023, 1024, 1500, 2100)
 def test_grouped_per_problem_split_meets_fp32_bound(algo):
     """The plan picks a split per problem by K: each problem's result meets the
     plain FP32 bound, whichever split was preferred (a problem below the
-    preferred split's threshold takes BF16 x 3 terms, K < 4 the CUDA cores)."""
+    preferred split's threshold takes BF16 x 3 terms, K < 9 the CUDA cores)."""
     torch = torch_gpu()
     import paper_1912_04379_gb300 as gb
     rng = np.random.default_rng(31)

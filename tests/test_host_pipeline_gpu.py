@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from _gpu import assert_bit_exact, assert_within_bound, check_padding, torch_gpu
+from _gpu import assert_bit_exact, assert_within_bound, auto_algo, check_padding, torch_gpu
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
@@ -37,7 +37,7 @@ def test_host_pipeline_against_oracle(algo, shape, ta, tb):
     p = wl.make_problem(ta, tb, m, n, k, 1.25, -0.5, seed=m + n + k, ld_pad=3)
     got = _run_host(p, algo)
     if algo == "auto":
-        algo = "bf16x3" if k >= 1024 else ("bf16x6" if k >= 4 else "simt")
+        algo = auto_algo(k)
     assert_within_bound(p, got, algo=algo)
     check_padding(p, got)
 

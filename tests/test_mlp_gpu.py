@@ -23,7 +23,7 @@ import pytest
 
 import oracle
 from oracle import mlp as omlp
-from _gpu import SPLIT_EXTRA, torch_gpu
+from _gpu import auto_algo, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
@@ -33,12 +33,12 @@ TINY = 2.0 ** -126
 def _resolve(algo, k):
     if algo != "auto":
         return algo
-    return "bf16x3" if k >= 1024 else ("bf16x6" if k >= 4 else "simt")
+    return auto_algo(k)
 
 
 def _gemm_bound(algo, k, D):
     a = _resolve(algo, k)
-    return (2 * max(k, 1) * U + SPLIT_EXTRA[a]) * D
+    return (2 * max(k, 1) * U + split_extra(a, k)) * D
 
 
 def _setup(widths, batch, hidden, algo, seed):

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from _gpu import SPLIT_EXTRA, run, torch_gpu
+from _gpu import run, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
@@ -51,7 +51,7 @@ def test_nonfinite_positions(algo, ta, tb):
         inf = np.isinf(C64)
         assert np.array_equal(g[inf], C64[inf])
     fin = ~bad64
-    bound = (2 * p.k * U + SPLIT_EXTRA[algo]) * D[fin]
+    bound = (2 * p.k * U + split_extra(algo, p.k)) * D[fin]
     assert np.all(np.abs(g[fin] - C64[fin]) <= bound)
 
 
@@ -70,5 +70,5 @@ def test_near_overflow_stays_finite(algo):
                           p.C, p.ldc)
     g = got[:p.m, :].astype(np.float64)
     assert np.all(np.isfinite(C64)) and np.all(np.isfinite(g))
-    bound = (2 * p.k * U + SPLIT_EXTRA[algo]) * D
+    bound = (2 * p.k * U + split_extra(algo, p.k)) * D
     assert np.all(np.abs(g - C64) <= bound)

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from _gpu import SPLIT_EXTRA, STANDARD_BOUND_MIN_K, assert_within_bound, run, torch_gpu
+from _gpu import STANDARD_BOUND_MIN_K, assert_within_bound, run, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -23,7 +23,7 @@ def _check(p, got, algo):
     C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb, p.beta,
                           p.C, p.ldc)
     sub = got[:p.m, :]
-    assert oracle.err_report(sub, C64, D, p.k, extra=SPLIT_EXTRA[algo])["max_ratio"] <= 1.0
+    assert oracle.err_report(sub, C64, D, p.k, extra=split_extra(algo, p.k))["max_ratio"] <= 1.0
     if p.k >= STANDARD_BOUND_MIN_K[algo]:
         assert oracle.err_report(sub, C64, D, p.k)["max_ratio"] <= 1.0
 
@@ -52,7 +52,7 @@ def test_every_grouped_configuration_within_bound(group, config, algo):
     torch.cuda.synchronize()
     for i, p in enumerate(group):
         a = algo if p.k >= STANDARD_BOUND_MIN_K[algo] or algo == "bf16x6" else "bf16x6"
-        _check(p, views[i].cpu().numpy(), a if p.k >= 4 else "simt")
+        _check(p, views[i].cpu().numpy(), a if p.k >= STANDARD_BOUND_MIN_K["bf16x6"] else "simt")
     plan.close()
     assert h.device_error() == (0, 0)
 

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from _gpu import SPLIT_EXTRA, assert_within_bound, torch_gpu
+from _gpu import assert_within_bound, split_extra, torch_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +59,7 @@ def test_noalloc_matches_gb_sgemm_on_two_calls_in_a_row(algo):
         assert np.array_equal(new, ref), "gb_sgemm_noalloc differs from gb_sgemm"
         C64, D = oracle.sgemm(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.A, p.lda, p.B, p.ldb,
                               p.beta, p.C, p.ldc)
-        bound = oracle.bound(D, p.k, SPLIT_EXTRA[algo])
+        bound = oracle.bound(D, p.k, split_extra(algo, p.k))
         diff = np.abs(new[:p.m].astype(np.float64) - ref[:p.m].astype(np.float64))
         assert np.all(diff <= bound), "gb_sgemm_noalloc differs from gb_sgemm beyond the bound"
         assert_within_bound(p, new, algo=algo)
