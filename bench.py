@@ -1029,6 +1029,26 @@ def run_ours(args, rank, world, local_rank):
     err_rc, site = h.device_error()
     if err_rc != 0:
         raise RuntimeError(f"device wait timeout at site {site}")
+    # how the step time moves under load: the kernel's mean in the first and
+    # last quarter of the timed steps, and a separate back-to-back run of
+    # about 1.5 s (the chip reaches its power cap within a fraction of a
+    # second; the short timed window above may end before it settles)
+    per = [a.elapsed_time(b) for a, b in ev]
+    q = max(1, len(per) // 4)
+    sus_steps = max(50, int(1500.0 / max(ms_step, 0.1)))
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(sus_steps):
+        step()
+        compute()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sus_ms = s0.elapsed_time(s1) / sus_steps
+    drift = {"kernel_ms_first_quarter": statistics.mean(per[:q]),
+             "kernel_ms_last_quarter": statistics.mean(per[-q:]),
+             "sustained": {"steps": sus_steps, "seconds": sus_ms * sus_steps / 1e3,
+                           "ms_per_step": sus_ms,
+                           "value": whole_job_value(2.0 * M * N * K, sus_ms, 1)}}
 
     # -------- comparison arms on the same inputs (same GPU, same call path)
     def time_algo(algo, promote, steps, out):
@@ -1202,7 +1222,7 @@ def run_ours(args, rank, world, local_rank):
             "headline_arm": headline,
             "data": "synthetic", "config": workload_config(
                 {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
-            "gpu_launches": 5 * args.steps, "e2e": e2e, "roofline": roofline,
+            "gpu_launches": 5 * args.steps, "e2e": e2e, "roofline": roofline, "drift": drift,
             "pack": pack, "arms": arms, "measured_rooflines": measured, "grouped": grouped,
             "shapes": shapes, "configs": configs, "mlp": mlp, "blas3": blas3, "clocks": clocks,
             "source_sha": sha}
