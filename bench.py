@@ -92,6 +92,9 @@ def parse():
                     help="run SSYRK or STRSM of size N (default 8192) twice and exit")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="run two training steps of the benchmark network and exit")
+    ap.add_argument("--profile-sgemm", default=None, metavar="M,N,K[,ALGO]",
+                    help="run gb_sgemm of this shape ('N','N') twice on device-resident random "
+                         "inputs and exit (the path gb_sgemm picks, e.g. the skinny kernel)")
     ap.add_argument("--profile", default=None, metavar="M,N,K[,ALGO[,PROMOTE]]",
                     help="run one warm-up and one measured SGEMM of this shape (pack A, pack B, "
                          "compute) and exit; a small case for ncu captures")
@@ -124,6 +127,25 @@ def run_profile_case(spec):
             gb.compute_raw(algo, m, n, k, 1.0, Ap, Bp, 0.0, C.data_ptr(), m)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": [m, n, k, algo, promote], "ok": True}), flush=True)
+    return 0
+
+
+def run_profile_sgemm(spec):
+    """Two gb_sgemm calls of one shape on device-resident random inputs (ncu target)."""
+    import torch
+    import paper_1912_04379_gb300 as gb
+    parts = spec.split(",")
+    m, n, k = (int(x) for x in parts[:3])
+    algo = parts[3] if len(parts) > 3 else "auto"
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    A = (torch.rand((k, m), device="cuda", generator=g) * 2 - 1).t()
+    B = (torch.rand((n, k), device="cuda", generator=g) * 2 - 1).t()
+    C = gb.colmajor(m, n)
+    for _ in range(2):
+        gb.sgemm(A, B, C, algo=algo)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sgemm": [m, n, k, algo], "ok": True}), flush=True)
     return 0
 
 
@@ -1274,6 +1296,8 @@ def main():
         return 2
     if args.profile:
         return run_profile_case(args.profile)
+    if args.profile_sgemm:
+        return run_profile_sgemm(args.profile_sgemm)
     if args.profile_grouped:
         return run_profile_grouped(args.profile_grouped)
     if args.profile_blas3:

@@ -355,6 +355,24 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
  * (9.2 ms against 1.9 ms at M = N = K = 8192). */
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 
+/* Whether gb_sgemm (and the calls built on it) may take the skinny-product
+ * kernel (default: 1). It applies to SPLIT_BF16X3 and SPLIT_BF16X6 (and AUTO
+ * when it resolves to one of them) when one side has at most 64 rows
+ * (M <= 64 or N <= 64), K >= 256, the long side times K is at least 2^22,
+ * promotion is off, and TMA can read the long operand in place (16-byte
+ * aligned, leading dimension a multiple of 4). Such a product is bound by
+ * reading the long operand once: the kernel reads it as FP32 and splits it
+ * in shared memory on its way to the tensor cores (paper Sec. 3, the
+ * re-buffering of B'), packs only the short operand, and spreads the
+ * k-blocks evenly over the SMs (stream-K); a tile shared by several SMs is
+ * summed by the last of them in a fixed order, so results are deterministic.
+ * The workspace of gb_sgemm_workspace_size covers it. Off: the two-pass
+ * form (split/pack pass, then the tensor-core kernel) runs instead.
+ * gb_get_skinny_split reads the setting back (GB_ERR_ARG for a null
+ * pointer). */
+GB_API int gb_set_skinny_split(gb_handle_t h, int enable);
+GB_API int gb_get_skinny_split(gb_handle_t h, int *enable);
+
 /* Promoted accumulation in the split algorithms' tensor-core kernel
  * (default 0 = off). The tensor cores add the term products of a tile into
  * an FP32 accumulator in tensor memory, and that addition is not IEEE

@@ -98,6 +98,8 @@ SIGNATURES = {
     "gb_get_device_error": ([c_vp, c_vp, ctypes.POINTER(c_int)], c_int),
     "gb_set_wait_limit": ([c_vp, c_i64], c_int),
     "gb_set_fused_split": ([c_vp, c_int], c_int),
+    "gb_set_skinny_split": ([c_vp, c_int], c_int),
+    "gb_get_skinny_split": ([c_vp, ctypes.POINTER(c_int)], c_int),
     "gb_set_promotion": ([c_vp, c_i64], c_int),
     "gb_tune_grouped": ([c_vp], c_int),
     "gb_tune_sgemm": ([c_vp, c_int, c_char, c_char, c_i64, c_i64, c_i64], c_int),

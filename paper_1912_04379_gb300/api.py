@@ -99,8 +99,17 @@ class Handle:
         return self._ws
 
     def set_fused_split(self, enable: bool):
-        """Allow (default) or forbid the split fused into the tensor-core kernel."""
+        """Allow or forbid (default) the split fused into the tensor-core kernel."""
         _lib.check("gb_set_fused_split", self.lib.gb_set_fused_split(self.h, 1 if enable else 0))
+
+    def set_skinny_split(self, enable: bool):
+        """Allow (default) or forbid the skinny-product kernel (one side <= 64 rows)."""
+        _lib.check("gb_set_skinny_split", self.lib.gb_set_skinny_split(self.h, 1 if enable else 0))
+
+    def skinny_split(self) -> bool:
+        v = ctypes.c_int(0)
+        _lib.check("gb_get_skinny_split", self.lib.gb_get_skinny_split(self.h, ctypes.byref(v)))
+        return bool(v.value)
 
     def set_promotion(self, k_chunk: int):
         """Promoted accumulation: a fresh tensor-core accumulator every k_chunk

@@ -62,13 +62,26 @@ uint32_t *packed_max(void *packed, int mode, bool a_side, int64_t mn, int64_t k)
                                         round_up(terms_bytes(mode, a_side, mn, k), 256));
 }
 
+// Workspace of the skinny kernel: [short operand packed][partial slots and
+// tile counters], 1 KiB aligned.
+size_t skinny_ws_total(int mode, int64_t m, int64_t n, int64_t k) {
+    const bool xb = skinny_x_is_b(m, n);
+    return round_up(packed_bytes(mode, xb, xb ? m : n, k), 1024) +
+           round_up(skinny_ws_bytes(xb ? n : m), 1024);
+}
+
 // Workspace of a split algorithm: [A packed][B packed][split-K partials],
-// each region 1 KiB aligned; the partials exist only when K is split.
+// each region 1 KiB aligned; the partials exist only when K is split. For a
+// skinny shape, at least the skinny kernel's (which one runs depends on the
+// operands' alignment, unknown here).
 size_t split_ws_bytes(int mode, int64_t m, int64_t n, int64_t k) {
     const int s = split_k_factor(mode, m, n, k);
     const size_t partials = s > 1 ? (size_t)s * (size_t)m * (size_t)n * sizeof(float) : 0;
-    return round_up(packed_bytes(mode, true, m, k), 1024) +
-           round_up(packed_bytes(mode, false, n, k), 1024) + round_up(partials, 1024);
+    const size_t two_pass = round_up(packed_bytes(mode, true, m, k), 1024) +
+                            round_up(packed_bytes(mode, false, n, k), 1024) + round_up(partials, 1024);
+    if (!skinny_shape(mode, m, n, k)) return two_pass;
+    const size_t sk = skinny_ws_total(mode, m, n, k);
+    return sk > two_pass ? sk : two_pass;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? GB_OK : GB_ERR_CUDA; }
@@ -247,6 +260,30 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
     char *Bp = Ap + round_up(packed_bytes(mode, true, m, k), 1024);
     char *Pp = Bp + round_up(packed_bytes(mode, false, n, k), 1024);
     const int splits = split_k_factor(mode, m, n, k);
+    // A skinny product whose long operand TMA can read in place: split that
+    // operand inside the kernel (one pass over it), pack only the short one.
+    if (h->skinny_split && h->promote_k == 0 && skinny_supported(mode, m, n, k, A, lda, B, ldb)) {
+        SkinnyArgs g{};
+        g.mode = mode;
+        g.ta = is_trans(ta); g.tb = is_trans(tb);
+        g.x_is_b = skinny_x_is_b(m, n);
+        g.m = m; g.n = n; g.k = k;
+        g.alpha = alpha; g.beta = beta;
+        g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
+        g.C = C; g.ldc = ldc;
+        g.kpad = split_kpad(mode, k);
+        char *Yp = static_cast<char *>(ws);
+        const int64_t yrows = g.x_is_b ? m : n;
+        g.Yp = Yp;
+        g.ws = Yp + round_up(packed_bytes(mode, g.x_is_b, yrows, k), 1024);
+        g.dstate = h->dstate;
+        g.wait_limit = h->wait_limit;
+        g.sm_count = h->sm_count;
+        cudaError_t e = g.x_is_b ? pack_operand(mode, true, g.ta, m, k, A, lda, Yp, s)
+                                 : pack_operand(mode, false, g.tb, n, k, B, ldb, Yp, s);
+        if (e == cudaSuccess) e = launch_tc_skinny(g, s);
+        if (e != cudaErrorNotSupported) return cuda_status(e);
+    }
     // Split fused into the tensor-core kernel, when the handle allows it and
     // TMA can read A and B as they are; otherwise the separate split/pack
     // pass. For K > 2048 both give bit-identical results.
@@ -374,6 +411,7 @@ GB_API int gb_create(gb_handle_t *out) {
     h->cc_minor = prop.minor;
     h->smem_optin = prop.sharedMemPerBlockOptin;
     h->wait_limit = 2000000;
+    h->skinny_split = true;
     strncpy(h->gpu_name, prop.name, sizeof(h->gpu_name) - 1);
     if (cudaRuntimeGetVersion(&h->cuda_runtime_version) != cudaSuccess) h->cuda_runtime_version = 0;
     if (cudaMalloc(&h->dstate, sizeof(DeviceState)) != cudaSuccess ||
@@ -569,6 +607,21 @@ GB_API int gb_get_device_error(gb_handle_t h, void *stream, int *site) {
 GB_API int gb_set_fused_split(gb_handle_t h, int enable) {
     if (!h || h->magic != kHandleMagic) return GB_ERR_HANDLE;
     h->fused_split = enable != 0;
+    return GB_OK;
+}
+
+GB_API int gb_set_skinny_split(gb_handle_t h, int enable) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    h->skinny_split = enable != 0;
+    return GB_OK;
+}
+
+GB_API int gb_get_skinny_split(gb_handle_t h, int *enable) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!enable) return GB_ERR_ARG;
+    *enable = h->skinny_split ? 1 : 0;
     return GB_OK;
 }
 

@@ -51,6 +51,7 @@ struct gb_handle_s {
     gb_tuning_gemm_t gemm_rb[GB_TUNING_MAX_GEMM];
     int rb_override;
     bool fused_split;           // allow the split fused into the tensor-core kernel (off by default)
+    bool skinny_split;          // allow the skinny-product kernel (on by default)
     int64_t promote_k;          // promoted accumulation: chunk length in K (0 = off)
     // gb_sgemm_host's pipeline (copy-in, compute, copy-out), created on first use
     bool pipe_ready;
@@ -189,6 +190,38 @@ bool fused_supported(int mode, const float *A, int64_t lda, const float *B, int6
 // Split-precision SGEMM reading FP32 operands directly (no pack pass).
 // cudaErrorNotSupported: use the two-pass path instead.
 cudaError_t launch_tc_fused(const FusedArgs &a, cudaStream_t s);
+// ------------------------------------ skinny products, split in the kernel --
+// One operand (Y) has at most 64 rows, the other (X) is long: X is read as
+// FP32 by TMA and split inside the kernel, Y is packed beforehand.
+constexpr int kSkinnyMaxCtas = 256;   // the grid never exceeds this (workspace bound)
+struct SkinnyArgs {
+    int mode;                   // 1 = BF16 x 2 terms, 2 = BF16 x 3 terms
+    bool ta, tb;
+    bool x_is_b;                // X = op(B)^T (M short), else X = op(A) (N short)
+    int64_t m, n, k;
+    float alpha, beta;
+    const float *A; int64_t lda;
+    const float *B; int64_t ldb;
+    const void *Yp;             // Y packed by launch_split_pack, terms Yrows * kpad apart
+    int64_t kpad;
+    float *C; int64_t ldc;
+    void *ws;                   // skinny_ws_bytes(rows of X), 256-byte aligned
+    DeviceState *dstate;
+    int64_t wait_limit;
+    int sm_count;
+};
+// Shapes the skinny kernel takes (BF16 split, one side <= 64 rows, K >= 256
+// and a long X).
+bool skinny_shape(int mode, int64_t m, int64_t n, int64_t k);
+bool skinny_x_is_b(int64_t m, int64_t n);
+// skinny_shape, and TMA can read X in place (16-byte aligned, leading
+// dimension a multiple of 4).
+bool skinny_supported(int mode, int64_t m, int64_t n, int64_t k, const float *A, int64_t lda,
+                      const float *B, int64_t ldb);
+// Partial-sum slots and per-tile counters for X with R rows.
+size_t skinny_ws_bytes(int64_t R);
+// cudaErrorNotSupported: use the two-pass path instead.
+cudaError_t launch_tc_skinny(const SkinnyArgs &a, cudaStream_t s);
 // Workspace layout helpers shared by the API and the launcher.
 int64_t split_kpad(int mode, int64_t k);
 int split_parts(int mode);

@@ -1,0 +1,495 @@
+// Split-precision SGEMM for skinny products: one operand has at most 64 rows
+// (M <= 64 or N <= 64) and the other is long. Such a product is bound by
+// reading the long operand once from HBM; the two-pass path would read it as
+// FP32, write its terms and read the terms again, three times the bytes.
+//
+// The long operand X (op(B)^T when M is short, op(A) when N is short) comes
+// by TMA as FP32 tiles of 128 rows x 32 k straight from the caller's storage,
+// and eight converter warps split each tile in shared memory into its BF16
+// terms, laid out as tcgen05.mma reads them (the paper's re-buffering of B',
+// Sec. 3, done between L2 and the tensor cores). The short operand Y is split
+// once by the pack pass (a few MB); converter thread 0 brings its terms by
+// TMA into the same stage. The MMA forms the 128 x 64 tile D[x, y] =
+// sum_k X[x, k] Y[y, k]: X rows on the TMEM lanes, Y rows on 64 columns.
+//
+// Work: the (tile, k-block) iteration space is cut into one contiguous range
+// of equal length per CTA (stream-K), so every SM streams the same number of
+// X bytes whatever the shape. A tile whose k-blocks fall to several CTAs is
+// finished by the last of them: each writes its raw partial sum to a slot
+// fixed by the partition, counts itself in at the tile's counter, and the
+// one that completes the count adds the slots in slot order and writes C.
+// The order of the additions is therefore fixed: the result does not depend
+// on timing.
+//
+// Warps: 0 TMA producer (X), 1 TMEM owner + MMA issuer, 2..5 epilogue,
+// 6..13 converters (448 threads, one CTA per SM). Every wait is bounded as in
+// the other tensor-core kernels.
+#include "f32_tile.cuh"
+
+namespace gb {
+namespace {
+
+using namespace tcx;
+using namespace fx;
+
+constexpr int SK_YN = 64;                      // MMA N: rows of the short operand
+constexpr int SK_NCONV = 8;                    // converter warps
+constexpr int SK_CONV0 = 6;                    // first converter warp
+constexpr int SK_THREADS = (SK_CONV0 + SK_NCONV) * 32;
+constexpr int SK_SLOT = BM * SK_YN;            // floats in one partial-sum slot
+
+template <int MODE>                            // 1: BF16 x 2 terms, 2: BF16 x 3 terms
+struct SkCfg {
+    static constexpr int PARTS = MODE == 2 ? 3 : 2;
+    static constexpr int NPAIRS = MODE == 2 ? 6 : 3;
+    static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X tile
+    static constexpr int X_OP = BM * 64;                    // one X term: 128 rows of 64 B
+    static constexpr int Y_OP = SK_YN * 64;                 // one Y term: 64 rows of 64 B
+    static constexpr int T_BYTES = PARTS * (X_OP + Y_OP);   // one operand stage
+    static constexpr int F32_STAGES = 6;
+    static constexpr int T_STAGES = MODE == 2 ? 3 : 4;
+    static constexpr int ITEMS = BM * 4 / (SK_NCONV * 32);  // 8-value items per thread per tile
+    static constexpr int TMEM_COLS = 2 * SK_YN;             // two accumulators
+    static constexpr int NBARS = 2 * F32_STAGES + 3 * T_STAGES + 5;
+    static constexpr int SMEM_BYTES =
+        1024 + F32_STAGES * F32_BYTES + T_STAGES * T_BYTES + 8 * NBARS + 16;
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+    static_assert(ITEMS * SK_NCONV * 32 == BM * 4, "converter items");
+    static_assert(F32_BYTES % 1024 == 0 && T_BYTES % 1024 == 0 && X_OP % 1024 == 0,
+                  "swizzle atoms stay aligned");
+};
+
+// The stream-K partition: L = tiles * nkb iterations, CTA c takes
+// [lo(c), lo(c + 1)); owner(g) is the CTA whose range holds iteration g.
+struct SkPart {
+    int64_t L;
+    int64_t nkb;
+    int G;
+    __device__ __forceinline__ int64_t lo(int c) const { return (int64_t)c * L / G; }
+    __device__ __forceinline__ int owner(int64_t g) const { return (int)(((g + 1) * G - 1) / L); }
+};
+
+struct SkArgs {
+    int64_t R;                    // rows of X
+    int64_t Yrows;                // rows of Y (<= 64)
+    float alpha, beta;
+    float *C;
+    int64_t ldc;
+    int x_is_b;                   // 1: X = op(B)^T, D[x, y] = C[y, x]; 0: X = op(A), D[x, y] = C[x, y]
+    int xkc;                      // X is K-contiguous in storage
+    float *slots;                 // partial sums, (tiles + G) slots of 128 x 64
+    unsigned *count;              // per tile, zero at launch
+};
+
+// Named barrier 1 over the four epilogue warps (barrier 0 is __syncthreads).
+__device__ __forceinline__ void epi_sync() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// AND of `pred` over the epilogue threads; also synchronises them.
+__device__ __forceinline__ bool epi_all(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
+
+// C for NV values of row x of the tile, columns y0 .. y0 + NV - 1: C[y, x]
+// (x_is_b) or C[x, y], y < Yrows; C <- alpha * v + beta * C (C not read
+// when beta == 0), the split-K reduction's arithmetic.
+template <int NV>
+__device__ __forceinline__ void sk_store_c(const SkArgs &a, int64_t x, int y0, const float (&v)[NV]) {
+    if (x >= a.R) return;
+    const int64_t step = a.x_is_b ? 1 : a.ldc;
+    float *p = (a.x_is_b ? a.C + x * a.ldc : a.C + x) + y0 * step;
+    const int ny = (int)a.Yrows - y0;
+    if (a.beta == 0.f) {
+#pragma unroll
+        for (int y = 0; y < NV; ++y)
+            if (y < ny) p[y * step] = a.alpha * v[y];
+    } else {
+#pragma unroll
+        for (int y = 0; y < NV; ++y)
+            if (y < ny) p[y * step] = fmaf(a.alpha, v[y], a.beta * p[y * step]);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(SK_THREADS, 1)
+tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                 const SkArgs a, const SkPart P, DeviceState *dstate, uint64_t limit_ns) {
+    using CF = SkCfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    // FP32 stages at base; operand stages after them (X terms at +p*X_OP,
+    // Y terms at +PARTS*X_OP + p*Y_OP); then the barriers
+    const uint32_t tbase = base + CF::F32_STAGES * CF::F32_BYTES;
+    uint8_t *gtbase = gbase + CF::F32_STAGES * CF::F32_BYTES;
+    const uint32_t bar_base = tbase + CF::T_STAGES * CF::T_BYTES;
+    uint8_t *gbar = gtbase + CF::T_STAGES * CF::T_BYTES;
+    constexpr int F = CF::F32_STAGES, T = CF::T_STAGES;
+    auto f32_full = [&](int s) { return bar_base + 8u * s; };
+    auto f32_empty = [&](int s) { return bar_base + 8u * (F + s); };
+    auto t_full = [&](int s) { return bar_base + 8u * (2 * F + s); };
+    auto y_full = [&](int s) { return bar_base + 8u * (2 * F + T + s); };
+    auto t_empty = [&](int s) { return bar_base + 8u * (2 * F + 2 * T + s); };
+    auto acc_full = [&](int b) { return bar_base + 8u * (2 * F + 3 * T + b); };
+    auto acc_empty = [&](int b) { return bar_base + 8u * (2 * F + 3 * T + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * F + 3 * T + 4);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbar + 8 * CF::NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 4);
+    volatile int *last_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 8);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    WaitCtx w{abort_flag, dstate, limit_ns};
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F; ++s) {
+            mbar_init(f32_full(s), 1);
+            mbar_init(f32_empty(s), SK_NCONV);
+        }
+        for (int s = 0; s < T; ++s) {
+            mbar_init(t_full(s), SK_NCONV);
+            mbar_init(y_full(s), 1);
+            mbar_init(t_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full(b), 1);
+            mbar_init(acc_empty(b), 4);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        *last_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_tmap(&mapX);
+        prefetch_tmap(&mapY);
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_holder), CF::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    const int64_t nkb = P.nkb;
+    const int64_t g0 = P.lo(blockIdx.x), g1 = P.lo(blockIdx.x + 1);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: FP32 tiles of X ----------------
+            int s = 0;
+            uint32_t ph = 0, issued = 0, last_par = 0;
+            int64_t t = g0 / nkb;
+            int kb = (int)(g0 - t * nkb);
+            for (int64_t g = g0; g < g1; ++g, ++kb) {
+                if (kb == nkb) { kb = 0; ++t; }
+                if (!wait_bounded(w, f32_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
+                const uint32_t dst = base + s * CF::F32_BYTES;
+                mbar_arrive_expect_tx(f32_full(s), CF::F32_BYTES);
+                // K-contiguous storage: (x = k, y = row); else (x = row, y = k)
+                if (a.xkc) tma_load_2d(dst, &mapX, f32_full(s), kb * FBK, (int)(t * BM));
+                else       tma_load_2d(dst, &mapX, f32_full(s), (int)(t * BM), kb * FBK);
+                issued |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == F) { s = 0; ph ^= 1u; }
+            }
+            for (int i = 0; i < F; ++i) {
+                if (!(issued & (1u << i))) continue;
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(f32_full(i), (last_par >> i) & 1u)) {
+                    if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t idesc = instr_desc<kFmtBF16, SK_YN>();
+            int st = 0, acc = 0;
+            uint32_t ph = 0, acc_ph = 0;
+            bool ok = true;
+            for (int64_t t = g0 / nkb; t * nkb < g1 && ok; ++t) {
+                const int kb0 = (int)((g0 > t * nkb ? g0 : t * nkb) - t * nkb);
+                const int kb1 = (int)((g1 < (t + 1) * nkb ? g1 : (t + 1) * nkb) - t * nkb);
+                if (!wait_bounded(w, acc_empty(acc), acc_ph ^ 1u, kSiteMmaAccEmpty)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * SK_YN);
+                uint32_t accumulate = 0;
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!wait_bounded(w, t_full(st), ph, kSiteMmaFull) ||
+                        !wait_bounded(w, y_full(st), ph, kSiteMmaFull)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = tbase + st * CF::T_BYTES;
+#pragma unroll
+                    for (int q = 0; q < CF::NPAIRS; ++q) {
+                        int sy, sx;                    // the pair set is symmetric in A and B
+                        pair_of<MODE>(q, sy, sx);
+                        const uint32_t x0 = sb + sx * CF::X_OP;
+                        const uint32_t y0 = sb + CF::PARTS * CF::X_OP + sy * CF::Y_OP;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            mma_issue<false>(d_tmem, smem_desc<64>(x0 + ks * 32),
+                                             smem_desc<64>(y0 + ks * 32), idesc, accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    mma_commit(t_empty(st));            // operand stage back to the converters
+                    if (++st == T) { st = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(acc_full(acc));
+                if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+            }
+            mma_commit(drain_bar);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(drain_bar, 0)) {
+                if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+            }
+        }
+        __syncwarp();
+    } else if (warp < SK_CONV0) {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                       // TMEM lanes 32q .. 32q + 31
+        const int xr = q * 32 + lane;                 // row of the tile
+        int acc = 0;
+        uint32_t acc_ph = 0;
+        for (int64_t t = g0 / nkb; t * nkb < g1; ++t) {
+            const int64_t s0 = g0 > t * nkb ? g0 : t * nkb;
+            const int64_t s1 = g1 < (t + 1) * nkb ? g1 : (t + 1) * nkb;
+            // all four warps go on or all leave: they meet at named barriers below
+            if (!epi_all(wait_bounded(w, acc_full(acc), acc_ph, kSiteEpiAccFull))) break;
+            tc_fence_after();
+            uint32_t r0[16], r1[16], r2[16], r3[16];
+            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * SK_YN);
+            tmem_ld16(ta, r0);
+            tmem_ld16(ta + 16, r1);
+            tmem_ld16(ta + 32, r2);
+            tmem_ld16(ta + 48, r3);
+            tmem_wait64(r0, r1, r2, r3);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(acc));
+            if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+            float v[SK_YN];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                v[j] = __uint_as_float(r0[j]);
+                v[16 + j] = __uint_as_float(r1[j]);
+                v[32 + j] = __uint_as_float(r2[j]);
+                v[48 + j] = __uint_as_float(r3[j]);
+            }
+            const int64_t x = t * BM + xr;
+            if (s0 == t * nkb && s1 == (t + 1) * nkb) {   // the whole K range here
+                sk_store_c<SK_YN>(a, x, 0, v);
+                continue;
+            }
+            // raw partial to this CTA's slot of the tile: [y / 4][row][y % 4]
+            float4 *slot = reinterpret_cast<float4 *>(a.slots + (t + blockIdx.x) * SK_SLOT);
+#pragma unroll
+            for (int j = 0; j < SK_YN / 4; ++j)
+                __stcg(slot + j * BM + xr, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            // Count in at the tile (release: the barrier orders every epilogue
+            // thread's slot stores before the leader's fence and atomic), and
+            // learn whether this CTA completes the count (acquire: the fence
+            // after the atomic orders the other CTAs' slot stores, which they
+            // released the same way, before the loads below).
+            epi_sync();
+            const int cf = P.owner(t * nkb), cl = P.owner((t + 1) * nkb - 1);
+            if (warp == 2 && lane == 0) {
+                __threadfence();
+                const unsigned old = atomicAdd(a.count + t, 1u);
+                __threadfence();
+                *last_flag = old == (unsigned)(cl - cf) ? 1 : 0;
+            }
+            epi_sync();
+            if (!*last_flag) continue;
+            // the last of the tile's CTAs: add the slots in slot order, 16
+            // columns at a time
+#pragma unroll 1
+            for (int yq = 0; yq < SK_YN / 16; ++yq) {
+                float u16[16];
+#pragma unroll 1
+                for (int c = cf; c <= cl; ++c) {
+                    const float4 *sp = reinterpret_cast<const float4 *>(a.slots + (t + c) * SK_SLOT) +
+                                       (yq * 4) * BM + xr;
+                    float4 u[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) u[j] = __ldcg(sp + j * BM);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float uu[4] = {u[j].x, u[j].y, u[j].z, u[j].w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            u16[4 * j + e] = c == cf ? uu[e] : __fadd_rn(u16[4 * j + e], uu[e]);
+                    }
+                }
+                sk_store_c<16>(a, x, 16 * yq, u16);
+            }
+        }
+    } else {
+        // ---------------- converters (warps 6..13) ----------------
+        // Per k-block: read this thread's part of the FP32 tile, wait for a
+        // free operand stage, split and write the X terms, make them visible
+        // to the tensor cores, signal, hand the FP32 stage back. Converter
+        // thread 0 also brings the k-block's Y terms.
+        const int ct = threadIdx.x - SK_CONV0 * 32;
+        const bool issuer = ct == 0;
+        int s = 0, st = 0;
+        uint32_t ph = 0, pht = 0, y_issued = 0, y_par = 0;
+        int kb = (int)(g0 % nkb);
+        for (int64_t g = g0; g < g1; ++g, ++kb) {
+            if (kb == nkb) kb = 0;
+            if (!__all_sync(0xffffffffu, wait_bounded(w, f32_full(s), ph, kSiteConvert))) break;
+            const float *fxp = reinterpret_cast<const float *>(gbase + s * CF::F32_BYTES);
+            float v[CF::ITEMS][8];
+#pragma unroll
+            for (int j = 0; j < CF::ITEMS; ++j) {
+                const int i = ct + j * SK_NCONV * 32;
+                read8<BM>(fxp, a.xkc != 0, i % BM, i / BM, v[j]);
+            }
+            if (!__all_sync(0xffffffffu, wait_bounded(w, t_empty(st), pht ^ 1u, kSiteConvert))) break;
+            if (issuer) {
+                const uint32_t yb = tbase + st * CF::T_BYTES + CF::PARTS * CF::X_OP;
+                mbar_arrive_expect_tx(y_full(st), CF::PARTS * CF::Y_OP);
+#pragma unroll
+                for (int p = 0; p < CF::PARTS; ++p)
+                    tma_load_3d(yb + p * CF::Y_OP, &mapY, y_full(st), kb * FBK, 0, p);
+                y_issued |= 1u << st;
+                y_par = (y_par & ~(1u << st)) | (pht << st);
+            }
+            uint8_t *sp = gtbase + st * CF::T_BYTES;
+#pragma unroll
+            for (int j = 0; j < CF::ITEMS; ++j) {
+                const int i = ct + j * SK_NCONV * 32;
+                write8<CF::PARTS>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+            }
+            fence_async_shared();                     // term writes -> tensor-core reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_full(st));
+            if (++st == T) { st = 0; pht ^= 1u; }
+            // The FP32 stage goes back only now, after the values read from it
+            // were used: handed back right after the loads were issued, a
+            // refill could overwrite the stage before the loads completed
+            // (seen as stale rows in the warp that also issues the Y copies).
+            if (lane == 0) mbar_arrive(f32_empty(s));
+            if (++s == F) { s = 0; ph ^= 1u; }
+        }
+        if (issuer) {
+            for (int i = 0; i < T; ++i) {
+                if (!(y_issued & (1u << i))) continue;
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(y_full(i), (y_par >> i) & 1u)) {
+                    if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, CF::TMEM_COLS);
+}
+
+// 3-D map over the packed short operand, [term][row][kpad] BF16 with terms
+// part_stride elements apart: a box is 32 k x 64 rows of one term, 64-byte
+// rows with the 64-byte swizzle. Rows past Yrows and k past K read as 0.
+bool make_terms_map(CUtensorMap *map, const void *ptr, int64_t k, int64_t rows, int64_t kpad,
+                    int parts, int64_t part_stride) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)parts};
+    cuuint64_t strides[2] = {(cuuint64_t)(kpad * 2), (cuuint64_t)(part_stride * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)FBK, (cuuint32_t)SK_YN, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_skinny_mode(const SkinnyArgs &h, cudaStream_t s) {
+    using CF = SkCfg<MODE>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        e = cudaFuncSetAttribute(tc_skinny_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CF::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    // X: op(B)^T (stored K x N unless B is transposed) or op(A) (stored
+    // M x K unless A is transposed); K-contiguous storage is read along K.
+    const bool xkc = h.x_is_b ? !h.tb : h.ta;
+    const float *X = h.x_is_b ? h.B : h.A;
+    const int64_t ldx = h.x_is_b ? h.ldb : h.lda;
+    const int64_t R = h.x_is_b ? h.n : h.m, Yrows = h.x_is_b ? h.m : h.n;
+    alignas(64) CUtensorMap mx, my;
+    if (!make_f32_map(&mx, X, xkc ? h.k : R, xkc ? R : h.k, ldx, xkc, BM) ||
+        !make_terms_map(&my, h.Yp, h.k, Yrows, h.kpad, CF::PARTS, Yrows * h.kpad))
+        return cudaErrorNotSupported;
+    const int64_t tiles = (R + BM - 1) / BM;
+    const int64_t nkb = (h.k + FBK - 1) / FBK;
+    int G = h.sm_count > 0 ? h.sm_count : 1;
+    if (G > kSkinnyMaxCtas) G = kSkinnyMaxCtas;
+    if (tiles * nkb < G) G = (int)(tiles * nkb);
+    // the slots and counters, as skinny_ws_bytes lays them out
+    float *slots = reinterpret_cast<float *>(h.ws);
+    unsigned *count = reinterpret_cast<unsigned *>(
+        static_cast<char *>(h.ws) + (size_t)(tiles + kSkinnyMaxCtas) * SK_SLOT * sizeof(float));
+    e = cudaMemsetAsync(count, 0, (size_t)tiles * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    SkArgs a{R, Yrows, h.alpha, h.beta, h.C, h.ldc, h.x_is_b ? 1 : 0, xkc ? 1 : 0, slots, count};
+    SkPart P{tiles * nkb, nkb, G};
+    tc_skinny_kernel<MODE><<<G, SK_THREADS, CF::SMEM_BYTES, s>>>(
+        mx, my, a, P, h.dstate, (uint64_t)h.wait_limit * 1000ull);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t skinny_ws_bytes(int64_t R) {
+    const int64_t tiles = (R + BM - 1) / BM;
+    return (size_t)(tiles + kSkinnyMaxCtas) * SK_SLOT * sizeof(float) + (size_t)tiles * sizeof(unsigned);
+}
+
+bool skinny_shape(int mode, int64_t m, int64_t n, int64_t k) {
+    if (mode != 1 && mode != 2) return false;
+    if ((m > SK_YN && n > SK_YN) || k < 256) return false;
+    const int64_t R = m > n ? m : n;
+    if (R * k < ((int64_t)1 << 22)) return false;
+    return R < 2147483647LL && k < 2147483647LL;
+}
+
+bool skinny_x_is_b(int64_t m, int64_t n) { return m <= SK_YN && n >= m; }
+
+bool skinny_supported(int mode, int64_t m, int64_t n, int64_t k, const float *A, int64_t lda,
+                      const float *B, int64_t ldb) {
+    if (!skinny_shape(mode, m, n, k)) return false;
+    return skinny_x_is_b(m, n) ? f32_tma_ok(B, ldb) : f32_tma_ok(A, lda);
+}
+
+cudaError_t launch_tc_skinny(const SkinnyArgs &a, cudaStream_t s) {
+    switch (a.mode) {
+        case 1: return launch_skinny_mode<1>(a, s);
+        case 2: return launch_skinny_mode<2>(a, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace gb

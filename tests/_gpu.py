@@ -162,3 +162,17 @@ def assert_bit_exact(p, got):
     want = C64.astype(np.float32)
     assert np.array_equal(got[:p.m, :], want), \
         f"not bit-exact: {np.count_nonzero(got[:p.m, :] != want)} elements differ"
+
+
+def aligned_problem(ta, tb, m, n, k, alpha, beta, seed, dist="uniform"):
+    """Leading dimensions padded up to a multiple of 4 (+4), so TMA can read A and B."""
+    rng = np.random.default_rng(seed)
+    gen = {"uniform": wl.uniform, "int": wl.int_uniform, "logu": wl.log_uniform_signed}[dist]
+    ar, ac = wl.stored_shape(ta, m, k)
+    br, bc = wl.stored_shape(tb, k, n)
+    r4 = lambda x: (x + 3) // 4 * 4 + 4
+    A = gen(rng, ar, ac, r4(ar))
+    B = gen(rng, br, bc, r4(br))
+    C = gen(rng, m, n, m + 3, pad=wl.CANARY)
+    return wl.Problem(ta, tb, m, n, k, float(np.float32(alpha)), float(np.float32(beta)),
+                      A, A.shape[0], B, B.shape[0], C, C.shape[0])

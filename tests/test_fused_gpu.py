@@ -11,24 +11,11 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from _gpu import aligned_problem as _aligned_problem
 from _gpu import assert_bit_exact, assert_within_bound, check_padding, torch_gpu
 
 pytestmark = pytest.mark.gpu
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
-
-
-def _aligned_problem(ta, tb, m, n, k, alpha, beta, seed, dist="uniform"):
-    """Leading dimensions padded up to a multiple of 4 (+4), so TMA can read A and B."""
-    rng = np.random.default_rng(seed)
-    gen = {"uniform": wl.uniform, "int": wl.int_uniform, "logu": wl.log_uniform_signed}[dist]
-    ar, ac = wl.stored_shape(ta, m, k)
-    br, bc = wl.stored_shape(tb, k, n)
-    r4 = lambda x: (x + 3) // 4 * 4 + 4
-    A = gen(rng, ar, ac, r4(ar))
-    B = gen(rng, br, bc, r4(br))
-    C = gen(rng, m, n, m + 3, pad=wl.CANARY)
-    return wl.Problem(ta, tb, m, n, k, float(np.float32(alpha)), float(np.float32(beta)),
-                      A, A.shape[0], B, B.shape[0], C, C.shape[0])
 
 
 def _run_both(p, algo):
@@ -37,6 +24,8 @@ def _run_both(p, algo):
     fused, twopass = gb.Handle(), gb.Handle()
     fused.set_fused_split(True)
     twopass.set_fused_split(False)
+    for h in (fused, twopass):          # the skinny-product kernel would take (64, 2048, 4096)
+        h.set_skinny_split(False)
     outs = []
     for h in (fused, twopass):
         _, A = gb.from_fortran(p.A)
