@@ -38,14 +38,17 @@ __device__ __forceinline__ void read8(const float *tile, bool kc, int row, int c
 // in the K-major operand tile of that term: 64-byte rows, chunk index XOR
 // (row / 2) % 4 (the 64-byte swizzle tcgen05 descriptors expect). The split
 // is the pack pass's (split2_bf16), so the terms are bit-identical to it.
-template <int PARTS>
+// FAST: the caller has checked that all 8 values take the fast path
+// (max_abs_bits below kBf16FastLimit), so no per-pair branch.
+template <int PARTS, bool FAST = false>
 __device__ __forceinline__ void write8(uint8_t *op0, int op_bytes, int row, int chunk,
                                        const float v[8]) {
     uint32_t w[PARTS][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
         uint32_t pr[PARTS];
-        split2_bf16<PARTS>(v[e], v[e + 1], pr);
+        if (FAST) split2_bf16_fast<PARTS>(v[e], v[e + 1], pr);
+        else      split2_bf16<PARTS>(v[e], v[e + 1], pr);
 #pragma unroll
         for (int p = 0; p < PARTS; ++p) w[p][e / 2] = pr[p];
     }

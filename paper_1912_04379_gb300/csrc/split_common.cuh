@@ -48,10 +48,40 @@ __device__ __forceinline__ void split_bf16(float a, __nv_bfloat16 t[PARTS]) {
 // inputs that are non-finite or could round to infinity in BF16
 // (|a| >= 0x7f7f8000 as bits) take split_bf16, so the result is always
 // bit-identical to split_bf16 on each element.
+// The fast path alone, for callers that have checked that neither input is
+// non-finite or near overflow (bf16_fast_ok over all their inputs at once:
+// one branch for many pairs lets the pairs' conversions interleave).
+template <int PARTS>
+__device__ __forceinline__ void split2_bf16_fast(float a0, float a1, uint32_t w[PARTS]) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+    const float r0 = a0 - __low2float(h), r1 = a1 - __high2float(h);
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    w[0] = *reinterpret_cast<const uint32_t *>(&h);
+    w[1] = *reinterpret_cast<const uint32_t *>(&m);
+    if (PARTS == 3) {
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - __low2float(m), r1 - __high2float(m));
+        w[PARTS - 1] = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// Largest |x| as bits over n values; the fast path applies when it is below
+// 0x7f7f8000 (finite and not rounding to infinity in BF16).
+template <int N>
+__device__ __forceinline__ uint32_t max_abs_bits(const float (&v)[N]) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+        const uint32_t u = __float_as_uint(v[e]) & 0x7fffffffu;
+        m = u > m ? u : m;
+    }
+    return m;
+}
+constexpr uint32_t kBf16FastLimit = 0x7f7f8000u;
+
 template <int PARTS>
 __device__ __forceinline__ void split2_bf16(float a0, float a1, uint32_t w[PARTS]) {
     const uint32_t u0 = __float_as_uint(a0) & 0x7fffffffu, u1 = __float_as_uint(a1) & 0x7fffffffu;
-    if ((u0 > u1 ? u0 : u1) >= 0x7f7f8000u) {
+    if ((u0 > u1 ? u0 : u1) >= kBf16FastLimit) {
         __nv_bfloat16 t0[PARTS], t1[PARTS];
         split_bf16<PARTS>(a0, t0);
         split_bf16<PARTS>(a1, t1);

@@ -8,9 +8,12 @@
 // and eight converter warps split each tile in shared memory into its BF16
 // terms, laid out as tcgen05.mma reads them (the paper's re-buffering of B',
 // Sec. 3, done between L2 and the tensor cores). The short operand Y is split
-// once by the pack pass (a few MB); converter thread 0 brings its terms by
-// TMA into the same stage. The MMA forms the 128 x 64 tile D[x, y] =
+// once by the pack pass (a few MB); the producer brings its terms by TMA into
+// the same stage as the FP32 tile. The MMA forms the 128 x 64 tile D[x, y] =
 // sum_k X[x, k] Y[y, k]: X rows on the TMEM lanes, Y rows on 64 columns.
+// The converters work in two groups of four warps that take alternate
+// k-blocks, so that one group's wait, load and signalling latency overlaps
+// the other's conversion.
 //
 // Work: the (tile, k-block) iteration space is cut into one contiguous range
 // of equal length per CTA (stream-K), so every SM streams the same number of
@@ -34,6 +37,8 @@ using namespace fx;
 
 constexpr int SK_YN = 64;                      // MMA N: rows of the short operand
 constexpr int SK_NCONV = 8;                    // converter warps
+constexpr int SK_GROUPS = 2;                   // converter groups, alternate k-blocks
+constexpr int SK_GW = SK_NCONV / SK_GROUPS;    // warps per group
 constexpr int SK_CONV0 = 6;                    // first converter warp
 constexpr int SK_THREADS = (SK_CONV0 + SK_NCONV) * 32;
 constexpr int SK_SLOT = BM * SK_YN;            // floats in one partial-sum slot
@@ -45,17 +50,24 @@ struct SkCfg {
     static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X tile
     static constexpr int X_OP = BM * 64;                    // one X term: 128 rows of 64 B
     static constexpr int Y_OP = SK_YN * 64;                 // one Y term: 64 rows of 64 B
-    static constexpr int T_BYTES = PARTS * (X_OP + Y_OP);   // one operand stage
-    static constexpr int F32_STAGES = 6;
-    static constexpr int T_STAGES = MODE == 2 ? 3 : 4;
-    static constexpr int ITEMS = BM * 4 / (SK_NCONV * 32);  // 8-value items per thread per tile
+    // A stage: the FP32 X tile, overwritten in place by its terms (which
+    // may run past it: 3 terms take 24 KB), then the Y terms.
+    static constexpr int TERM_BYTES = F32_BYTES > PARTS * X_OP ? F32_BYTES : PARTS * X_OP;
+    static constexpr int STAGE = TERM_BYTES + PARTS * Y_OP;
+    static constexpr int TX_BYTES = F32_BYTES + PARTS * Y_OP;   // what TMA brings per stage
+    static constexpr int STAGES = MODE == 2 ? 6 : 8;
+    static constexpr int ITEMS = BM * 4 / (SK_GW * 32);     // 8-value items per thread per tile
     static constexpr int TMEM_COLS = 2 * SK_YN;             // two accumulators
-    static constexpr int NBARS = 2 * F32_STAGES + 3 * T_STAGES + 5;
-    static constexpr int SMEM_BYTES =
-        1024 + F32_STAGES * F32_BYTES + T_STAGES * T_BYTES + 8 * NBARS + 16;
+    static constexpr int NBARS = 3 * STAGES + 5;
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE + 8 * NBARS + 16;
     static_assert(SMEM_BYTES <= 232448, "shared memory");
-    static_assert(ITEMS * SK_NCONV * 32 == BM * 4, "converter items");
-    static_assert(F32_BYTES % 1024 == 0 && T_BYTES % 1024 == 0 && X_OP % 1024 == 0,
+    static_assert(ITEMS * SK_GW * 32 == BM * 4, "converter items");
+    // Every stage belongs to one group (stage count a multiple of the group
+    // count): a group then waits on a stage's barrier only one phase ahead of
+    // the last phase it saw there, so a parity wait cannot pass on an older
+    // phase of the same parity.
+    static_assert(STAGES % SK_GROUPS == 0, "stage ownership");
+    static_assert(STAGE % 1024 == 0 && TERM_BYTES % 1024 == 0 && X_OP % 1024 == 0,
                   "swizzle atoms stay aligned");
 };
 
@@ -100,6 +112,24 @@ __device__ __forceinline__ bool epi_all(bool pred) {
     return r != 0;
 }
 
+// Named barrier 2 + gi over the SK_GW warps of converter group gi: AND of
+// `pred` (all go on or all leave), and a plain synchronisation.
+__device__ __forceinline__ bool grp_all(int gi, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(2 + gi), "n"(SK_GW * 32)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void grp_sync(int gi) {
+    asm volatile("bar.sync %0, %1;" ::"r"(2 + gi), "n"(SK_GW * 32) : "memory");
+}
+
 // C for NV values of row x of the tile, columns y0 .. y0 + NV - 1: C[y, x]
 // (x_is_b) or C[x, y], y < Yrows; C <- alpha * v + beta * C (C not read
 // when beta == 0), the split-K reduction's arithmetic.
@@ -129,21 +159,20 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    // FP32 stages at base; operand stages after them (X terms at +p*X_OP,
-    // Y terms at +PARTS*X_OP + p*Y_OP); then the barriers
-    const uint32_t tbase = base + CF::F32_STAGES * CF::F32_BYTES;
-    uint8_t *gtbase = gbase + CF::F32_STAGES * CF::F32_BYTES;
-    const uint32_t bar_base = tbase + CF::T_STAGES * CF::T_BYTES;
-    uint8_t *gbar = gtbase + CF::T_STAGES * CF::T_BYTES;
-    constexpr int F = CF::F32_STAGES, T = CF::T_STAGES;
-    auto f32_full = [&](int s) { return bar_base + 8u * s; };
-    auto f32_empty = [&](int s) { return bar_base + 8u * (F + s); };
-    auto t_full = [&](int s) { return bar_base + 8u * (2 * F + s); };
-    auto y_full = [&](int s) { return bar_base + 8u * (2 * F + T + s); };
-    auto t_empty = [&](int s) { return bar_base + 8u * (2 * F + 2 * T + s); };
-    auto acc_full = [&](int b) { return bar_base + 8u * (2 * F + 3 * T + b); };
-    auto acc_empty = [&](int b) { return bar_base + 8u * (2 * F + 3 * T + 2 + b); };
-    const uint32_t drain_bar = bar_base + 8u * (2 * F + 3 * T + 4);
+    // stage s at base + s*STAGE: the FP32 X tile at +0, overwritten by the
+    // X terms (+p*X_OP); the Y terms at +TERM_BYTES + p*Y_OP. Then the
+    // barriers.
+    const uint32_t bar_base = base + CF::STAGES * CF::STAGE;
+    uint8_t *gbar = gbase + CF::STAGES * CF::STAGE;
+    constexpr int F = CF::STAGES;
+    // in_full: TMA landed X and Y; conv: the group wrote the X terms;
+    // in_empty: the MMAs read the stage
+    auto in_full = [&](int s) { return bar_base + 8u * s; };
+    auto conv = [&](int s) { return bar_base + 8u * (F + s); };
+    auto in_empty = [&](int s) { return bar_base + 8u * (2 * F + s); };
+    auto acc_full = [&](int b) { return bar_base + 8u * (3 * F + b); };
+    auto acc_empty = [&](int b) { return bar_base + 8u * (3 * F + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (3 * F + 4);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbar + 8 * CF::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 4);
     volatile int *last_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 8);
@@ -154,13 +183,9 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < F; ++s) {
-            mbar_init(f32_full(s), 1);
-            mbar_init(f32_empty(s), SK_NCONV);
-        }
-        for (int s = 0; s < T; ++s) {
-            mbar_init(t_full(s), SK_NCONV);
-            mbar_init(y_full(s), 1);
-            mbar_init(t_empty(s), 1);
+            mbar_init(in_full(s), 1);
+            mbar_init(conv(s), SK_GW);
+            mbar_init(in_empty(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
@@ -184,19 +209,22 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer: FP32 tiles of X ----------------
+            // ------------- TMA producer: FP32 tiles of X, terms of Y -------------
             int s = 0;
             uint32_t ph = 0, issued = 0, last_par = 0;
             int64_t t = g0 / nkb;
             int kb = (int)(g0 - t * nkb);
             for (int64_t g = g0; g < g1; ++g, ++kb) {
                 if (kb == nkb) { kb = 0; ++t; }
-                if (!wait_bounded(w, f32_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
-                const uint32_t dst = base + s * CF::F32_BYTES;
-                mbar_arrive_expect_tx(f32_full(s), CF::F32_BYTES);
+                if (!wait_bounded(w, in_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
+                const uint32_t dst = base + s * CF::STAGE;
+                mbar_arrive_expect_tx(in_full(s), CF::TX_BYTES);
                 // K-contiguous storage: (x = k, y = row); else (x = row, y = k)
-                if (a.xkc) tma_load_2d(dst, &mapX, f32_full(s), kb * FBK, (int)(t * BM));
-                else       tma_load_2d(dst, &mapX, f32_full(s), (int)(t * BM), kb * FBK);
+                if (a.xkc) tma_load_2d(dst, &mapX, in_full(s), kb * FBK, (int)(t * BM));
+                else       tma_load_2d(dst, &mapX, in_full(s), (int)(t * BM), kb * FBK);
+#pragma unroll
+                for (int p = 0; p < CF::PARTS; ++p)
+                    tma_load_3d(dst + CF::TERM_BYTES + p * CF::Y_OP, &mapY, in_full(s), kb * FBK, 0, p);
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == F) { s = 0; ph ^= 1u; }
@@ -204,7 +232,7 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             for (int i = 0; i < F; ++i) {
                 if (!(issued & (1u << i))) continue;
                 const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(f32_full(i), (last_par >> i) & 1u)) {
+                while (!mbar_try_wait(in_full(i), (last_par >> i) & 1u)) {
                     if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
                 }
             }
@@ -214,7 +242,7 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t idesc = instr_desc<kFmtBF16, SK_YN>();
-            int st = 0, acc = 0;
+            int s = 0, acc = 0;
             uint32_t ph = 0, acc_ph = 0;
             bool ok = true;
             for (int64_t t = g0 / nkb; t * nkb < g1 && ok; ++t) {
@@ -225,19 +253,20 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * SK_YN);
                 uint32_t accumulate = 0;
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!wait_bounded(w, t_full(st), ph, kSiteMmaFull) ||
-                        !wait_bounded(w, y_full(st), ph, kSiteMmaFull)) {
+                    if (!wait_bounded(w, conv(s), ph, kSiteMmaFull) ||
+                        !wait_bounded(w, in_full(s), ph, kSiteMmaFull)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sb = tbase + st * CF::T_BYTES;
+                    const uint32_t xs = base + s * CF::STAGE;
+                    const uint32_t ys = xs + CF::TERM_BYTES;
 #pragma unroll
                     for (int q = 0; q < CF::NPAIRS; ++q) {
                         int sy, sx;                    // the pair set is symmetric in A and B
                         pair_of<MODE>(q, sy, sx);
-                        const uint32_t x0 = sb + sx * CF::X_OP;
-                        const uint32_t y0 = sb + CF::PARTS * CF::X_OP + sy * CF::Y_OP;
+                        const uint32_t x0 = xs + sx * CF::X_OP;
+                        const uint32_t y0 = ys + sy * CF::Y_OP;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
                             mma_issue<false>(d_tmem, smem_desc<64>(x0 + ks * 32),
@@ -245,8 +274,8 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                             accumulate = 1;
                         }
                     }
-                    mma_commit(t_empty(st));            // operand stage back to the converters
-                    if (++st == T) { st = 0; ph ^= 1u; }
+                    mma_commit(in_empty(s));            // stage back to the producer
+                    if (++s == F) { s = 0; ph ^= 1u; }
                 }
                 if (!ok) break;
                 mma_commit(acc_full(acc));
@@ -339,61 +368,52 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             }
         }
     } else {
-        // ---------------- converters (warps 6..13) ----------------
-        // Per k-block: read this thread's part of the FP32 tile, wait for a
-        // free operand stage, split and write the X terms, make them visible
-        // to the tensor cores, signal, hand the FP32 stage back. Converter
-        // thread 0 also brings the k-block's Y terms.
+        // ---------------- converters (warps 6..13, two groups) ----------------
+        // Group gi takes the k-blocks at even (gi = 0) or odd (gi = 1)
+        // positions of this CTA's range, and so the stages s with s % 2 = gi.
+        // Per k-block: every thread of the group reads its part of the FP32
+        // tile, the group synchronises (the terms overwrite the FP32 bytes),
+        // each thread splits and writes its terms, makes them visible to the
+        // tensor cores, and each warp signals.
         const int ct = threadIdx.x - SK_CONV0 * 32;
-        const bool issuer = ct == 0;
-        int s = 0, st = 0;
-        uint32_t ph = 0, pht = 0, y_issued = 0, y_par = 0;
-        int kb = (int)(g0 % nkb);
-        for (int64_t g = g0; g < g1; ++g, ++kb) {
-            if (kb == nkb) kb = 0;
-            if (!__all_sync(0xffffffffu, wait_bounded(w, f32_full(s), ph, kSiteConvert))) break;
-            const float *fxp = reinterpret_cast<const float *>(gbase + s * CF::F32_BYTES);
+        const int gi = ct / (32 * SK_GW);
+        const int gt = ct - gi * (32 * SK_GW);
+        for (int64_t it = gi; it < g1 - g0; it += SK_GROUPS) {
+            const int s = (int)(it % F);
+            const uint32_t ph = (uint32_t)(it / F) & 1u;
+            if (!grp_all(gi, wait_bounded(w, in_full(s), ph, kSiteConvert))) break;
+            uint8_t *sp = gbase + s * CF::STAGE;
+            const float *fxp = reinterpret_cast<const float *>(sp);
             float v[CF::ITEMS][8];
 #pragma unroll
             for (int j = 0; j < CF::ITEMS; ++j) {
-                const int i = ct + j * SK_NCONV * 32;
+                const int i = gt + j * SK_GW * 32;
                 read8<BM>(fxp, a.xkc != 0, i % BM, i / BM, v[j]);
             }
-            if (!__all_sync(0xffffffffu, wait_bounded(w, t_empty(st), pht ^ 1u, kSiteConvert))) break;
-            if (issuer) {
-                const uint32_t yb = tbase + st * CF::T_BYTES + CF::PARTS * CF::X_OP;
-                mbar_arrive_expect_tx(y_full(st), CF::PARTS * CF::Y_OP);
+            grp_sync(gi);                             // all FP32 reads before any term write
+            // one branch for all of this thread's values: the exact scalar
+            // split only when one of them is non-finite or near overflow
+            float all[CF::ITEMS * 8];
 #pragma unroll
-                for (int p = 0; p < CF::PARTS; ++p)
-                    tma_load_3d(yb + p * CF::Y_OP, &mapY, y_full(st), kb * FBK, 0, p);
-                y_issued |= 1u << st;
-                y_par = (y_par & ~(1u << st)) | (pht << st);
-            }
-            uint8_t *sp = gtbase + st * CF::T_BYTES;
+            for (int j = 0; j < CF::ITEMS; ++j)
 #pragma unroll
-            for (int j = 0; j < CF::ITEMS; ++j) {
-                const int i = ct + j * SK_NCONV * 32;
-                write8<CF::PARTS>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+                for (int e = 0; e < 8; ++e) all[8 * j + e] = v[j][e];
+            if (max_abs_bits(all) < kBf16FastLimit) {
+#pragma unroll
+                for (int j = 0; j < CF::ITEMS; ++j) {
+                    const int i = gt + j * SK_GW * 32;
+                    write8<CF::PARTS, true>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CF::ITEMS; ++j) {
+                    const int i = gt + j * SK_GW * 32;
+                    write8<CF::PARTS>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+                }
             }
             fence_async_shared();                     // term writes -> tensor-core reads
             __syncwarp();
-            if (lane == 0) mbar_arrive(t_full(st));
-            if (++st == T) { st = 0; pht ^= 1u; }
-            // The FP32 stage goes back only now, after the values read from it
-            // were used: handed back right after the loads were issued, a
-            // refill could overwrite the stage before the loads completed
-            // (seen as stale rows in the warp that also issues the Y copies).
-            if (lane == 0) mbar_arrive(f32_empty(s));
-            if (++s == F) { s = 0; ph ^= 1u; }
-        }
-        if (issuer) {
-            for (int i = 0; i < T; ++i) {
-                if (!(y_issued & (1u << i))) continue;
-                const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(y_full(i), (y_par >> i) & 1u)) {
-                    if (global_ns() - t0 > kDrainLimitNs) { record_timeout(w, kSiteDrain); break; }
-                }
-            }
+            if (lane == 0) mbar_arrive(conv(s));
         }
     }
 
