@@ -209,6 +209,15 @@ __device__ __forceinline__ void tmem_wait32(uint32_t a[16], uint32_t b[16]) {
                  : "memory");
 }
 
+// Waits for this thread's outstanding TMEM loads, with the 48 registers of
+// three 16-column loads as in/out operands (see tmem_wait16).
+__device__ __forceinline__ void tmem_wait48(uint32_t a[16], uint32_t b[16], uint32_t c[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]), "+r"(c[8]), "+r"(c[9]), "+r"(c[10]), "+r"(c[11]), "+r"(c[12]), "+r"(c[13]), "+r"(c[14]), "+r"(c[15])
+                 :
+                 : "memory");
+}
+
 // Waits for this thread's outstanding TMEM loads, with the 64 registers of
 // four 16-column loads as in/out operands (see tmem_wait16).
 __device__ __forceinline__ void tmem_wait64(uint32_t a[16], uint32_t b[16], uint32_t c[16],

@@ -11,6 +11,13 @@
 // once by the pack pass (a few MB); the producer brings its terms by TMA into
 // the same stage as the FP32 tile. The MMA forms the 128 x 64 tile D[x, y] =
 // sum_k X[x, k] Y[y, k]: X rows on the TMEM lanes, Y rows on 64 columns.
+// The products of one X term with all the Y terms it pairs with go into one
+// MMA, the Y terms stacked along N (they lie one after another in shared
+// memory): for three terms X0 [Y0; Y1; Y2] (N = 192), X1 [Y0; Y1] (N = 128)
+// and X2 Y0 (N = 64), three MMAs per 16 k instead of six. Column group j of
+// the accumulator then holds the products with Y_j, and the epilogue adds
+// the groups in order. A narrow MMA costs about as much to issue as a wide
+// one, so the count of MMA instructions, not their width, set the pace.
 // The converters work in two groups of four warps that take alternate
 // k-blocks, so that one group's wait, load and signalling latency overlaps
 // the other's conversion.
@@ -46,7 +53,6 @@ constexpr int SK_SLOT = BM * SK_YN;            // floats in one partial-sum slot
 template <int MODE>                            // 1: BF16 x 2 terms, 2: BF16 x 3 terms
 struct SkCfg {
     static constexpr int PARTS = MODE == 2 ? 3 : 2;
-    static constexpr int NPAIRS = MODE == 2 ? 6 : 3;
     static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X tile
     static constexpr int X_OP = BM * 64;                    // one X term: 128 rows of 64 B
     static constexpr int Y_OP = SK_YN * 64;                 // one Y term: 64 rows of 64 B
@@ -57,7 +63,8 @@ struct SkCfg {
     static constexpr int TX_BYTES = F32_BYTES + PARTS * Y_OP;   // what TMA brings per stage
     static constexpr int STAGES = MODE == 2 ? 6 : 8;
     static constexpr int ITEMS = BM * 4 / (SK_GW * 32);     // 8-value items per thread per tile
-    static constexpr int TMEM_COLS = 2 * SK_YN;             // two accumulators
+    static constexpr int ACC_COLS = PARTS * SK_YN;          // one accumulator: PARTS column groups
+    static constexpr int TMEM_COLS = PARTS == 3 ? 512 : 256;  // two accumulators, power of 2
     static constexpr int NBARS = 3 * STAGES + 5;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE + 8 * NBARS + 16;
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -67,6 +74,7 @@ struct SkCfg {
     // the last phase it saw there, so a parity wait cannot pass on an older
     // phase of the same parity.
     static_assert(STAGES % SK_GROUPS == 0, "stage ownership");
+    static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
     static_assert(STAGE % 1024 == 0 && TERM_BYTES % 1024 == 0 && X_OP % 1024 == 0,
                   "swizzle atoms stay aligned");
 };
@@ -241,7 +249,6 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc = instr_desc<kFmtBF16, SK_YN>();
             int s = 0, acc = 0;
             uint32_t ph = 0, acc_ph = 0;
             bool ok = true;
@@ -250,7 +257,7 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 const int kb1 = (int)((g1 < (t + 1) * nkb ? g1 : (t + 1) * nkb) - t * nkb);
                 if (!wait_bounded(w, acc_empty(acc), acc_ph ^ 1u, kSiteMmaAccEmpty)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * SK_YN);
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::ACC_COLS);
                 uint32_t accumulate = 0;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!wait_bounded(w, conv(s), ph, kSiteMmaFull) ||
@@ -261,16 +268,20 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                     tc_fence_after();
                     const uint32_t xs = base + s * CF::STAGE;
                     const uint32_t ys = xs + CF::TERM_BYTES;
+                    // X term i with Y terms 0 .. PARTS-1-i stacked along N: the
+                    // pairs of the split (i + j <= PARTS - 1), heaviest first
 #pragma unroll
-                    for (int q = 0; q < CF::NPAIRS; ++q) {
-                        int sy, sx;                    // the pair set is symmetric in A and B
-                        pair_of<MODE>(q, sy, sx);
-                        const uint32_t x0 = xs + sx * CF::X_OP;
-                        const uint32_t y0 = ys + sy * CF::Y_OP;
+                    for (int i = 0; i < CF::PARTS; ++i) {
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            mma_issue<false>(d_tmem, smem_desc<64>(x0 + ks * 32),
-                                             smem_desc<64>(y0 + ks * 32), idesc, accumulate);
+                            const uint64_t xd = smem_desc<64>(xs + i * CF::X_OP + ks * 32);
+                            const uint64_t yd = smem_desc<64>(ys + ks * 32);
+                            if (CF::PARTS - i == 3)
+                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, 3 * SK_YN>(), accumulate);
+                            else if (CF::PARTS - i == 2)
+                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, 2 * SK_YN>(), accumulate);
+                            else
+                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, SK_YN>(), accumulate);
                             accumulate = 1;
                         }
                     }
@@ -300,35 +311,43 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             // all four warps go on or all leave: they meet at named barriers below
             if (!epi_all(wait_bounded(w, acc_full(acc), acc_ph, kSiteEpiAccFull))) break;
             tc_fence_after();
-            uint32_t r0[16], r1[16], r2[16], r3[16];
-            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * SK_YN);
-            tmem_ld16(ta, r0);
-            tmem_ld16(ta + 16, r1);
-            tmem_ld16(ta + 32, r2);
-            tmem_ld16(ta + 48, r3);
-            tmem_wait64(r0, r1, r2, r3);
+            // 16 columns at a time: the column groups' values (products with
+            // Y_0, Y_1, ...), added in group order, go to C (the whole K range
+            // is here) or to this CTA's partial-sum slot of the tile, laid
+            // out [y / 4][row][y % 4]
+            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CF::ACC_COLS);
+            const int64_t x = t * BM + xr;
+            const bool whole = s0 == t * nkb && s1 == (t + 1) * nkb;
+            float4 *slot = reinterpret_cast<float4 *>(a.slots + (t + blockIdx.x) * SK_SLOT);
+#pragma unroll 1
+            for (int c = 0; c < SK_YN; c += 16) {
+                uint32_t r[3][16];
+#pragma unroll
+                for (int u = 0; u < CF::PARTS; ++u) tmem_ld16(ta + (uint32_t)(u * SK_YN + c), r[u]);
+                if (CF::PARTS == 3) tmem_wait48(r[0], r[1], r[2]);
+                else tmem_wait32(r[0], r[1]);
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float z = __uint_as_float(r[0][j]);
+#pragma unroll
+                    for (int u = 1; u < CF::PARTS; ++u) z = __fadd_rn(z, __uint_as_float(r[u][j]));
+                    v[j] = z;
+                }
+                if (whole) {
+                    sk_store_c<16>(a, x, c, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        __stcg(slot + (c / 4 + j) * BM + xr,
+                               make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+                }
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(acc));
             if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
-            float v[SK_YN];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                v[j] = __uint_as_float(r0[j]);
-                v[16 + j] = __uint_as_float(r1[j]);
-                v[32 + j] = __uint_as_float(r2[j]);
-                v[48 + j] = __uint_as_float(r3[j]);
-            }
-            const int64_t x = t * BM + xr;
-            if (s0 == t * nkb && s1 == (t + 1) * nkb) {   // the whole K range here
-                sk_store_c<SK_YN>(a, x, 0, v);
-                continue;
-            }
-            // raw partial to this CTA's slot of the tile: [y / 4][row][y % 4]
-            float4 *slot = reinterpret_cast<float4 *>(a.slots + (t + blockIdx.x) * SK_SLOT);
-#pragma unroll
-            for (int j = 0; j < SK_YN / 4; ++j)
-                __stcg(slot + j * BM + xr, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            if (whole) continue;
             // Count in at the tile (release: the barrier orders every epilogue
             // thread's slot stores before the leader's fence and atomic), and
             // learn whether this CTA completes the count (acquire: the fence
