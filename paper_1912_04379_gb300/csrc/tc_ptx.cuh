@@ -228,6 +228,34 @@ __device__ __forceinline__ void tmem_wait64(uint32_t a[16], uint32_t b[16], uint
                  : "memory");
 }
 
+// 32 lanes x 32 bits, 16 consecutive columns from this thread's registers:
+// thread t of the warp writes row (lane base + t). Asynchronous: complete
+// only after tmem_wait_st().
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (+)= A * B with the A operand in tensor memory (128 lanes = M rows, K
+// packed two 16-bit values per 32-bit column starting at a_tmem, the lower
+// K in the low half) and B in shared memory (descriptor), kind::f16.
+__device__ __forceinline__ void mma_issue_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Term pair (A term, B term) for step q, smallest weight first.
 template <int MODE>
 __device__ __forceinline__ void pair_of(int q, int &sa, int &sb) {

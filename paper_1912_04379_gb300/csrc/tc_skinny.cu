@@ -54,29 +54,29 @@ template <int MODE>                            // 1: BF16 x 2 terms, 2: BF16 x 3
 struct SkCfg {
     static constexpr int PARTS = MODE == 2 ? 3 : 2;
     static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X tile
-    static constexpr int X_OP = BM * 64;                    // one X term: 128 rows of 64 B
     static constexpr int Y_OP = SK_YN * 64;                 // one Y term: 64 rows of 64 B
-    // A stage: the FP32 X tile, overwritten in place by its terms (which
-    // may run past it: 3 terms take 24 KB), then the Y terms.
-    static constexpr int TERM_BYTES = F32_BYTES > PARTS * X_OP ? F32_BYTES : PARTS * X_OP;
-    static constexpr int STAGE = TERM_BYTES + PARTS * Y_OP;
-    static constexpr int TX_BYTES = F32_BYTES + PARTS * Y_OP;   // what TMA brings per stage
-    static constexpr int STAGES = MODE == 2 ? 6 : 8;
-    static constexpr int ITEMS = BM * 4 / (SK_GW * 32);     // 8-value items per thread per tile
-    static constexpr int ACC_COLS = PARTS * SK_YN;          // one accumulator: PARTS column groups
-    static constexpr int TMEM_COLS = PARTS == 3 ? 512 : 256;  // two accumulators, power of 2
-    static constexpr int NBARS = 3 * STAGES + 5;
+    // A shared-memory stage: the FP32 X tile, then the Y terms.
+    static constexpr int STAGE = F32_BYTES + PARTS * Y_OP;
+    static constexpr int STAGES = 8;
+    // TMEM: two accumulators of PARTS column groups (products with Y_0,
+    // Y_1, ...), then the X-term stages, PARTS terms of 16 columns (32 BF16
+    // of K, two per column) each
+    static constexpr int ACC_COLS = PARTS * SK_YN;
+    static constexpr int XCOLS = PARTS * (FBK / 2);
+    static constexpr int T_STAGES = MODE == 2 ? 2 : 8;
+    static constexpr int TMEM_COLS = 512;
+    // equal ring lengths: one MMA commit per k-block releases both stages
+    static constexpr bool SHARED_RELEASE = T_STAGES == STAGES;
+    static constexpr int NBARS = 2 * STAGES + 2 * T_STAGES + 5;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE + 8 * NBARS + 16;
     static_assert(SMEM_BYTES <= 232448, "shared memory");
-    static_assert(ITEMS * SK_GW * 32 == BM * 4, "converter items");
-    // Every stage belongs to one group (stage count a multiple of the group
-    // count): a group then waits on a stage's barrier only one phase ahead of
-    // the last phase it saw there, so a parity wait cannot pass on an older
-    // phase of the same parity.
-    static_assert(STAGES % SK_GROUPS == 0, "stage ownership");
-    static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
-    static_assert(STAGE % 1024 == 0 && TERM_BYTES % 1024 == 0 && X_OP % 1024 == 0,
-                  "swizzle atoms stay aligned");
+    static_assert(2 * ACC_COLS + T_STAGES * XCOLS <= TMEM_COLS, "tensor memory");
+    // Every stage belongs to one group (stage counts a multiple of the group
+    // count): a group then waits on a stage's barrier only one phase ahead
+    // of the last phase it saw there, so a parity wait cannot pass on an
+    // older phase of the same parity.
+    static_assert(STAGES % SK_GROUPS == 0 && T_STAGES % SK_GROUPS == 0, "stage ownership");
+    static_assert(STAGE % 1024 == 0 && F32_BYTES % 1024 == 0, "swizzle atoms stay aligned");
 };
 
 // The stream-K partition: L = tiles * nkb iterations, CTA c takes
@@ -120,24 +120,6 @@ __device__ __forceinline__ bool epi_all(bool pred) {
     return r != 0;
 }
 
-// Named barrier 2 + gi over the SK_GW warps of converter group gi: AND of
-// `pred` (all go on or all leave), and a plain synchronisation.
-__device__ __forceinline__ bool grp_all(int gi, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, %2, %3, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(2 + gi), "n"(SK_GW * 32)
-        : "memory");
-    return r != 0;
-}
-__device__ __forceinline__ void grp_sync(int gi) {
-    asm volatile("bar.sync %0, %1;" ::"r"(2 + gi), "n"(SK_GW * 32) : "memory");
-}
-
 // C for NV values of row x of the tile, columns y0 .. y0 + NV - 1: C[y, x]
 // (x_is_b) or C[x, y], y < Yrows; C <- alpha * v + beta * C (C not read
 // when beta == 0), the split-K reduction's arithmetic.
@@ -167,20 +149,20 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    // stage s at base + s*STAGE: the FP32 X tile at +0, overwritten by the
-    // X terms (+p*X_OP); the Y terms at +TERM_BYTES + p*Y_OP. Then the
-    // barriers.
+    // stage s at base + s*STAGE: the FP32 X tile at +0, the Y terms at
+    // +F32_BYTES + p*Y_OP; then the barriers
     const uint32_t bar_base = base + CF::STAGES * CF::STAGE;
     uint8_t *gbar = gbase + CF::STAGES * CF::STAGE;
-    constexpr int F = CF::STAGES;
-    // in_full: TMA landed X and Y; conv: the group wrote the X terms;
-    // in_empty: the MMAs read the stage
+    constexpr int F = CF::STAGES, T = CF::T_STAGES;
+    // in_full: TMA landed X and Y; in_empty: the group's converters used X
+    // and the MMAs read Y; t_full: X terms in TMEM; t_empty: MMAs read them
     auto in_full = [&](int s) { return bar_base + 8u * s; };
-    auto conv = [&](int s) { return bar_base + 8u * (F + s); };
-    auto in_empty = [&](int s) { return bar_base + 8u * (2 * F + s); };
-    auto acc_full = [&](int b) { return bar_base + 8u * (3 * F + b); };
-    auto acc_empty = [&](int b) { return bar_base + 8u * (3 * F + 2 + b); };
-    const uint32_t drain_bar = bar_base + 8u * (3 * F + 4);
+    auto in_empty = [&](int s) { return bar_base + 8u * (F + s); };
+    auto t_full = [&](int s) { return bar_base + 8u * (2 * F + s); };
+    auto t_empty = [&](int s) { return bar_base + 8u * (2 * F + T + s); };
+    auto acc_full = [&](int b) { return bar_base + 8u * (2 * F + 2 * T + b); };
+    auto acc_empty = [&](int b) { return bar_base + 8u * (2 * F + 2 * T + 2 + b); };
+    const uint32_t drain_bar = bar_base + 8u * (2 * F + 2 * T + 4);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbar + 8 * CF::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 4);
     volatile int *last_flag = reinterpret_cast<volatile int *>(gbar + 8 * CF::NBARS + 8);
@@ -192,8 +174,11 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     if (threadIdx.x == 0) {
         for (int s = 0; s < F; ++s) {
             mbar_init(in_full(s), 1);
-            mbar_init(conv(s), SK_GW);
-            mbar_init(in_empty(s), 1);
+            mbar_init(in_empty(s), SK_GW + (CF::SHARED_RELEASE ? 0 : 1));
+        }
+        for (int s = 0; s < T; ++s) {
+            mbar_init(t_full(s), SK_GW);
+            mbar_init(t_empty(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
@@ -225,14 +210,17 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             for (int64_t g = g0; g < g1; ++g, ++kb) {
                 if (kb == nkb) { kb = 0; ++t; }
                 if (!wait_bounded(w, in_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
+                // with one ring length, the MMAs' release of the k-block's
+                // TMEM stage also releases its input stage (same index)
+                if (CF::SHARED_RELEASE && !wait_bounded(w, t_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
                 const uint32_t dst = base + s * CF::STAGE;
-                mbar_arrive_expect_tx(in_full(s), CF::TX_BYTES);
+                mbar_arrive_expect_tx(in_full(s), CF::STAGE);
                 // K-contiguous storage: (x = k, y = row); else (x = row, y = k)
                 if (a.xkc) tma_load_2d(dst, &mapX, in_full(s), kb * FBK, (int)(t * BM));
                 else       tma_load_2d(dst, &mapX, in_full(s), (int)(t * BM), kb * FBK);
 #pragma unroll
                 for (int p = 0; p < CF::PARTS; ++p)
-                    tma_load_3d(dst + CF::TERM_BYTES + p * CF::Y_OP, &mapY, in_full(s), kb * FBK, 0, p);
+                    tma_load_3d(dst + CF::F32_BYTES + p * CF::Y_OP, &mapY, in_full(s), kb * FBK, 0, p);
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == F) { s = 0; ph ^= 1u; }
@@ -249,8 +237,8 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            int s = 0, acc = 0;
-            uint32_t ph = 0, acc_ph = 0;
+            int s = 0, st = 0, acc = 0;
+            uint32_t ph = 0, pht = 0, acc_ph = 0;
             bool ok = true;
             for (int64_t t = g0 / nkb; t * nkb < g1 && ok; ++t) {
                 const int kb0 = (int)((g0 > t * nkb ? g0 : t * nkb) - t * nkb);
@@ -260,32 +248,38 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CF::ACC_COLS);
                 uint32_t accumulate = 0;
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!wait_bounded(w, conv(s), ph, kSiteMmaFull) ||
-                        !wait_bounded(w, in_full(s), ph, kSiteMmaFull)) {
+                    // The converters of this k-block waited for its stage to
+                    // land (X and Y alike) before they signalled t_full, so
+                    // that one wait orders the Y bytes before the MMAs too.
+                    if (!wait_bounded(w, t_full(st), pht, kSiteMmaFull)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t xs = base + s * CF::STAGE;
-                    const uint32_t ys = xs + CF::TERM_BYTES;
-                    // X term i with Y terms 0 .. PARTS-1-i stacked along N: the
-                    // pairs of the split (i + j <= PARTS - 1), heaviest first
+                    const uint32_t xt = tmem_base + (uint32_t)(2 * CF::ACC_COLS + st * CF::XCOLS);
+                    const uint32_t ys = base + s * CF::STAGE + CF::F32_BYTES;
+                    // X term i (from TMEM) with Y terms 0 .. PARTS-1-i stacked
+                    // along N: the pairs of the split (i + j <= PARTS - 1)
 #pragma unroll
                     for (int i = 0; i < CF::PARTS; ++i) {
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t xd = smem_desc<64>(xs + i * CF::X_OP + ks * 32);
+                            // K = 16 per MMA: 8 TMEM columns of X, 32 bytes of a Y row
+                            const uint32_t xa = xt + (uint32_t)(i * (FBK / 2) + ks * 8);
                             const uint64_t yd = smem_desc<64>(ys + ks * 32);
                             if (CF::PARTS - i == 3)
-                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, 3 * SK_YN>(), accumulate);
+                                mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, 3 * SK_YN>(), accumulate);
                             else if (CF::PARTS - i == 2)
-                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, 2 * SK_YN>(), accumulate);
+                                mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, 2 * SK_YN>(), accumulate);
                             else
-                                mma_issue<false>(d_tmem, xd, yd, instr_desc<kFmtBF16, SK_YN>(), accumulate);
+                                mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, SK_YN>(), accumulate);
                             accumulate = 1;
                         }
                     }
-                    mma_commit(in_empty(s));            // stage back to the producer
+                    mma_commit(t_empty(st));            // X terms read
+                    if (!CF::SHARED_RELEASE)
+                        mma_commit(in_empty(s));        // Y terms read: the MMA's share of the stage
+                    if (++st == T) { st = 0; pht ^= 1u; }
                     if (++s == F) { s = 0; ph ^= 1u; }
                 }
                 if (!ok) break;
@@ -389,50 +383,56 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     } else {
         // ---------------- converters (warps 6..13, two groups) ----------------
         // Group gi takes the k-blocks at even (gi = 0) or odd (gi = 1)
-        // positions of this CTA's range, and so the stages s with s % 2 = gi.
-        // Per k-block: every thread of the group reads its part of the FP32
-        // tile, the group synchronises (the terms overwrite the FP32 bytes),
-        // each thread splits and writes its terms, makes them visible to the
-        // tensor cores, and each warp signals.
+        // positions of this CTA's range. Each thread converts one row of the
+        // tile, the TMEM lane its warp may access (32 (warp % 4) + lane):
+        // reads its 32 FP32 values, splits them, waits for a free TMEM stage,
+        // stores the terms there, waits for the stores, and signals; the
+        // input stage goes back only now, after its values were used.
         const int ct = threadIdx.x - SK_CONV0 * 32;
         const int gi = ct / (32 * SK_GW);
-        const int gt = ct - gi * (32 * SK_GW);
+        const int row = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         for (int64_t it = gi; it < g1 - g0; it += SK_GROUPS) {
-            const int s = (int)(it % F);
-            const uint32_t ph = (uint32_t)(it / F) & 1u;
-            if (!grp_all(gi, wait_bounded(w, in_full(s), ph, kSiteConvert))) break;
-            uint8_t *sp = gbase + s * CF::STAGE;
-            const float *fxp = reinterpret_cast<const float *>(sp);
-            float v[CF::ITEMS][8];
+            const int s = (int)(it % F), st = (int)(it % T);
+            const uint32_t ph = (uint32_t)(it / F) & 1u, pht = (uint32_t)(it / T) & 1u;
+            if (!__all_sync(0xffffffffu, wait_bounded(w, in_full(s), ph, kSiteConvert))) break;
+            const float *fxp = reinterpret_cast<const float *>(gbase + s * CF::STAGE);
+            float v[FBK];
 #pragma unroll
-            for (int j = 0; j < CF::ITEMS; ++j) {
-                const int i = gt + j * SK_GW * 32;
-                read8<BM>(fxp, a.xkc != 0, i % BM, i / BM, v[j]);
-            }
-            grp_sync(gi);                             // all FP32 reads before any term write
-            // one branch for all of this thread's values: the exact scalar
-            // split only when one of them is non-finite or near overflow
-            float all[CF::ITEMS * 8];
+            for (int c = 0; c < FBK / 8; ++c) read8<BM>(fxp, a.xkc != 0, row, c, v + 8 * c);
+            // terms, two K values per 32-bit column (the lower K in the low
+            // half); one branch for all 32 values: the exact scalar split only
+            // when one of them is non-finite or near overflow
+            uint32_t tw[CF::PARTS][FBK / 2];
+            if (max_abs_bits(v) < kBf16FastLimit) {
 #pragma unroll
-            for (int j = 0; j < CF::ITEMS; ++j)
+                for (int e = 0; e < FBK / 2; ++e) {
+                    uint32_t pr[CF::PARTS];
+                    split2_bf16_fast<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) all[8 * j + e] = v[j][e];
-            if (max_abs_bits(all) < kBf16FastLimit) {
-#pragma unroll
-                for (int j = 0; j < CF::ITEMS; ++j) {
-                    const int i = gt + j * SK_GW * 32;
-                    write8<CF::PARTS, true>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+                    for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < CF::ITEMS; ++j) {
-                    const int i = gt + j * SK_GW * 32;
-                    write8<CF::PARTS>(sp, CF::X_OP, i % BM, i / BM, v[j]);
+                for (int e = 0; e < FBK / 2; ++e) {
+                    uint32_t pr[CF::PARTS];
+                    split2_bf16<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
+#pragma unroll
+                    for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
                 }
             }
-            fence_async_shared();                     // term writes -> tensor-core reads
+            if (!__all_sync(0xffffffffu, wait_bounded(w, t_empty(st), pht ^ 1u, kSiteConvert))) break;
+            tc_fence_after();
+            const uint32_t xt = tmem_base + lane_base + (uint32_t)(2 * CF::ACC_COLS + st * CF::XCOLS);
+#pragma unroll
+            for (int p = 0; p < CF::PARTS; ++p) tmem_st16(xt + (uint32_t)(p * (FBK / 2)), tw[p]);
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(conv(s));
+            if (lane == 0) {
+                mbar_arrive(t_full(st));
+                mbar_arrive(in_empty(s));
+            }
         }
     }
 
