@@ -53,17 +53,25 @@ constexpr int SK_SLOT = BM * SK_YN;            // floats in one partial-sum slot
 template <int MODE>                            // 1: BF16 x 2 terms, 2: BF16 x 3 terms
 struct SkCfg {
     static constexpr int PARTS = MODE == 2 ? 3 : 2;
-    static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X tile
+    // k per stage: KH sub-blocks of 32 (the TMA boxes and the 64-byte rows
+    // of the Y terms are 32 k wide); two for the two-term split, whose
+    // narrower accumulators leave tensor memory for 64-k stages: per k, the
+    // MMA issuer's waits and commits then cost half
+    static constexpr int KH = MODE == 2 ? 1 : 2;
+    static constexpr int SKB = KH * FBK;
+    static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X sub-tile
+    static constexpr int X_BYTES = KH * F32_BYTES;
     static constexpr int Y_OP = SK_YN * 64;                 // one Y term: 64 rows of 64 B
-    // A shared-memory stage: the FP32 X tile, then the Y terms.
-    static constexpr int STAGE = F32_BYTES + PARTS * Y_OP;
-    static constexpr int STAGES = 8;
+    // A shared-memory stage: the FP32 X sub-tiles (h at +h*F32_BYTES), then
+    // the Y terms (sub-block h, term p at +X_BYTES + (h*PARTS + p)*Y_OP).
+    static constexpr int STAGE = X_BYTES + KH * PARTS * Y_OP;
+    static constexpr int STAGES = MODE == 2 ? 8 : 4;
     // TMEM: two accumulators of PARTS column groups (products with Y_0,
-    // Y_1, ...), then the X-term stages, PARTS terms of 16 columns (32 BF16
-    // of K, two per column) each
+    // Y_1, ...), then the X-term stages: sub-block h, term p at 16 (h*PARTS
+    // + p) columns (32 BF16 of K, two per column)
     static constexpr int ACC_COLS = PARTS * SK_YN;
-    static constexpr int XCOLS = PARTS * (FBK / 2);
-    static constexpr int T_STAGES = MODE == 2 ? 2 : 8;
+    static constexpr int XCOLS = KH * PARTS * (FBK / 2);
+    static constexpr int T_STAGES = MODE == 2 ? 2 : 4;
     static constexpr int TMEM_COLS = 512;
     // equal ring lengths: one MMA commit per k-block releases both stages
     static constexpr bool SHARED_RELEASE = T_STAGES == STAGES;
@@ -216,11 +224,16 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 const uint32_t dst = base + s * CF::STAGE;
                 mbar_arrive_expect_tx(in_full(s), CF::STAGE);
                 // K-contiguous storage: (x = k, y = row); else (x = row, y = k)
-                if (a.xkc) tma_load_2d(dst, &mapX, in_full(s), kb * FBK, (int)(t * BM));
-                else       tma_load_2d(dst, &mapX, in_full(s), (int)(t * BM), kb * FBK);
 #pragma unroll
-                for (int p = 0; p < CF::PARTS; ++p)
-                    tma_load_3d(dst + CF::F32_BYTES + p * CF::Y_OP, &mapY, in_full(s), kb * FBK, 0, p);
+                for (int h = 0; h < CF::KH; ++h) {
+                    const int k0 = kb * CF::SKB + h * FBK;
+                    if (a.xkc) tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(s), k0, (int)(t * BM));
+                    else       tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(s), (int)(t * BM), k0);
+#pragma unroll
+                    for (int p = 0; p < CF::PARTS; ++p)
+                        tma_load_3d(dst + CF::X_BYTES + (h * CF::PARTS + p) * CF::Y_OP, &mapY, in_full(s),
+                                    k0, 0, p);
+                }
                 issued |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == F) { s = 0; ph ^= 1u; }
@@ -257,16 +270,18 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                     }
                     tc_fence_after();
                     const uint32_t xt = tmem_base + (uint32_t)(2 * CF::ACC_COLS + st * CF::XCOLS);
-                    const uint32_t ys = base + s * CF::STAGE + CF::F32_BYTES;
                     // X term i (from TMEM) with Y terms 0 .. PARTS-1-i stacked
                     // along N: the pairs of the split (i + j <= PARTS - 1)
+#pragma unroll
+                    for (int h = 0; h < CF::KH; ++h)
 #pragma unroll
                     for (int i = 0; i < CF::PARTS; ++i) {
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
                             // K = 16 per MMA: 8 TMEM columns of X, 32 bytes of a Y row
-                            const uint32_t xa = xt + (uint32_t)(i * (FBK / 2) + ks * 8);
-                            const uint64_t yd = smem_desc<64>(ys + ks * 32);
+                            const uint32_t xa = xt + (uint32_t)((h * CF::PARTS + i) * (FBK / 2) + ks * 8);
+                            const uint64_t yd = smem_desc<64>(base + s * CF::STAGE + CF::X_BYTES +
+                                                              h * CF::PARTS * CF::Y_OP + ks * 32);
                             if (CF::PARTS - i == 3)
                                 mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, 3 * SK_YN>(), accumulate);
                             else if (CF::PARTS - i == 2)
@@ -384,10 +399,11 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         // ---------------- converters (warps 6..13, two groups) ----------------
         // Group gi takes the k-blocks at even (gi = 0) or odd (gi = 1)
         // positions of this CTA's range. Each thread converts one row of the
-        // tile, the TMEM lane its warp may access (32 (warp % 4) + lane):
-        // reads its 32 FP32 values, splits them, waits for a free TMEM stage,
-        // stores the terms there, waits for the stores, and signals; the
-        // input stage goes back only now, after its values were used.
+        // tile, the TMEM lane its warp may access (32 (warp % 4) + lane): it
+        // waits for a free TMEM stage, then per 32-k sub-block reads its FP32
+        // values, splits them and stores the terms there; it waits for the
+        // stores and signals; the input stage goes back only now, after its
+        // values were used.
         const int ct = threadIdx.x - SK_CONV0 * 32;
         const int gi = ct / (32 * SK_GW);
         const int row = 32 * (warp & 3) + lane;
@@ -396,36 +412,40 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             const int s = (int)(it % F), st = (int)(it % T);
             const uint32_t ph = (uint32_t)(it / F) & 1u, pht = (uint32_t)(it / T) & 1u;
             if (!__all_sync(0xffffffffu, wait_bounded(w, in_full(s), ph, kSiteConvert))) break;
-            const float *fxp = reinterpret_cast<const float *>(gbase + s * CF::STAGE);
-            float v[FBK];
-#pragma unroll
-            for (int c = 0; c < FBK / 8; ++c) read8<BM>(fxp, a.xkc != 0, row, c, v + 8 * c);
-            // terms, two K values per 32-bit column (the lower K in the low
-            // half); one branch for all 32 values: the exact scalar split only
-            // when one of them is non-finite or near overflow
-            uint32_t tw[CF::PARTS][FBK / 2];
-            if (max_abs_bits(v) < kBf16FastLimit) {
-#pragma unroll
-                for (int e = 0; e < FBK / 2; ++e) {
-                    uint32_t pr[CF::PARTS];
-                    split2_bf16_fast<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
-#pragma unroll
-                    for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < FBK / 2; ++e) {
-                    uint32_t pr[CF::PARTS];
-                    split2_bf16<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
-#pragma unroll
-                    for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
-                }
-            }
             if (!__all_sync(0xffffffffu, wait_bounded(w, t_empty(st), pht ^ 1u, kSiteConvert))) break;
             tc_fence_after();
             const uint32_t xt = tmem_base + lane_base + (uint32_t)(2 * CF::ACC_COLS + st * CF::XCOLS);
 #pragma unroll
-            for (int p = 0; p < CF::PARTS; ++p) tmem_st16(xt + (uint32_t)(p * (FBK / 2)), tw[p]);
+            for (int h = 0; h < CF::KH; ++h) {
+                const float *fxp = reinterpret_cast<const float *>(gbase + s * CF::STAGE + h * CF::F32_BYTES);
+                float v[FBK];
+#pragma unroll
+                for (int c = 0; c < FBK / 8; ++c) read8<BM>(fxp, a.xkc != 0, row, c, v + 8 * c);
+                // terms, two K values per 32-bit column (the lower K in the low
+                // half); one branch for all 32 values: the exact scalar split
+                // only when one of them is non-finite or near overflow
+                uint32_t tw[CF::PARTS][FBK / 2];
+                if (max_abs_bits(v) < kBf16FastLimit) {
+#pragma unroll
+                    for (int e = 0; e < FBK / 2; ++e) {
+                        uint32_t pr[CF::PARTS];
+                        split2_bf16_fast<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
+#pragma unroll
+                        for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < FBK / 2; ++e) {
+                        uint32_t pr[CF::PARTS];
+                        split2_bf16<CF::PARTS>(v[2 * e], v[2 * e + 1], pr);
+#pragma unroll
+                        for (int p = 0; p < CF::PARTS; ++p) tw[p][e] = pr[p];
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < CF::PARTS; ++p)
+                    tmem_st16(xt + (uint32_t)((h * CF::PARTS + p) * (FBK / 2)), tw[p]);
+            }
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
@@ -483,7 +503,7 @@ cudaError_t launch_skinny_mode(const SkinnyArgs &h, cudaStream_t s) {
         !make_terms_map(&my, h.Yp, h.k, Yrows, h.kpad, CF::PARTS, Yrows * h.kpad))
         return cudaErrorNotSupported;
     const int64_t tiles = (R + BM - 1) / BM;
-    const int64_t nkb = (h.k + FBK - 1) / FBK;
+    const int64_t nkb = (h.k + CF::SKB - 1) / CF::SKB;
     int G = h.sm_count > 0 ? h.sm_count : 1;
     if (G > kSkinnyMaxCtas) G = kSkinnyMaxCtas;
     if (tiles * nkb < G) G = (int)(tiles * nkb);
