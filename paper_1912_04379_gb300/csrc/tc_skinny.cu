@@ -105,6 +105,7 @@ struct SkArgs {
     int64_t ldc;
     int x_is_b;                   // 1: X = op(B)^T, D[x, y] = C[y, x]; 0: X = op(A), D[x, y] = C[x, y]
     int xkc;                      // X is K-contiguous in storage
+    int cvec;                     // x_is_b and rows of C 16-byte aligned (C and ldc): float4 stores
     float *slots;                 // partial sums, (tiles + G) slots of 128 x 64
     unsigned *count;              // per tile, zero at launch
 };
@@ -130,13 +131,35 @@ __device__ __forceinline__ bool epi_all(bool pred) {
 
 // C for NV values of row x of the tile, columns y0 .. y0 + NV - 1: C[y, x]
 // (x_is_b) or C[x, y], y < Yrows; C <- alpha * v + beta * C (C not read
-// when beta == 0), the split-K reduction's arithmetic.
+// when beta == 0), the split-K reduction's arithmetic. With x_is_b the
+// values are contiguous in C, 16-byte vectors when cvec (y0 % 4 == 0).
 template <int NV>
 __device__ __forceinline__ void sk_store_c(const SkArgs &a, int64_t x, int y0, const float (&v)[NV]) {
     if (x >= a.R) return;
     const int64_t step = a.x_is_b ? 1 : a.ldc;
     float *p = (a.x_is_b ? a.C + x * a.ldc : a.C + x) + y0 * step;
     const int ny = (int)a.Yrows - y0;
+    if (a.cvec) {
+#pragma unroll
+        for (int y = 0; y < NV; y += 4) {
+            if (y + 3 < ny) {
+                float4 *q = reinterpret_cast<float4 *>(p + y);
+                float4 r = make_float4(a.alpha * v[y], a.alpha * v[y + 1], a.alpha * v[y + 2],
+                                       a.alpha * v[y + 3]);
+                if (a.beta != 0.f) {
+                    const float4 c = *q;
+                    r = make_float4(fmaf(a.alpha, v[y], a.beta * c.x), fmaf(a.alpha, v[y + 1], a.beta * c.y),
+                                    fmaf(a.alpha, v[y + 2], a.beta * c.z), fmaf(a.alpha, v[y + 3], a.beta * c.w));
+                }
+                *q = r;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (y + e < ny) p[y + e] = a.beta == 0.f ? a.alpha * v[y + e] : fmaf(a.alpha, v[y + e], a.beta * p[y + e]);
+            }
+        }
+        return;
+    }
     if (a.beta == 0.f) {
 #pragma unroll
         for (int y = 0; y < NV; ++y)
@@ -373,23 +396,33 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             epi_sync();
             if (!*last_flag) continue;
             // the last of the tile's CTAs: add the slots in slot order, 16
-            // columns at a time
+            // columns at a time, the loads of up to four slots issued
+            // together (each load is an L2 round trip, and this runs in the
+            // kernel's tail)
 #pragma unroll 1
             for (int yq = 0; yq < SK_YN / 16; ++yq) {
                 float u16[16];
 #pragma unroll 1
-                for (int c = cf; c <= cl; ++c) {
-                    const float4 *sp = reinterpret_cast<const float4 *>(a.slots + (t + c) * SK_SLOT) +
-                                       (yq * 4) * BM + xr;
-                    float4 u[4];
+                for (int c0 = cf; c0 <= cl; c0 += 4) {
+                    float4 u[4][4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) u[j] = __ldcg(sp + j * BM);
+                    for (int cc = 0; cc < 4; ++cc) {
+                        if (c0 + cc > cl) break;
+                        const float4 *sp = reinterpret_cast<const float4 *>(
+                                               a.slots + (t + c0 + cc) * SK_SLOT) + (yq * 4) * BM + xr;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float uu[4] = {u[j].x, u[j].y, u[j].z, u[j].w};
+                        for (int j = 0; j < 4; ++j) u[cc][j] = __ldcg(sp + j * BM);
+                    }
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            u16[4 * j + e] = c == cf ? uu[e] : __fadd_rn(u16[4 * j + e], uu[e]);
+                    for (int cc = 0; cc < 4; ++cc) {
+                        if (c0 + cc > cl) break;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float uu[4] = {u[cc][j].x, u[cc][j].y, u[cc][j].z, u[cc][j].w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                u16[4 * j + e] = (c0 + cc == cf) ? uu[e] : __fadd_rn(u16[4 * j + e], uu[e]);
+                        }
                     }
                 }
                 sk_store_c<16>(a, x, 16 * yq, u16);
@@ -513,7 +546,9 @@ cudaError_t launch_skinny_mode(const SkinnyArgs &h, cudaStream_t s) {
         static_cast<char *>(h.ws) + (size_t)(tiles + kSkinnyMaxCtas) * SK_SLOT * sizeof(float));
     e = cudaMemsetAsync(count, 0, (size_t)tiles * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    SkArgs a{R, Yrows, h.alpha, h.beta, h.C, h.ldc, h.x_is_b ? 1 : 0, xkc ? 1 : 0, slots, count};
+    const bool cvec = h.x_is_b && !(reinterpret_cast<uintptr_t>(h.C) & 15) && h.ldc % 4 == 0;
+    SkArgs a{R, Yrows, h.alpha, h.beta, h.C, h.ldc, h.x_is_b ? 1 : 0, xkc ? 1 : 0, cvec ? 1 : 0,
+             slots, count};
     SkPart P{tiles * nkb, nkb, G};
     tc_skinny_kernel<MODE><<<G, SK_THREADS, CF::SMEM_BYTES, s>>>(
         mx, my, a, P, h.dstate, (uint64_t)h.wait_limit * 1000ull);
