@@ -105,13 +105,39 @@ bool pipe_ready(gb_handle_t h) {
 }
 
 // ---------------------------------------------- 2-D blocked pipeline --
-// Row blocks of op(A) and column blocks of op(B): multiples of 256 (the
-// scaled FP16 split scales op(B) per 256 columns), about an eighth of the
-// dimension and at least 1024.
-int64_t block_2d(int64_t x) {
+// Row blocks of op(A) and column blocks of op(B), multiples of 256 (the
+// scaled FP16 split scales op(B) per 256 columns). A long dimension (at
+// least 6144) gets blocks that shrink toward its end, about 1/4, 3/16,
+// 5/32, 1/8, 3/32, 1/16, 1/16, 1/32, 1/32 of it: everything the last pair
+// of blocks leaves to do (the GEMMs of its L and their downloads) starts
+// only after the last upload, so the last blocks should be small, while the
+// large first blocks keep the early GEMMs efficient. Shorter dimensions get
+// about eighths, at least 1024. Fills off[0..count] with the boundaries and
+// returns count (<= kMaxBlocks2d).
+constexpr int kMaxBlocks2d = 9;
+int schedule_2d(int64_t x, int64_t *off) {
+    const int64_t units = (x + 255) / 256;
+    int count = 0;
+    off[0] = 0;
+    if (units >= 24) {
+        static const int w[kMaxBlocks2d] = {8, 6, 5, 4, 3, 2, 2, 1, 1};   // in 32nds
+        int64_t used = 0;
+        for (int i = 0; i < kMaxBlocks2d; ++i) {
+            int64_t u = (units * w[i] + 16) / 32;
+            if (u < 1) u = 1;
+            if (i == kMaxBlocks2d - 1 || used + u > units) u = units - used;
+            if (u <= 0) break;
+            used += u;
+            off[++count] = used * 256 < x ? used * 256 : x;
+            if (used >= units) break;
+        }
+        return count;
+    }
     int64_t b = (x + 7) / 8;
     b = (b + 255) / 256 * 256;
-    return b < 1024 ? 1024 : b;
+    if (b < 1024) b = 1024;
+    for (int64_t r = 0; r < x; r += b) off[++count] = r + b < x ? r + b : x;
+    return count;
 }
 
 bool use_2d(int mode, int64_t m, int64_t n, bool compute) {
@@ -120,17 +146,15 @@ bool use_2d(int mode, int64_t m, int64_t n, bool compute) {
 
 struct Grid2 {
     int mode;
-    int64_t mb, nb;           // rows of an op(A) block, columns of an op(B) block
-    int ra, cb;               // number of op(A) and op(B) blocks
+    int ra, cb;               // number of op(A) row blocks and op(B) column blocks
+    int64_t aoff[kMaxBlocks2d + 1], boff[kMaxBlocks2d + 1];   // their boundaries
     size_t a_dev, b_dev, a_pack, b_pack, c_dev, total;
 };
 
 void grid2(int mode, int64_t m, int64_t n, int64_t k, Grid2 *G) {
     G->mode = mode;
-    G->mb = block_2d(m);
-    G->nb = block_2d(n);
-    G->ra = (int)((m + G->mb - 1) / G->mb);
-    G->cb = (int)((n + G->nb - 1) / G->nb);
+    G->ra = schedule_2d(m, G->aoff);
+    G->cb = schedule_2d(n, G->boff);
     size_t off = 0;
     G->a_dev = off; off += round_up((size_t)m * (size_t)k * 4, 256);      // op(A) as stored
     G->b_dev = off; off += round_up((size_t)k * (size_t)n * 4, 256);      // op(B) as stored
@@ -162,10 +186,10 @@ int run_2d(gb_handle_t h, const Grid2 &G, char ta, char tb, int64_t m, int64_t n
     for (int i = 0; i < 5; ++i) GB_TRY(cudaStreamWaitEvent(h->pipe_stream[i], ev[0], 0));
     // the C strips of pair s: rows [r0, r1) x columns [0, c1) and rows [0, r0) x [c0, c1)
     auto strips = [&](int s, int64_t &r0, int64_t &r1, int64_t &c0, int64_t &c1) {
-        r0 = s < G.ra ? s * G.mb : m;
-        r1 = s < G.ra ? (r0 + G.mb < m ? r0 + G.mb : m) : m;
-        c0 = s < G.cb ? s * G.nb : n;
-        c1 = s < G.cb ? (c0 + G.nb < n ? c0 + G.nb : n) : n;
+        r0 = s < G.ra ? G.aoff[s] : m;
+        r1 = s < G.ra ? G.aoff[s + 1] : m;
+        c0 = s < G.cb ? G.boff[s] : n;
+        c1 = s < G.cb ? G.boff[s + 1] : n;
     };
     auto copy_c = [&](bool up, int64_t i0, int64_t i1, int64_t j0, int64_t j1, cudaStream_t st) {
         if (i1 <= i0 || j1 <= j0) return cudaSuccess;
