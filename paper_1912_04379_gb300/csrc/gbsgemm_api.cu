@@ -279,8 +279,10 @@ int sgemm_impl(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64
         g.dstate = h->dstate;
         g.wait_limit = h->wait_limit;
         g.sm_count = h->sm_count;
-        cudaError_t e = g.x_is_b ? pack_operand(mode, true, g.ta, m, k, A, lda, Yp, s)
-                                 : pack_operand(mode, false, g.tb, n, k, B, ldb, Yp, s);
+        cudaError_t e = skinny_clear(g, s);
+        if (e == cudaSuccess)
+            e = g.x_is_b ? pack_operand(mode, true, g.ta, m, k, A, lda, Yp, s)
+                         : pack_operand(mode, false, g.tb, n, k, B, ldb, Yp, s);
         if (e == cudaSuccess) e = launch_tc_skinny(g, s);
         if (e != cudaErrorNotSupported) return cuda_status(e);
     }

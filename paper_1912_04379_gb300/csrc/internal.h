@@ -220,6 +220,9 @@ bool skinny_supported(int mode, int64_t m, int64_t n, int64_t k, const float *A,
                       const float *B, int64_t ldb);
 // Partial-sum slots and per-tile counters for X with R rows.
 size_t skinny_ws_bytes(int64_t R);
+// Zeroes the per-tile counters in a.ws; call before the pack of Y, which
+// the kernel's launch then follows directly (it may overlap the pack's tail).
+cudaError_t skinny_clear(const SkinnyArgs &a, cudaStream_t s);
 // cudaErrorNotSupported: use the two-pass path instead.
 cudaError_t launch_tc_skinny(const SkinnyArgs &a, cudaStream_t s);
 // Workspace layout helpers shared by the API and the launcher.

@@ -94,6 +94,10 @@ __global__ void __launch_bounds__(256)
 split_pack_kc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64_t ld,
                      void *__restrict__ out, int64_t kpad, int64_t ps,
                      const uint32_t *__restrict__ mx) {
+    // a kernel launched after this one as its programmatic dependent (the
+    // skinny kernel) may start now; it waits for this grid before it reads
+    // what this grid writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t p = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
     if (p >= kpad) return;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
@@ -178,6 +182,7 @@ split_pack_rc_kernel(int64_t rows, int64_t K, const float *__restrict__ X, int64
                      void *__restrict__ out, int64_t kpad, int64_t ps,
                      const uint32_t *__restrict__ mx) {
     __shared__ float T[64][65];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // as above
     pack_tile64<MODE>(X, ld, false, VEC, rows, K, out, kpad, ps, (int64_t)blockIdx.y * 64,
                       (int64_t)blockIdx.x * 64, T, mx);
 }

@@ -234,30 +234,64 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     if (warp == 0) {
         if (lane == 0) {
             // ------------- TMA producer: FP32 tiles of X, terms of Y -------------
+            // The kernel may start while the pack of Y (the launch before it)
+            // still runs: the first F stages' X tiles go out at once, then
+            // the producer waits for that grid (griddepcontrol.wait; a no-op
+            // when the kernel was not launched as its dependent) and issues
+            // their Y terms; from then on X and Y together. Each stage's
+            // expect_tx counts X and Y, so in_full completes only with both.
             int s = 0;
             uint32_t ph = 0, issued = 0, last_par = 0;
             int64_t t = g0 / nkb;
             int kb = (int)(g0 - t * nkb);
-            for (int64_t g = g0; g < g1; ++g, ++kb) {
-                if (kb == nkb) { kb = 0; ++t; }
-                if (!wait_bounded(w, in_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
-                // with one ring length, the MMAs' release of the k-block's
-                // TMEM stage also releases its input stage (same index)
-                if (CF::SHARED_RELEASE && !wait_bounded(w, t_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
-                const uint32_t dst = base + s * CF::STAGE;
-                mbar_arrive_expect_tx(in_full(s), CF::STAGE);
-                // K-contiguous storage: (x = k, y = row); else (x = row, y = k)
+            const int64_t early = (g1 - g0) < F ? (g1 - g0) : F;   // stages whose Y waits
+            auto load_x = [&](uint32_t dst, int st, int64_t tt, int kk) {
 #pragma unroll
                 for (int h = 0; h < CF::KH; ++h) {
-                    const int k0 = kb * CF::SKB + h * FBK;
-                    if (a.xkc) tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(s), k0, (int)(t * BM));
-                    else       tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(s), (int)(t * BM), k0);
+                    const int k0 = kk * CF::SKB + h * FBK;
+                    if (a.xkc) tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(st), k0, (int)(tt * BM));
+                    else       tma_load_2d(dst + h * CF::F32_BYTES, &mapX, in_full(st), (int)(tt * BM), k0);
+                }
+            };
+            auto load_y = [&](uint32_t dst, int st, int kk) {
+#pragma unroll
+                for (int h = 0; h < CF::KH; ++h)
 #pragma unroll
                     for (int p = 0; p < CF::PARTS; ++p)
-                        tma_load_3d(dst + CF::X_BYTES + (h * CF::PARTS + p) * CF::Y_OP, &mapY, in_full(s),
-                                    k0, 0, p);
+                        tma_load_3d(dst + CF::X_BYTES + (h * CF::PARTS + p) * CF::Y_OP, &mapY, in_full(st),
+                                    kk * CF::SKB + h * FBK, 0, p);
+            };
+            // the first stages are empty: X only
+            {
+                int64_t tt = t;
+                int kk = kb;
+                for (int64_t i = 0; i < early; ++i, ++kk) {
+                    if (kk == nkb) { kk = 0; ++tt; }
+                    const uint32_t dst = base + (int)i * CF::STAGE;
+                    mbar_arrive_expect_tx(in_full((int)i), CF::STAGE);
+                    load_x(dst, (int)i, tt, kk);
                 }
-                issued |= 1u << s;
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                kk = kb;
+                for (int64_t i = 0; i < early; ++i, ++kk) {
+                    if (kk == nkb) kk = 0;
+                    load_y(base + (int)i * CF::STAGE, (int)i, kk);
+                    issued |= 1u << i;
+                }
+            }
+            for (int64_t g = g0; g < g1; ++g, ++kb) {
+                if (kb == nkb) { kb = 0; ++t; }
+                if (g - g0 >= early) {
+                    if (!wait_bounded(w, in_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
+                    // with one ring length, the MMAs' release of the k-block's
+                    // TMEM stage also releases its input stage (same index)
+                    if (CF::SHARED_RELEASE && !wait_bounded(w, t_empty(s), ph ^ 1u, kSiteProducerEmpty)) break;
+                    const uint32_t dst = base + s * CF::STAGE;
+                    mbar_arrive_expect_tx(in_full(s), CF::STAGE);
+                    load_x(dst, s, t, kb);
+                    load_y(dst, s, kb);
+                    issued |= 1u << s;
+                }
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == F) { s = 0; ph ^= 1u; }
             }
@@ -540,18 +574,31 @@ cudaError_t launch_skinny_mode(const SkinnyArgs &h, cudaStream_t s) {
     int G = h.sm_count > 0 ? h.sm_count : 1;
     if (G > kSkinnyMaxCtas) G = kSkinnyMaxCtas;
     if (tiles * nkb < G) G = (int)(tiles * nkb);
-    // the slots and counters, as skinny_ws_bytes lays them out
+    // the slots and counters, as skinny_ws_bytes lays them out (the
+    // counters were zeroed by skinny_clear before the pack of Y)
     float *slots = reinterpret_cast<float *>(h.ws);
     unsigned *count = reinterpret_cast<unsigned *>(
         static_cast<char *>(h.ws) + (size_t)(tiles + kSkinnyMaxCtas) * SK_SLOT * sizeof(float));
-    e = cudaMemsetAsync(count, 0, (size_t)tiles * sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
     const bool cvec = h.x_is_b && !(reinterpret_cast<uintptr_t>(h.C) & 15) && h.ldc % 4 == 0;
     SkArgs a{R, Yrows, h.alpha, h.beta, h.C, h.ldc, h.x_is_b ? 1 : 0, xkc ? 1 : 0, cvec ? 1 : 0,
              slots, count};
     SkPart P{tiles * nkb, nkb, G};
-    tc_skinny_kernel<MODE><<<G, SK_THREADS, CF::SMEM_BYTES, s>>>(
-        mx, my, a, P, h.dstate, (uint64_t)h.wait_limit * 1000ull);
+    // launched as the programmatic dependent of the pack of Y before it: the
+    // kernel's set-up and first X loads overlap the pack's tail (the
+    // producer waits for the pack before it reads Y)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(SK_THREADS);
+    cfg.dynamicSmemBytes = CF::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, tc_skinny_kernel<MODE>, mx, my, a, P, h.dstate,
+                           (uint64_t)h.wait_limit * 1000ull);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -571,6 +618,14 @@ bool skinny_shape(int mode, int64_t m, int64_t n, int64_t k) {
 }
 
 bool skinny_x_is_b(int64_t m, int64_t n) { return m <= SK_YN && n >= m; }
+
+cudaError_t skinny_clear(const SkinnyArgs &a, cudaStream_t s) {
+    const int64_t R = a.x_is_b ? a.n : a.m;
+    const int64_t tiles = (R + BM - 1) / BM;
+    unsigned *count = reinterpret_cast<unsigned *>(
+        static_cast<char *>(a.ws) + (size_t)(tiles + kSkinnyMaxCtas) * SK_SLOT * sizeof(float));
+    return cudaMemsetAsync(count, 0, (size_t)tiles * sizeof(unsigned), s);
+}
 
 bool skinny_supported(int mode, int64_t m, int64_t n, int64_t k, const float *A, int64_t lda,
                       const float *B, int64_t ldb) {
