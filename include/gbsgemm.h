@@ -356,7 +356,7 @@ GB_API int gb_set_wait_limit(gb_handle_t h, int64_t microseconds);
 GB_API int gb_set_fused_split(gb_handle_t h, int enable);
 
 /* Whether gb_sgemm (and the calls built on it) may take the skinny-product
- * kernel (default: 1). It applies to SPLIT_BF16X3 and SPLIT_BF16X6 (and AUTO
+ * kernel (default: 1). It applies to SPLIT_BF16X3, SPLIT_BF16X6 and SPLIT_BF16X9 (and AUTO
  * when it resolves to one of them) when one side has at most 64 rows
  * (M <= 64 or N <= 64), K >= 256, the long side times K is at least 2^22,
  * promotion is off, and TMA can read the long operand in place (16-byte

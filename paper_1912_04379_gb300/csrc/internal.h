@@ -195,7 +195,7 @@ cudaError_t launch_tc_fused(const FusedArgs &a, cudaStream_t s);
 // FP32 by TMA and split inside the kernel, Y is packed beforehand.
 constexpr int kSkinnyMaxCtas = 256;   // the grid never exceeds this (workspace bound)
 struct SkinnyArgs {
-    int mode;                   // 1 = BF16 x 2 terms, 2 = BF16 x 3 terms
+    int mode;                   // 1 = BF16 x 2 terms, 2 = x 3 terms (6 products), 3 = (9 products)
     bool ta, tb;
     bool x_is_b;                // X = op(B)^T (M short), else X = op(A) (N short)
     int64_t m, n, k;
@@ -210,7 +210,7 @@ struct SkinnyArgs {
     int64_t wait_limit;
     int sm_count;
 };
-// Shapes the skinny kernel takes (BF16 split, one side <= 64 rows, K >= 256
+// Shapes the skinny kernel takes (a BF16 split, one side <= 64 rows, K >= 256
 // and a long X).
 bool skinny_shape(int mode, int64_t m, int64_t n, int64_t k);
 bool skinny_x_is_b(int64_t m, int64_t n);

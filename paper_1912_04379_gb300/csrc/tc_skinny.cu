@@ -50,14 +50,14 @@ constexpr int SK_CONV0 = 6;                    // first converter warp
 constexpr int SK_THREADS = (SK_CONV0 + SK_NCONV) * 32;
 constexpr int SK_SLOT = BM * SK_YN;            // floats in one partial-sum slot
 
-template <int MODE>                            // 1: BF16 x 2 terms, 2: BF16 x 3 terms
+template <int MODE>     // 1: BF16 x 2 terms, 3 products; 2: x 3 terms, 6 products; 3: x 3 terms, 9
 struct SkCfg {
-    static constexpr int PARTS = MODE == 2 ? 3 : 2;
+    static constexpr int PARTS = MODE >= 2 ? 3 : 2;
     // k per stage: KH sub-blocks of 32 (the TMA boxes and the 64-byte rows
     // of the Y terms are 32 k wide); two for the two-term split, whose
     // narrower accumulators leave tensor memory for 64-k stages: per k, the
     // MMA issuer's waits and commits then cost half
-    static constexpr int KH = MODE == 2 ? 1 : 2;
+    static constexpr int KH = MODE >= 2 ? 1 : 2;
     static constexpr int SKB = KH * FBK;
     static constexpr int F32_BYTES = BM * FBK * 4;          // one FP32 X sub-tile
     static constexpr int X_BYTES = KH * F32_BYTES;
@@ -65,13 +65,13 @@ struct SkCfg {
     // A shared-memory stage: the FP32 X sub-tiles (h at +h*F32_BYTES), then
     // the Y terms (sub-block h, term p at +X_BYTES + (h*PARTS + p)*Y_OP).
     static constexpr int STAGE = X_BYTES + KH * PARTS * Y_OP;
-    static constexpr int STAGES = MODE == 2 ? 8 : 4;
+    static constexpr int STAGES = MODE >= 2 ? 8 : 4;
     // TMEM: two accumulators of PARTS column groups (products with Y_0,
     // Y_1, ...), then the X-term stages: sub-block h, term p at 16 (h*PARTS
     // + p) columns (32 BF16 of K, two per column)
     static constexpr int ACC_COLS = PARTS * SK_YN;
     static constexpr int XCOLS = KH * PARTS * (FBK / 2);
-    static constexpr int T_STAGES = MODE == 2 ? 2 : 4;
+    static constexpr int T_STAGES = MODE >= 2 ? 2 : 4;
     static constexpr int TMEM_COLS = 512;
     // equal ring lengths: one MMA commit per k-block releases both stages
     static constexpr bool SHARED_RELEASE = T_STAGES == STAGES;
@@ -327,8 +327,9 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                     }
                     tc_fence_after();
                     const uint32_t xt = tmem_base + (uint32_t)(2 * CF::ACC_COLS + st * CF::XCOLS);
-                    // X term i (from TMEM) with Y terms 0 .. PARTS-1-i stacked
-                    // along N: the pairs of the split (i + j <= PARTS - 1)
+                    // X term i (from TMEM) with Y terms 0 .. NY(i)-1 stacked along
+                    // N: the pairs of the split (i + j <= PARTS - 1; all nine
+                    // pairs for BF16 x 3 terms with 9 products)
 #pragma unroll
                     for (int h = 0; h < CF::KH; ++h)
 #pragma unroll
@@ -339,9 +340,10 @@ tc_skinny_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                             const uint32_t xa = xt + (uint32_t)((h * CF::PARTS + i) * (FBK / 2) + ks * 8);
                             const uint64_t yd = smem_desc<64>(base + s * CF::STAGE + CF::X_BYTES +
                                                               h * CF::PARTS * CF::Y_OP + ks * 32);
-                            if (CF::PARTS - i == 3)
+                            const int ny = MODE == 3 ? CF::PARTS : CF::PARTS - i;
+                            if (ny == 3)
                                 mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, 3 * SK_YN>(), accumulate);
-                            else if (CF::PARTS - i == 2)
+                            else if (ny == 2)
                                 mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, 2 * SK_YN>(), accumulate);
                             else
                                 mma_issue_ta(d_tmem, xa, yd, instr_desc<kFmtBF16, SK_YN>(), accumulate);
@@ -610,7 +612,7 @@ size_t skinny_ws_bytes(int64_t R) {
 }
 
 bool skinny_shape(int mode, int64_t m, int64_t n, int64_t k) {
-    if (mode != 1 && mode != 2) return false;
+    if (mode < 1 || mode > 3) return false;
     if ((m > SK_YN && n > SK_YN) || k < 256) return false;
     const int64_t R = m > n ? m : n;
     if (R * k < ((int64_t)1 << 22)) return false;
@@ -637,6 +639,7 @@ cudaError_t launch_tc_skinny(const SkinnyArgs &a, cudaStream_t s) {
     switch (a.mode) {
         case 1: return launch_skinny_mode<1>(a, s);
         case 2: return launch_skinny_mode<2>(a, s);
+        case 3: return launch_skinny_mode<3>(a, s);
         default: return cudaErrorNotSupported;
     }
 }

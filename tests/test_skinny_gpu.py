@@ -69,7 +69,7 @@ def _kernel_names(fn):
     return names
 
 
-@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6", "bf16x9"))
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_skinny_within_bound(handles, algo, shape):
     on, off = handles
@@ -98,7 +98,7 @@ def test_skinny_repeated_runs_identical(handles, algo):
 
 
 @pytest.mark.parametrize("ta,tb", TRANS)
-@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6", "bf16x9"))
 def test_skinny_all_transposes(handles, algo, ta, tb):
     on, _ = handles
     for (m, n, k) in ((40, 2100, 2500), (2100, 40, 2500)):
@@ -108,7 +108,7 @@ def test_skinny_all_transposes(handles, algo, ta, tb):
         check_padding(p, got)
 
 
-@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6"))
+@pytest.mark.parametrize("algo", ("bf16x3", "bf16x6", "bf16x9"))
 def test_skinny_integer_bit_exact(handles, algo):
     on, _ = handles
     for (ta, tb, m, n, k) in (("N", "N", 64, 4000, 4099), ("T", "T", 3000, 33, 3000)):
