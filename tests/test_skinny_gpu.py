@@ -223,3 +223,45 @@ def test_skinny_bounded_wait_expires_cleanly():
     q = aligned_problem("N", "N", 64, 3000, 1100, 1.0, 0.0, seed=24)
     got = _run(q, "bf16x3", h)
     assert_within_bound(q, got, algo="bf16x3")
+
+
+def _vec_c_problem(ta, tb, m, n, k, alpha, beta, seed):
+    """As aligned_problem, but C's leading dimension is a multiple of 4 (C
+    rows 16-byte aligned): the float4 store path when op(A) is the short
+    side."""
+    p = aligned_problem(ta, tb, m, n, k, alpha, beta, seed)
+    ldc = (m + 3) // 4 * 4 + 4
+    C = wl.uniform(np.random.default_rng(seed + 1), m, n, ldc, pad=wl.CANARY)
+    return wl.Problem(p.ta, p.tb, p.m, p.n, p.k, p.alpha, p.beta, p.A, p.lda, p.B, p.ldb, C,
+                      C.shape[0])
+
+
+@pytest.mark.parametrize("beta", (0.0, -0.5))
+@pytest.mark.parametrize("m", (64, 50, 37))
+def test_skinny_vector_c_stores(handles, m, beta):
+    """C rows 16-byte aligned (ldc % 4 == 0): whole float4 stores, and a
+    scalar tail when M is not a multiple of 4; beta != 0 reads C the same
+    way. Both a whole-tile and a shared-tile (reduced) store occur (K long
+    enough to split tiles over several CTAs)."""
+    on, off = handles
+    p = _vec_c_problem("N", "N", m, 6000, 3000, 1.25, beta, seed=300 + m)
+    assert p.ldc % 4 == 0
+    got = _run(p, "bf16x3", on)
+    assert_within_bound(p, got, algo="bf16x3")
+    check_padding(p, got)
+    ref = _run(p, "bf16x3", off)
+    assert_within_bound(p, ref, algo="bf16x3")
+
+
+@pytest.mark.parametrize("shape", [(64, 8192, 255), (65, 8192, 2048), (100, 100, 100000)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_skinny_route_boundaries(handles, shape):
+    """Just outside the skinny rule (K < 256; both sides over 64): the
+    two-pass path runs whatever the switch says, so both handles give the
+    same bits; both meet the bound."""
+    on, off = handles
+    m, n, k = shape
+    p = aligned_problem("N", "N", m, n, k, 1.0, 0.0, seed=330 + m)
+    a, b = _run(p, "bf16x6", on), _run(p, "bf16x6", off)
+    assert np.array_equal(a, b)
+    assert_within_bound(p, a, algo="bf16x6")
