@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "split_common.cuh"
 
 namespace gb {
 namespace {
@@ -218,10 +219,16 @@ trsm_leaf_prep_kernel(int64_t ms, const float *__restrict__ A, int64_t lda, int 
 
 // The leaf at rows (left) or columns (right) [r0, r0 + s) of B, its L' and D
 // prepared in prep (kPrepFloats, 16-byte aligned).
+// With xp non-null the solved rows (left) or columns (right) are also
+// split into their three BF16 terms and stored into the packed copy of X:
+// term p of vector v, position r0 + i at xp[p * xps + v * xkpad + r0 + i]
+// (the layout of a packed GEMM operand whose K index is the row (left) or
+// column (right) of X), so that the updates read X without a pack pass.
 template <bool LEFT>
 __global__ void __launch_bounds__(kLeafThreads, 1)
 trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__restrict__ prep,
-                 float *__restrict__ B, int64_t ldb) {
+                 float *__restrict__ B, int64_t ldb, __nv_bfloat16 *__restrict__ xp,
+                 int64_t xkpad, int64_t xps) {
     extern __shared__ __align__(16) float smem[];
     float *S = smem;                      // L', at colbase(j) + i
     float *D = S + kSFloats;              // D[i] = 1 / L'(i, i)
@@ -348,6 +355,25 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             B[(v0 + lane) + (r0 + col) * ldb] = X[lane * kXS + i];
         }
     }
+    if (xp) {
+        // one vector per warp at a time, consecutive lanes on consecutive
+        // rows (or columns) of the leaf: contiguous in the packed copy
+#pragma unroll 1
+        for (int v = warp; v < kVecs; v += kLeafWarps) {
+            if (v0 + v >= nvec) break;
+            __nv_bfloat16 *xv = xp + (v0 + v) * xkpad + r0;
+#pragma unroll
+            for (int k = 0; k < kTLeaf / 32; ++k) {
+                const int i = lane + 32 * k;
+                if (i >= s) break;
+                const int pos = rev ? s - 1 - i : i;
+                __nv_bfloat16 t[3];
+                split_bf16<3>(X[v * kXS + i], t);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) xv[p * xps + pos] = t[p];
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------- host
@@ -363,15 +389,34 @@ size_t prep_smem_bytes() { return (size_t)kHalfLeaf * kRawStride * sizeof(float)
 
 // STRSM workspace: the GEMM updates' area first (256-byte rounded), then
 // every leaf's prepared L' and D.
+// STRSM workspace: the GEMM updates' area first (256-byte rounded), then
+// every leaf's prepared L' and D, then (pack-once updates) op(A) and X in
+// split form: three BF16 terms each, rows of kpad = split_kpad(BF16 x 3, ms)
+// elements, ms rows for op(A) and vecs rows (columns of B on the left, rows
+// on the right) for X.
 struct TrsmWorkspace {
-    size_t gemm_bytes, prep_offset, total;
+    size_t gemm_bytes, prep_offset, ap_offset, xp_offset, total;
+    int64_t kpad;
 };
-TrsmWorkspace trsm_workspace(size_t gemm_need, int64_t ms) {
+TrsmWorkspace trsm_workspace(size_t gemm_need, int64_t ms, int64_t vecs, bool pack_once) {
     TrsmWorkspace w;
     w.gemm_bytes = gemm_need;
     w.prep_offset = (gemm_need + 255) / 256 * 256;
-    w.total = w.prep_offset + (size_t)((ms + kTLeaf - 1) / kTLeaf) * kPrepBytes;
+    size_t off = w.prep_offset + (size_t)((ms + kTLeaf - 1) / kTLeaf) * kPrepBytes;
+    w.kpad = pack_once ? split_kpad(2, ms) : 0;
+    w.ap_offset = (off + 255) / 256 * 256;
+    if (pack_once) off = w.ap_offset + 3 * (size_t)ms * (size_t)w.kpad * 2;
+    w.xp_offset = (off + 255) / 256 * 256;
+    if (pack_once) off = w.xp_offset + 3 * (size_t)vecs * (size_t)w.kpad * 2;
+    w.total = off;
     return w;
+}
+
+// Pack-once updates for the BF16 splits (AUTO among them: its updates are
+// BF16 x 2 or x 3 terms except for K < 9, which keep their own gb_sgemm).
+bool trsm_pack_once(gb_algo_t algo) {
+    return algo == GB_ALGO_AUTO || algo == GB_ALGO_SPLIT_BF16X3 || algo == GB_ALGO_SPLIT_BF16X6 ||
+           algo == GB_ALGO_SPLIT_BF16X9;
 }
 
 bool is_t(char c) { return c == 'T' || c == 't' || c == 'C' || c == 'c'; }
@@ -477,7 +522,38 @@ struct TrsmCtx {
     int64_t ldb;
     int sm_count;
     const float *prep;      // every leaf's L' and D (kPrepFloats per 256 rows)
+    // Pack-once updates (BF16 splits): op(A) split and packed once (ap: as
+    // the updates' op(A) on the left, as their op(B) on the right), and X
+    // in the same split form, written by the leaves (xp); both rows of
+    // xkpad elements, three terms. Null: each update is one gb_sgemm.
+    bool pack_once = false;
+    const __nv_bfloat16 *ap = nullptr;
+    __nv_bfloat16 *xp = nullptr;
+    int64_t xkpad = 0;
 };
+
+// One update, C -= op(A)_gemm op(B)_gemm with K = kk. With pack-once updates
+// and a BF16 split for this K: a compute launch on views of the packed op(A)
+// (rows a_row0.. on the left; as op(B), columns b_row0.. on the right) and
+// the packed X, K range [k0, k0 + kk). Otherwise one gb_sgemm (or, when
+// probing, its workspace need).
+int trsm_gemm(const TrsmCtx &c, char ta, char tb, int64_t M, int64_t N, int64_t kk,
+              const float *A, int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc,
+              int64_t a_row0, int64_t b_row0, int64_t k0) {
+    if (c.pack_once) {
+        const int mode = split_mode(resolve_algo(c.g.algo, kk));
+        if (mode >= 1 && mode <= 3) {
+            if (c.g.ws_need) return GB_OK;
+            const int64_t ms = c.left ? c.m : c.n, vecs = c.left ? c.n : c.m;
+            const void *Ap = c.left ? (const void *)c.ap : (const void *)c.xp;
+            const void *Bp = c.left ? (const void *)c.xp : (const void *)c.ap;
+            return compute_packed_view(c.g.h, mode, M, N, kk, -1.f, Ap, c.left ? ms : vecs, a_row0,
+                                       Bp, c.left ? vecs : ms, b_row0, 1.f, C, ldc, c.g.s, k0,
+                                       c.xkpad);
+        }
+    }
+    return c.g(ta, tb, M, N, kk, -1.f, A, lda, B, ldb, 1.f, C, ldc);
+}
 
 // op(A)[R0.., S0..] as a GEMM operand (pointer, trans flag)
 inline const float *opa_block(const TrsmCtx &c, int64_t R0, int64_t S0, char *t) {
@@ -493,10 +569,10 @@ int trsm_leaf(const TrsmCtx &c, int64_t r0, int64_t s) {
     const float *prep = c.prep + (r0 / kTLeaf) * kPrepFloats;
     if (c.left)
         trsm_leaf_kernel<true><<<(unsigned)blocks, kLeafThreads, smem, c.g.s>>>(
-            (int)s, c.n, r0, c.tlower, prep, c.B, c.ldb);
+            (int)s, c.n, r0, c.tlower, prep, c.B, c.ldb, c.xp, c.xkpad, vecs * c.xkpad);
     else
         trsm_leaf_kernel<false><<<(unsigned)blocks, kLeafThreads, smem, c.g.s>>>(
-            (int)s, c.m, r0, c.tlower, prep, c.B, c.ldb);
+            (int)s, c.m, r0, c.tlower, prep, c.B, c.ldb, c.xp, c.xkpad, vecs * c.xkpad);
     return cudaGetLastError() == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
@@ -513,10 +589,12 @@ int trsm_rec(const TrsmCtx &c, int64_t r0, int64_t mm) {
         if (rc) return rc;
         if (fwd) {
             const float *op = opa_block(c, b, a, &t);
-            rc = c.g(t, 'N', m2, c.n, m1, -1.f, op, c.lda, c.B + a, c.ldb, 1.f, c.B + b, c.ldb);
+            rc = trsm_gemm(c, t, 'N', m2, c.n, m1, op, c.lda, c.B + a, c.ldb, c.B + b, c.ldb,
+                           b, 0, a);
         } else {
             const float *op = opa_block(c, a, b, &t);
-            rc = c.g(t, 'N', m1, c.n, m2, -1.f, op, c.lda, c.B + b, c.ldb, 1.f, c.B + a, c.ldb);
+            rc = trsm_gemm(c, t, 'N', m1, c.n, m2, op, c.lda, c.B + b, c.ldb, c.B + a, c.ldb,
+                           a, 0, b);
         }
         if (rc) return rc;
         return fwd ? trsm_rec(c, b, m2) : trsm_rec(c, a, m1);
@@ -526,12 +604,12 @@ int trsm_rec(const TrsmCtx &c, int64_t r0, int64_t mm) {
     if (rc) return rc;
     if (fwd) {   // B[:, 2] -= X[:, 1] op(A)[1, 2]
         const float *op = opa_block(c, a, b, &t);
-        rc = c.g('N', t, c.m, m2, m1, -1.f, c.B + a * c.ldb, c.ldb, op, c.lda, 1.f,
-                 c.B + b * c.ldb, c.ldb);
+        rc = trsm_gemm(c, 'N', t, c.m, m2, m1, c.B + a * c.ldb, c.ldb, op, c.lda,
+                       c.B + b * c.ldb, c.ldb, 0, b, a);
     } else {     // B[:, 1] -= X[:, 2] op(A)[2, 1]
         const float *op = opa_block(c, b, a, &t);
-        rc = c.g('N', t, c.m, m1, m2, -1.f, c.B + b * c.ldb, c.ldb, op, c.lda, 1.f,
-                 c.B + a * c.ldb, c.ldb);
+        rc = trsm_gemm(c, 'N', t, c.m, m1, m2, c.B + b * c.ldb, c.ldb, op, c.lda,
+                       c.B + a * c.ldb, c.ldb, 0, a, b);
     }
     if (rc) return rc;
     return fwd ? trsm_rec(c, b, m2) : trsm_rec(c, a, m1);
@@ -672,9 +750,10 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
         *bytes = 0;
         return GB_OK;
     }
+    c.pack_once = trsm_pack_once(algo);
     rc = trsm_rec(c, 0, is_l(side) ? m : n);
     if (rc) return rc;
-    *bytes = trsm_workspace(need, is_l(side) ? m : n).total;
+    *bytes = trsm_workspace(need, is_l(side) ? m : n, is_l(side) ? n : m, c.pack_once).total;
     return GB_OK;
 }
 
@@ -696,10 +775,11 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
     size_t need = 0;
     GemmRunner probe{nullptr, algo, nullptr, 0, nullptr, &need};
     TrsmCtx pc = trsm_ctx(probe, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
-    const int64_t ms = is_l(side) ? m : n;
+    pc.pack_once = trsm_pack_once(algo);
+    const int64_t ms = is_l(side) ? m : n, vecs = is_l(side) ? n : m;
     rc = trsm_rec(pc, 0, ms);
     if (rc) return rc;
-    const TrsmWorkspace w = trsm_workspace(need, ms);
+    const TrsmWorkspace w = trsm_workspace(need, ms, vecs, pc.pack_once);
     if (ws_bytes < w.total || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 15))
         return GB_ERR_WORKSPACE;
     if (!leaf_attrs_set(h->device)) return GB_ERR_CUDA;
@@ -716,6 +796,18 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
         trsm_leaf_prep_kernel<false><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
             ms, A, lda, c.trans, c.tlower, c.unit, prep);
     if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
+    if (pc.pack_once) {
+        // op(A) split once: as the updates' op(A) (left) or op(B) (right);
+        // the leaves then write X in the same form
+        char *ws = static_cast<char *>(workspace);
+        c.pack_once = true;
+        c.ap = reinterpret_cast<const __nv_bfloat16 *>(ws + w.ap_offset);
+        c.xp = reinterpret_cast<__nv_bfloat16 *>(ws + w.xp_offset);
+        c.xkpad = w.kpad;
+        if (pack_operand_rows(2, c.left, c.trans, ms, ms, A, lda, ws + w.ap_offset, ms, 0, s) !=
+            cudaSuccess)
+            return GB_ERR_CUDA;
+    }
     return trsm_rec(c, 0, ms);
 }
 

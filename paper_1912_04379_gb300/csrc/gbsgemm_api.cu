@@ -187,16 +187,20 @@ size_t gb::packed_operand_bytes(int mode, bool a_side, int64_t mn, int64_t k) {
 int gb::compute_packed_view(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k,
                             float alpha, const void *Ap, int64_t a_rows, int64_t a_row0,
                             const void *Bp, int64_t b_rows, int64_t b_row0, float beta, float *C,
-                            int64_t ldc, cudaStream_t s) {
+                            int64_t ldc, cudaStream_t s, int64_t k0, int64_t kstride) {
     if (mode == 4 && (b_row0 % 256) != 0) return GB_ERR_ARG;   // one scaling block per tile
-    const int64_t kpad = split_kpad(mode, k);
+    if (mode == 4 && (k0 != 0 || kstride != 0)) return GB_ERR_ARG;   // maxima are per whole row
+    const int64_t kpad = kstride > 0 ? kstride : split_kpad(mode, k);
     const int64_t eb = split_elem_bytes(mode);
+    // TMA needs 16-byte aligned rows: the row stride and the K offset in
+    // whole 16-byte groups (the packing pads rows to that)
+    if (kpad < k0 + k || (kpad * eb) % 16 != 0 || (k0 * eb) % 16 != 0) return GB_ERR_ARG;
     TcArgs t{};
     t.mode = mode;
     t.m = m; t.n = n; t.k = k; t.kpad = kpad;
     t.alpha = alpha; t.beta = beta;
-    t.Ap = static_cast<const char *>(Ap) + a_row0 * kpad * eb;
-    t.Bp = static_cast<const char *>(Bp) + b_row0 * kpad * eb;
+    t.Ap = static_cast<const char *>(Ap) + (a_row0 * kpad + k0) * eb;
+    t.Bp = static_cast<const char *>(Bp) + (b_row0 * kpad + k0) * eb;
     t.a_part_stride = a_rows * kpad; t.b_part_stride = b_rows * kpad;
     t.C = C; t.ldc = ldc;
     t.splits = 1;

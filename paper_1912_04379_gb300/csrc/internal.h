@@ -294,11 +294,14 @@ int sgemm_epi(gb_handle_t h, gb_algo_t algo, char ta, char tb, int64_t m, int64_
 // C <- alpha op(A)[a_row0 .. a_row0+m) op(B)[:, b_row0 .. b_row0+n) + beta C,
 // from whole packed operands of a_rows rows (op(A)) and b_rows columns
 // (op(B)), as gb_sgemm_pack laid them out; no split-K. Mode 4 needs b_row0 a
-// multiple of 256 (its column-block scaling). Returns a GB_* status.
+// multiple of 256 (its column-block scaling). k0 / kstride (0: none / the
+// operand's own padded K) take a K range [k0, k0 + k) of operands packed
+// with row stride kstride (the K offset and stride in whole 16-byte groups;
+// not mode 4). Returns a GB_* status.
 int compute_packed_view(gb_handle_t h, int mode, int64_t m, int64_t n, int64_t k, float alpha,
                         const void *Ap, int64_t a_rows, int64_t a_row0, const void *Bp,
                         int64_t b_rows, int64_t b_row0, float beta, float *C, int64_t ldc,
-                        cudaStream_t s);
+                        cudaStream_t s, int64_t k0 = 0, int64_t kstride = 0);
 // Split + pack rows [row0, row0+rows) of op(X) (a_side) or op(B)^T into the
 // packed operand of total_rows rows at `packed` (layout of gb_sgemm_pack).
 cudaError_t pack_operand_rows(int mode, bool a_side, bool trans, int64_t rows, int64_t k,
