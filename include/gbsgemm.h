@@ -558,7 +558,10 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
 /* Workspace bytes of gb_strsm with these arguments: the GEMM updates' need
  * (256-byte rounded) plus 197,632 bytes per 256 rows of A's diagonal, where
  * each diagonal block's triangle and diagonal reciprocals are laid out once
- * per call for the substitution kernels. */
+ * per call for the substitution kernels; for AUTO and the BF16 splits also
+ * op(A) and X in split form (three BF16 terms each: 6 * s * kpad bytes for
+ * op(A) and 6 * v * kpad for X, s = m (side 'L') or n, v the other
+ * dimension, kpad = s rounded up to a multiple of 8). */
 GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char transa, char diag,
                                    int64_t m, int64_t n, size_t *bytes);
 
@@ -569,10 +572,14 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
  * alpha first; alpha = 0 sets B to 0 without reading A or B. A singular A
  * gives infinities or NaNs, as in BLAS. Negative returns are BLAS argument
  * positions (1 side, 2 uplo, 3 transa, 4 diag, 5 m, 6 n, 9 lda, 11 ldb).
- * Recursion by halving: each level's off-diagonal block update is one
- * gb_sgemm call with `algo` (alpha = -1, beta = 1), and the diagonal blocks
- * (at most 256 rows) are solved by substitution in FP32, with each diagonal
- * entry's reciprocal rounded once. `workspace` (16-byte aligned, at least
+ * Recursion by halving: each level's off-diagonal block update is a GEMM
+ * with `algo` (alpha = -1, beta = 1), and the diagonal blocks (at most 256
+ * rows) are solved by substitution in FP32, with each diagonal entry's
+ * reciprocal rounded once. For AUTO and the BF16 splits, op(A) is split
+ * once per call and the substitution kernels also write X in split form, so
+ * each update is one tensor-core launch on views of the two (the same
+ * terms and products as a gb_sgemm of the blocks); for the other
+ * algorithms each update is one gb_sgemm call. `workspace` (16-byte aligned, at least
  * gb_strsm_workspace_size bytes) is always needed when m, n > 0 and alpha != 0;
  * otherwise GB_ERR_WORKSPACE. */
 GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
