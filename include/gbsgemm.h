@@ -579,7 +579,14 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
  * once per call and the substitution kernels also write X in split form, so
  * each update is one tensor-core launch on views of the two (the same
  * terms and products as a gb_sgemm of the blocks); for the other
- * algorithms each update is one gb_sgemm call. `workspace` (16-byte aligned, at least
+ * algorithms each update is one gb_sgemm call. The handle keeps the last
+ * call's launches as an instantiated CUDA graph: a call with the same
+ * arguments (pointers included) and handle settings replays it, any other
+ * call captures anew (on a stream of the handle; the first call of a given
+ * set of arguments therefore costs the capture too). Inside the caller's
+ * own stream capture the launches go straight into that capture. The
+ * cache makes a handle unsafe for gb_strsm calls from several host threads
+ * at once. `workspace` (16-byte aligned, at least
  * gb_strsm_workspace_size bytes) is always needed when m, n > 0 and alpha != 0;
  * otherwise GB_ERR_WORKSPACE. */
 GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,

@@ -21,6 +21,8 @@
 // and output blocks are disjoint parts of the same arrays.
 #include <stdint.h>
 
+#include <new>
+
 #include "internal.h"
 #include "split_common.cuh"
 
@@ -757,6 +759,91 @@ GB_API int gb_strsm_workspace_size(gb_algo_t algo, char side, char uplo, char tr
     return GB_OK;
 }
 
+}  // extern "C"
+
+namespace gb {
+namespace {
+
+// The whole of one STRSM call after its checks, enqueued on s.
+int strsm_run(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
+              int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
+              int64_t ldb, void *workspace, const TrsmWorkspace &w, bool pack_once,
+              cudaStream_t s) {
+    const int64_t ms = is_l(side) ? m : n;
+    if (alpha != 1.f && launch_scale_c(m, n, alpha, B, ldb, s) != cudaSuccess) return GB_ERR_CUDA;
+    GemmRunner g{h, algo, workspace, w.gemm_bytes, s, nullptr};
+    TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
+    float *prep = reinterpret_cast<float *>(static_cast<char *>(workspace) + w.prep_offset);
+    c.prep = prep;
+    const dim3 prep_grid((unsigned)((ms + kTLeaf - 1) / kTLeaf), 3);
+    if (c.left)
+        trsm_leaf_prep_kernel<true><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
+            ms, A, lda, c.trans, c.tlower, c.unit, prep);
+    else
+        trsm_leaf_prep_kernel<false><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
+            ms, A, lda, c.trans, c.tlower, c.unit, prep);
+    if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
+    if (pack_once) {
+        // op(A) split once: as the updates' op(A) (left) or op(B) (right);
+        // the leaves then write X in the same form
+        char *ws = static_cast<char *>(workspace);
+        c.pack_once = true;
+        c.ap = reinterpret_cast<const __nv_bfloat16 *>(ws + w.ap_offset);
+        c.xp = reinterpret_cast<__nv_bfloat16 *>(ws + w.xp_offset);
+        c.xkpad = w.kpad;
+        if (pack_operand_rows(2, c.left, c.trans, ms, ms, A, lda, ws + w.ap_offset, ms, 0, s) !=
+            cudaSuccess)
+            return GB_ERR_CUDA;
+    }
+    return trsm_rec(c, 0, ms);
+}
+
+// One STRSM call's arguments and settings, and its launches captured as an
+// instantiated graph: a call with the same arguments (and handle settings)
+// replays the graph instead of issuing its ~70 dependent launches again.
+struct TrsmGraph {
+    bool valid = false;
+    gb_algo_t algo{};
+    char side = 0, uplo = 0, transa = 0, diag = 0;
+    int64_t m = 0, n = 0, lda = 0, ldb = 0;
+    float alpha = 0.f;
+    const float *A = nullptr;
+    float *B = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t promote_k = 0, wait_limit = 0;
+    int rb_override = 0, n_gemm_rb = 0;
+    bool skinny = false, fused = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;      // the stream the launches are captured on
+};
+
+bool same_call(const TrsmGraph &G, gb_handle_t h, gb_algo_t algo, char side, char uplo,
+               char transa, char diag, int64_t m, int64_t n, float alpha, const float *A,
+               int64_t lda, float *B, int64_t ldb, void *ws, size_t ws_bytes) {
+    return G.valid && G.algo == algo && G.side == side && G.uplo == uplo && G.transa == transa &&
+           G.diag == diag && G.m == m && G.n == n && G.alpha == alpha && G.A == A &&
+           G.lda == lda && G.B == B && G.ldb == ldb && G.ws == ws && G.ws_bytes == ws_bytes &&
+           G.promote_k == h->promote_k && G.wait_limit == h->wait_limit &&
+           G.rb_override == h->rb_override && G.n_gemm_rb == h->n_gemm_rb &&
+           G.skinny == h->skinny_split && G.fused == h->fused_split;
+}
+
+}  // namespace
+
+void destroy_trsm_graph(gb_handle_t h) {
+    TrsmGraph *G = static_cast<TrsmGraph *>(h->trsm_graph);
+    if (!G) return;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->cs) cudaStreamDestroy(G->cs);
+    delete G;
+    h->trsm_graph = nullptr;
+}
+
+}  // namespace gb
+
+extern "C" {
+
 GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char transa, char diag,
                     int64_t m, int64_t n, float alpha, const float *A, int64_t lda, float *B,
                     int64_t ldb, void *workspace, size_t ws_bytes, void *stream) {
@@ -783,32 +870,58 @@ GB_API int gb_strsm(gb_handle_t h, gb_algo_t algo, char side, char uplo, char tr
     if (ws_bytes < w.total || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 15))
         return GB_ERR_WORKSPACE;
     if (!leaf_attrs_set(h->device)) return GB_ERR_CUDA;
-    if (alpha != 1.f && launch_scale_c(m, n, alpha, B, ldb, s) != cudaSuccess) return GB_ERR_CUDA;
-    GemmRunner g{h, algo, workspace, w.gemm_bytes, s, nullptr};
-    TrsmCtx c = trsm_ctx(g, side, uplo, transa, diag, m, n, A, lda, B, ldb, h->sm_count);
-    float *prep = reinterpret_cast<float *>(static_cast<char *>(workspace) + w.prep_offset);
-    c.prep = prep;
-    const dim3 prep_grid((unsigned)((ms + kTLeaf - 1) / kTLeaf), 3);
-    if (c.left)
-        trsm_leaf_prep_kernel<true><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
-            ms, A, lda, c.trans, c.tlower, c.unit, prep);
-    else
-        trsm_leaf_prep_kernel<false><<<prep_grid, kPrepThreads, prep_smem_bytes(), s>>>(
-            ms, A, lda, c.trans, c.tlower, c.unit, prep);
-    if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
-    if (pc.pack_once) {
-        // op(A) split once: as the updates' op(A) (left) or op(B) (right);
-        // the leaves then write X in the same form
-        char *ws = static_cast<char *>(workspace);
-        c.pack_once = true;
-        c.ap = reinterpret_cast<const __nv_bfloat16 *>(ws + w.ap_offset);
-        c.xp = reinterpret_cast<__nv_bfloat16 *>(ws + w.xp_offset);
-        c.xkpad = w.kpad;
-        if (pack_operand_rows(2, c.left, c.trans, ms, ms, A, lda, ws + w.ap_offset, ms, 0, s) !=
-            cudaSuccess)
-            return GB_ERR_CUDA;
+    // Inside the caller's own stream capture: enqueue the launches there.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return GB_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone)
+        return strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                         w, pc.pack_once, s);
+    // Otherwise replay the cached graph of an identical call, or capture
+    // this one (on the handle's own stream) and keep it.
+    if (!h->trsm_graph) h->trsm_graph = new (std::nothrow) TrsmGraph();
+    TrsmGraph *G = static_cast<TrsmGraph *>(h->trsm_graph);
+    if (!G)
+        return strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                         w, pc.pack_once, s);
+    if (same_call(*G, h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                  ws_bytes))
+        return cudaGraphLaunch(G->exec, s) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+    G->valid = false;
+    if (!G->cs && cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        G->cs = nullptr;
+        return strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                         w, pc.pack_once, s);
     }
-    return trsm_rec(c, 0, ms);
+    if (cudaStreamBeginCapture(G->cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                         w, pc.pack_once, s);
+    }
+    rc = strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace, w,
+                   pc.pack_once, G->cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(G->cs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = rc == GB_OK && ec == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        // nothing ran: enqueue the call directly (it reports its own errors)
+        cudaGetLastError();                 // a failed capture leaves no sticky error
+        if (exec) cudaGraphExecDestroy(exec);
+        return strsm_run(h, algo, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, workspace,
+                         w, pc.pack_once, s);
+    }
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    G->exec = exec;
+    G->valid = true;
+    G->algo = algo; G->side = side; G->uplo = uplo; G->transa = transa; G->diag = diag;
+    G->m = m; G->n = n; G->alpha = alpha; G->A = A; G->lda = lda; G->B = B; G->ldb = ldb;
+    G->ws = workspace; G->ws_bytes = ws_bytes;
+    G->promote_k = h->promote_k; G->wait_limit = h->wait_limit;
+    G->rb_override = h->rb_override; G->n_gemm_rb = h->n_gemm_rb;
+    G->skinny = h->skinny_split; G->fused = h->fused_split;
+    return cudaGraphLaunch(G->exec, s) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -444,6 +444,7 @@ GB_API int gb_destroy(gb_handle_t h) {
     cudaDeviceSynchronize();
     gb::destroy_pipe(h);
     gb::destroy_side(h);
+    gb::destroy_trsm_graph(h);
     cudaFree(h->dstate);
     h->magic = 0;
     delete h;

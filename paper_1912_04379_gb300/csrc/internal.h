@@ -65,9 +65,15 @@ struct gb_handle_s {
     // device address of gb_sgemm_noalloc's static scratch array on this
     // handle's device, looked up by gb_create (null if that failed)
     void *noalloc_scratch;
+    // gb_strsm's last call as an instantiated CUDA graph with its arguments
+    // (blas3.cu), replayed while the arguments repeat; created on first use
+    void *trsm_graph;
 };
 
 namespace gb {
+
+// Frees gb_strsm's cached graph (gb_destroy).
+void destroy_trsm_graph(gb_handle_t h);
 
 constexpr int kHandleMagic = 0x6b5e3a21;
 // Smallest K at which each split meets the plain FP32 bound 2*K*u*D under the
