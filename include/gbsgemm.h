@@ -556,7 +556,7 @@ GB_API int gb_ssyrk(gb_handle_t h, gb_algo_t algo, char uplo, char trans, int64_
                     void *workspace, size_t ws_bytes, void *stream);
 
 /* Workspace bytes of gb_strsm with these arguments: the GEMM updates' need
- * (256-byte rounded) plus 197,632 bytes per 256 rows of A's diagonal, where
+ * (256-byte rounded) plus 140,288 bytes per 256 rows of A's diagonal, where
  * each diagonal block's triangle and diagonal reciprocals are laid out once
  * per call for the substitution kernels; for AUTO and the BF16 splits also
  * op(A) and X in split form (three BF16 terms each: 6 * s * kpad bytes for

@@ -11,8 +11,8 @@
 //          FP32 SIMT kernel (64 x 64 tiles, the tiles above or below the
 //          diagonal skipped).
 //   STRSM  leaves: substitution in one kernel per leaf, the leaf's triangle
-//          in shared memory; 32 columns (left) or rows (right) of B per CTA,
-//          one per lane, each warp owning 16 rows of the solve and taking
+//          in shared memory; 64 columns (left) or rows (right) of B per CTA,
+//          two per lane, each warp owning 16 rows of the solve and taking
 //          the earlier warps' solved rows as named barriers release them.
 //          Leaves depend on one another through the GEMM updates, so they
 //          run in order.
@@ -112,7 +112,7 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 // x' = x when M is lower, else L'(i, j) = M(s-1-i, s-1-j) and x'_i = x_{s-1-i}.
 // Then x'_i = (b'_i - sum over j < i of L'(i, j) x'_j) / L'(i, i), i ascending.
 //
-// A CTA holds 32 vectors (one per lane) and sixteen warps; warp q owns rows
+// A CTA holds 64 vectors (two per lane) and sixteen warps; warp q owns rows
 // [16q, 16q + 16) of every vector in registers. It subtracts the products of
 // each earlier row block p as soon as warp p has solved it (p ascending,
 // columns ascending within a block, so every x'_i accumulates its terms in
@@ -123,26 +123,29 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 // x'_i that depend on it. A 256-row leaf does in one launch what two 128-row
 // leaves and the K = 128 GEMM update between them would do.
 //
-// L' in shared memory keeps what a lower triangle needs, column-major:
-// columns 0..127 with all 256 rows, then columns 128..255 with rows
-// 128..255; L'(i, j) is at colbase(j) + i.
+// L' in shared memory keeps only the 136 16 x 16 blocks (q, p), p <= q, of
+// its lower triangle, block after block in row-block order ((0,0), (1,0),
+// (1,1), (2,0), ...), each column-major: L'(i, j) at lpos(i, j). Warp q
+// reads block (q, p) as 16 columns of 16 contiguous floats.
 constexpr int kBlk = 16;                        // rows per warp block
 constexpr int kLeafWarps = kTLeaf / kBlk;       // 16
 constexpr int kLeafThreads = 32 * kLeafWarps;   // 512
-constexpr int kVecs = 32;                       // vectors per CTA
+constexpr int kVecs = 64;                       // vectors per CTA (two per lane)
+constexpr int kVecsPerLane = kVecs / 32;
 constexpr int kHalfLeaf = kTLeaf / 2;           // 128
 constexpr int kXS = kTLeaf + 4;                 // stride of each vector
-constexpr int kSFloats = kHalfLeaf * kTLeaf + kHalfLeaf * kHalfLeaf;   // 49,152
-constexpr int kPrepFloats = kSFloats + kTLeaf;                          // L' and D
-constexpr size_t kPrepBytes = (size_t)kPrepFloats * sizeof(float);     // 197,632
-constexpr int kRawStride = kHalfLeaf + 1;                               // prep's staging tile
+constexpr int kSFloats = kLeafWarps * (kLeafWarps + 1) / 2 * kBlk * kBlk;   // 34,816
+constexpr int kPrepFloats = kSFloats + kTLeaf;                              // L' and D
+constexpr size_t kPrepBytes = (size_t)kPrepFloats * sizeof(float);         // 140,288
+constexpr int kRawStride = kHalfLeaf + 1;                                   // prep's staging tile
 constexpr int kPrepThreads = 256;
 
-__host__ __device__ constexpr int colbase(int j) {
-    return j < kHalfLeaf ? kTLeaf * j : kSFloats - kHalfLeaf * kTLeaf + kHalfLeaf * j - kHalfLeaf;
+__host__ __device__ constexpr int lblock(int q, int p) { return (q * (q + 1) / 2 + p) * kBlk * kBlk; }
+__host__ __device__ constexpr int lpos(int i, int j) {
+    return lblock(i / kBlk, j / kBlk) + (j % kBlk) * kBlk + i % kBlk;
 }
-static_assert(colbase(kHalfLeaf) + kHalfLeaf == kHalfLeaf * kTLeaf, "L' layout");
-static_assert(colbase(kTLeaf - 1) + kTLeaf == kSFloats, "L' layout");
+static_assert(lpos(kTLeaf - 1, kTLeaf - 1) + 1 == kSFloats, "L' layout");
+static_assert(kPrepBytes % 16 == 0, "L' and D are copied in 16-byte pieces");
 
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -160,7 +163,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Builds every leaf's L' and D once per call into prep[b * kPrepFloats ..]
 // (leaf b = rows [256 b, 256 b + s) of op(A)'s diagonal): L'(i, j) at
-// colbase(j) + i for j < i < s and 0 elsewhere, then D[i] = 1 / L'(i, i) (1
+// lpos(i, j) for j < i < s and 0 elsewhere in the stored blocks, then D[i] = 1 / L'(i, i) (1
 // for a unit diagonal and for padding rows). One CTA per leaf and 128 x 128
 // region of L' (blockIdx.y: rows/columns 0-127, rows 128-255 x columns
 // 0-127, rows/columns 128-255). The stored (sr, sc) is M(sr, sc), or M(sc, sr)
@@ -200,13 +203,14 @@ trsm_leaf_prep_kernel(int64_t ms, const float *__restrict__ A, int64_t lda, int 
     float *out = prep + (int64_t)blockIdx.x * kPrepFloats;
     for (int e = tid; e < kHalfLeaf * kHalfLeaf; e += kPrepThreads) {
         const int i = i0 + (e & (kHalfLeaf - 1)), j = j0 + e / kHalfLeaf;
+        if (j / kBlk > i / kBlk) continue;         // above the diagonal blocks: not stored
         float v = 0.f;
         if (i < s && j < i) {
             const int mi = rev ? s - 1 - i : i, mj = rev ? s - 1 - j : j;
             const int sr = swap ? mj : mi, sc = swap ? mi : mj;
             v = R[(sc - sc0) * kRawStride + (sr - sr0)];
         }
-        out[colbase(j) + i] = v;
+        out[lpos(i, j)] = v;
     }
     if (ib == jb && tid < kHalfLeaf) {
         const int i = i0 + tid;
@@ -232,7 +236,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                  float *__restrict__ B, int64_t ldb, __nv_bfloat16 *__restrict__ xp,
                  int64_t xkpad, int64_t xps) {
     extern __shared__ __align__(16) float smem[];
-    float *S = smem;                      // L', at colbase(j) + i
+    float *S = smem;                      // L', at lpos(i, j)
     float *D = S + kSFloats;              // D[i] = 1 / L'(i, i)
     float *X = D + kTLeaf;                // X[v * kXS + i] = b'_i, then x'_i, of vector v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -258,16 +262,23 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
         }
     } else {
 #pragma unroll
-        for (int g = 0; g < kTLeaf / kLeafWarps; g += 4) {
-            float t[4];
+        for (int g = 0; g < kTLeaf / kLeafWarps; g += 2) {
+            float t[2][kVecsPerLane];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 2; ++k) {
                 const int i = warp + kLeafWarps * (g + k);
                 const int col = rev ? s - 1 - i : i;
-                t[k] = (i < s && v0 + lane < nvec) ? B[(v0 + lane) + (r0 + col) * ldb] : 0.f;
+#pragma unroll
+                for (int h = 0; h < kVecsPerLane; ++h) {
+                    const int64_t v = v0 + lane + 32 * h;
+                    t[k][h] = (i < s && v < nvec) ? B[v + (r0 + col) * ldb] : 0.f;
+                }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) X[lane * kXS + warp + kLeafWarps * (g + k)] = t[k];
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int h = 0; h < kVecsPerLane; ++h)
+                    X[(lane + 32 * h) * kXS + warp + kLeafWarps * (g + k)] = t[k][h];
         }
     }
     cp_async_wait_all();
@@ -276,36 +287,44 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
     const int nblk = (s + kBlk - 1) / kBlk;
     const int q = warp;
     if (q < nblk) {                       // warp-uniform: every lane reaches each barrier
-        float x[kBlk];
-        const float4 *xq = reinterpret_cast<const float4 *>(X + lane * kXS + q * kBlk);
+        // x[h][r]: row 16q + r of vector lane + 32h
+        float x[kVecsPerLane][kBlk];
 #pragma unroll
-        for (int g = 0; g < kBlk / 4; ++g) {
-            const float4 f = xq[g];
-            x[4 * g] = f.x; x[4 * g + 1] = f.y; x[4 * g + 2] = f.z; x[4 * g + 3] = f.w;
+        for (int h = 0; h < kVecsPerLane; ++h) {
+            const float4 *xq = reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + q * kBlk);
+#pragma unroll
+            for (int g = 0; g < kBlk / 4; ++g) {
+                const float4 f = xq[g];
+                x[h][4 * g] = f.x; x[h][4 * g + 1] = f.y; x[h][4 * g + 2] = f.z; x[h][4 * g + 3] = f.w;
+            }
         }
 #pragma unroll 1
         for (int p = 0; p < q; ++p) {
             named_bar_sync(1 + p, 32 * (nblk - p));       // block p solved
-            float y[kBlk];
-            const float4 *xp = reinterpret_cast<const float4 *>(X + lane * kXS + p * kBlk);
+            float y[kVecsPerLane][kBlk];
 #pragma unroll
-            for (int g = 0; g < kBlk / 4; ++g) {
-                const float4 f = xp[g];
-                y[4 * g] = f.x; y[4 * g + 1] = f.y; y[4 * g + 2] = f.z; y[4 * g + 3] = f.w;
+            for (int h = 0; h < kVecsPerLane; ++h) {
+                const float4 *xp = reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + p * kBlk);
+#pragma unroll
+                for (int g = 0; g < kBlk / 4; ++g) {
+                    const float4 f = xp[g];
+                    y[h][4 * g] = f.x; y[h][4 * g + 1] = f.y; y[h][4 * g + 2] = f.z; y[h][4 * g + 3] = f.w;
+                }
             }
-            // columns p*16 .. p*16+15 of L' (one side of column 128), rows q*16 ..
-            const float *sp = S + colbase(p * kBlk) + q * kBlk;
-            const int cs = p * kBlk < kHalfLeaf ? kTLeaf : kHalfLeaf;
+            const float *sp = S + lblock(q, p);           // block (q, p), column-major
 #pragma unroll
             for (int c = 0; c < kBlk; ++c) {
-                const float4 *lc = reinterpret_cast<const float4 *>(sp + c * cs);
+                const float4 *lc = reinterpret_cast<const float4 *>(sp + c * kBlk);
 #pragma unroll
                 for (int g = 0; g < kBlk / 4; ++g) {
                     const float4 l = lc[g];
-                    x[4 * g] = fmaf(-l.x, y[c], x[4 * g]);
-                    x[4 * g + 1] = fmaf(-l.y, y[c], x[4 * g + 1]);
-                    x[4 * g + 2] = fmaf(-l.z, y[c], x[4 * g + 2]);
-                    x[4 * g + 3] = fmaf(-l.w, y[c], x[4 * g + 3]);
+#pragma unroll
+                    for (int h = 0; h < kVecsPerLane; ++h) {
+                        x[h][4 * g] = fmaf(-l.x, y[h][c], x[h][4 * g]);
+                        x[h][4 * g + 1] = fmaf(-l.y, y[h][c], x[h][4 * g + 1]);
+                        x[h][4 * g + 2] = fmaf(-l.z, y[h][c], x[h][4 * g + 2]);
+                        x[h][4 * g + 3] = fmaf(-l.w, y[h][c], x[h][4 * g + 3]);
+                    }
                 }
             }
         }
@@ -316,25 +335,31 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             const float4 f = dq[g];
             d[4 * g] = f.x; d[4 * g + 1] = f.y; d[4 * g + 2] = f.z; d[4 * g + 3] = f.w;
         }
-        const float *sq = S + colbase(q * kBlk) + q * kBlk;
-        const int cq = q * kBlk < kHalfLeaf ? kTLeaf : kHalfLeaf;
+        const float *sq = S + lblock(q, q);
 #pragma unroll
         for (int j = 0; j < kBlk; ++j) {                  // the diagonal block, column by column
-            x[j] *= d[j];
-            const float4 *lc = reinterpret_cast<const float4 *>(sq + j * cq);
+#pragma unroll
+            for (int h = 0; h < kVecsPerLane; ++h) x[h][j] *= d[j];
+            const float4 *lc = reinterpret_cast<const float4 *>(sq + j * kBlk);
 #pragma unroll
             for (int g = (j + 1) / 4; g < kBlk / 4; ++g) {
                 const float4 l = lc[g];
                 const float lv[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (4 * g + e > j) x[4 * g + e] = fmaf(-lv[e], x[j], x[4 * g + e]);
+                    if (4 * g + e > j)
+#pragma unroll
+                        for (int h = 0; h < kVecsPerLane; ++h)
+                            x[h][4 * g + e] = fmaf(-lv[e], x[h][j], x[h][4 * g + e]);
             }
         }
-        float4 *xo = reinterpret_cast<float4 *>(X + lane * kXS + q * kBlk);
 #pragma unroll
-        for (int g = 0; g < kBlk / 4; ++g)
-            xo[g] = make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
+        for (int h = 0; h < kVecsPerLane; ++h) {
+            float4 *xo = reinterpret_cast<float4 *>(X + (lane + 32 * h) * kXS + q * kBlk);
+#pragma unroll
+            for (int g = 0; g < kBlk / 4; ++g)
+                xo[g] = make_float4(x[h][4 * g], x[h][4 * g + 1], x[h][4 * g + 2], x[h][4 * g + 3]);
+        }
         if (q + 1 < nblk) named_bar_arrive(1 + q, 32 * (nblk - q));
     }
     __syncthreads();
@@ -350,11 +375,16 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                 if (i < s) B[r0 + row + (v0 + v) * ldb] = X[v * kXS + i];
             }
         }
-    } else if (v0 + lane < nvec) {
+    } else {
+#pragma unroll
+        for (int h = 0; h < kVecsPerLane; ++h) {
+            const int64_t v = v0 + lane + 32 * h;
+            if (v >= nvec) break;
 #pragma unroll 4
-        for (int i = warp; i < s; i += kLeafWarps) {
-            const int col = rev ? s - 1 - i : i;
-            B[(v0 + lane) + (r0 + col) * ldb] = X[lane * kXS + i];
+            for (int i = warp; i < s; i += kLeafWarps) {
+                const int col = rev ? s - 1 - i : i;
+                B[v + (r0 + col) * ldb] = X[(lane + 32 * h) * kXS + i];
+            }
         }
     }
     if (xp) {
@@ -381,7 +411,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
 // ------------------------------------------------------------------- host
 
 // Shared memory of a leaf CTA: L' (kSFloats), the diagonal reciprocals
-// (256) and the 32 vectors (kXS floats each): 230,912 bytes.
+// (256) and the 64 vectors (kXS floats each): 206,848 bytes.
 size_t leaf_smem_bytes() {
     return (size_t)(kSFloats + kTLeaf + kVecs * kXS) * sizeof(float);
 }

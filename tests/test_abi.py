@@ -119,14 +119,15 @@ def test_no_handle_without_gpu_or_bad_handle():
 def test_blas3_and_split_k_workspace_sizes():
     """Workspace sizes that follow from the library's layout rules, with no GPU:
     STRSM lays out every 256-row diagonal block's triangle and reciprocals
-    (256 x 128 + 128 x 128 floats, then 256) after the GEMM updates' area
+    (its 136 16 x 16 blocks on or below the diagonal, then 256 floats) after
+    the GEMM updates' area
     (none for SIMT); BF16 x 3 terms keeps 256-column tiles for K > 2048, so a
     64 x 8192 output (32 tiles) with K = 8192 is cut into 4 K-slices of FP32
     partials, while at K = 2048 its 128-column tiles (64 of them) are enough."""
     lib = _lib.load()
     out = ctypes.c_size_t(0)
     simt = _lib.ALGOS["simt"]
-    per_leaf = (256 * 128 + 128 * 128 + 256) * 4
+    per_leaf = (16 * 17 // 2 * 16 * 16 + 256) * 4
     for side, uplo, tr, diag, m, n, leaves in (("L", "L", "N", "N", 300, 50, 2),
                                                ("R", "U", "T", "U", 10, 513, 3),
                                                ("L", "U", "N", "N", 256, 1, 1),
