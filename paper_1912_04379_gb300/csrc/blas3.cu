@@ -24,6 +24,7 @@
 #include <new>
 
 #include "internal.h"
+#include "f32x2.cuh"
 #include "split_common.cuh"
 
 namespace gb {
@@ -125,8 +126,9 @@ syrk_diag_kernel(int64_t n, int64_t k, float alpha, const float *__restrict__ A,
 //
 // L' in shared memory keeps only the 136 16 x 16 blocks (q, p), p <= q, of
 // its lower triangle, block after block in row-block order ((0,0), (1,0),
-// (1,1), (2,0), ...), each column-major: L'(i, j) at lpos(i, j). Warp q
-// reads block (q, p) as 16 columns of 16 contiguous floats.
+// (1,1), (2,0), ...), each column-major: -L'(i, j) at lpos(i, j), negated so
+// that every subtraction is one fused multiply-add and pairs of them one
+// paired FMA. Warp q reads block (q, p) as 16 columns of 16 contiguous floats.
 constexpr int kBlk = 16;                        // rows per warp block
 constexpr int kLeafWarps = kTLeaf / kBlk;       // 16
 constexpr int kLeafThreads = 32 * kLeafWarps;   // 512
@@ -162,7 +164,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Builds every leaf's L' and D once per call into prep[b * kPrepFloats ..]
-// (leaf b = rows [256 b, 256 b + s) of op(A)'s diagonal): L'(i, j) at
+// (leaf b = rows [256 b, 256 b + s) of op(A)'s diagonal): -L'(i, j) at
 // lpos(i, j) for j < i < s and 0 elsewhere in the stored blocks, then D[i] = 1 / L'(i, i) (1
 // for a unit diagonal and for padding rows). One CTA per leaf and 128 x 128
 // region of L' (blockIdx.y: rows/columns 0-127, rows 128-255 x columns
@@ -208,7 +210,7 @@ trsm_leaf_prep_kernel(int64_t ms, const float *__restrict__ A, int64_t lda, int 
         if (i < s && j < i) {
             const int mi = rev ? s - 1 - i : i, mj = rev ? s - 1 - j : j;
             const int sr = swap ? mj : mi, sc = swap ? mi : mj;
-            v = R[(sc - sc0) * kRawStride + (sr - sr0)];
+            v = -R[(sc - sc0) * kRawStride + (sr - sr0)];
         }
         out[lpos(i, j)] = v;
     }
@@ -236,7 +238,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                  float *__restrict__ B, int64_t ldb, __nv_bfloat16 *__restrict__ xp,
                  int64_t xkpad, int64_t xps) {
     extern __shared__ __align__(16) float smem[];
-    float *S = smem;                      // L', at lpos(i, j)
+    float *S = smem;                      // -L', at lpos(i, j)
     float *D = S + kSFloats;              // D[i] = 1 / L'(i, i)
     float *X = D + kTLeaf;                // X[v * kXS + i] = b'_i, then x'_i, of vector v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -287,15 +289,16 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
     const int nblk = (s + kBlk - 1) / kBlk;
     const int q = warp;
     if (q < nblk) {                       // warp-uniform: every lane reaches each barrier
-        // x[h][r]: row 16q + r of vector lane + 32h
-        float x[kVecsPerLane][kBlk];
+        // xx[h][r]: rows (16q + 2r, 16q + 2r + 1) of vector lane + 32h, as
+        // one FP32 pair; each pair of rows takes one paired FMA per term
+        unsigned long long xx[kVecsPerLane][kBlk / 2];
 #pragma unroll
         for (int h = 0; h < kVecsPerLane; ++h) {
-            const float4 *xq = reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + q * kBlk);
+            const ulonglong2 *xq = reinterpret_cast<const ulonglong2 *>(X + (lane + 32 * h) * kXS + q * kBlk);
 #pragma unroll
             for (int g = 0; g < kBlk / 4; ++g) {
-                const float4 f = xq[g];
-                x[h][4 * g] = f.x; x[h][4 * g + 1] = f.y; x[h][4 * g + 2] = f.z; x[h][4 * g + 3] = f.w;
+                const ulonglong2 f = xq[g];
+                xx[h][2 * g] = f.x; xx[h][2 * g + 1] = f.y;
             }
         }
 #pragma unroll 1
@@ -314,20 +317,26 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             const float *sp = S + lblock(q, p);           // block (q, p), column-major
 #pragma unroll
             for (int c = 0; c < kBlk; ++c) {
-                const float4 *lc = reinterpret_cast<const float4 *>(sp + c * kBlk);
+                const ulonglong2 *lc = reinterpret_cast<const ulonglong2 *>(sp + c * kBlk);
+                unsigned long long yy[kVecsPerLane];
+#pragma unroll
+                for (int h = 0; h < kVecsPerLane; ++h) yy[h] = pack2(y[h][c], y[h][c]);
 #pragma unroll
                 for (int g = 0; g < kBlk / 4; ++g) {
-                    const float4 l = lc[g];
+                    const ulonglong2 l = lc[g];            // -L' of rows 4g .. 4g + 3, column c
 #pragma unroll
                     for (int h = 0; h < kVecsPerLane; ++h) {
-                        x[h][4 * g] = fmaf(-l.x, y[h][c], x[h][4 * g]);
-                        x[h][4 * g + 1] = fmaf(-l.y, y[h][c], x[h][4 * g + 1]);
-                        x[h][4 * g + 2] = fmaf(-l.z, y[h][c], x[h][4 * g + 2]);
-                        x[h][4 * g + 3] = fmaf(-l.w, y[h][c], x[h][4 * g + 3]);
+                        ffma2(xx[h][2 * g], l.x, yy[h]);
+                        ffma2(xx[h][2 * g + 1], l.y, yy[h]);
                     }
                 }
             }
         }
+        float x[kVecsPerLane][kBlk];
+#pragma unroll
+        for (int h = 0; h < kVecsPerLane; ++h)
+#pragma unroll
+            for (int r = 0; r < kBlk / 2; ++r) unpack2(xx[h][r], x[h][2 * r], x[h][2 * r + 1]);
         float d[kBlk];
         const float4 *dq = reinterpret_cast<const float4 *>(D + q * kBlk);
 #pragma unroll
@@ -350,7 +359,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                     if (4 * g + e > j)
 #pragma unroll
                         for (int h = 0; h < kVecsPerLane; ++h)
-                            x[h][4 * g + e] = fmaf(-lv[e], x[h][j], x[h][4 * g + e]);
+                            x[h][4 * g + e] = fmaf(lv[e], x[h][j], x[h][4 * g + e]);
             }
         }
 #pragma unroll

@@ -18,6 +18,7 @@
 // matrix is contiguous along M (or N) is read along M; one contiguous along
 // K is read along K and transposed on its way into shared memory. float4
 // loads are used when every address involved is 16-byte aligned.
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace gb {
@@ -27,22 +28,6 @@ constexpr int BM = 128, BN = 128, BK = 8;
 constexpr int NT = 256;
 constexpr int LDS = BM + 4;   // padded shared row (floats); conflict-free transposed stores
 constexpr int LDSB = 2 * BN + 8;   // B panel row: every value stored twice (see below)
-
-// Two IEEE FP32 fused multiply-adds, round to nearest, in one instruction
-// (sm_100 family): d.lo += a.lo * b.lo, d.hi += a.hi * b.hi. Each lane
-// rounds exactly as fmaf does, so results equal the scalar form bit for bit.
-__device__ __forceinline__ void ffma2(unsigned long long &d, unsigned long long a,
-                                      unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-    unsigned long long v;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
-    return v;
-}
 
 // Loads this thread's four elements of a 128 x 8 panel of op(X), where op(X)
 // is (rows x K) and the panel starts at (r0, k0). KC: the stored matrix is
