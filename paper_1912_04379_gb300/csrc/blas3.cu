@@ -240,90 +240,94 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
     extern __shared__ __align__(16) float smem[];
     float *S = smem;                      // -L', at lpos(i, j)
     float *D = S + kSFloats;              // D[i] = 1 / L'(i, i)
-    float *X = D + kTLeaf;                // X[v * kXS + i] = b'_i, then x'_i, of vector v
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *X = D + kTLeaf;                // X[v * kXS + i] = x'_i of vector v, once solved
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
     const bool rev = LEFT ? tlower == 0 : tlower != 0;    // M upper
     const int64_t v0 = (int64_t)blockIdx.x * kVecs;
+    const int nblk = (s + kBlk - 1) / kBlk;
+    if (q >= nblk) return;                // the named barriers count only warps < nblk
 
-    for (int e = tid; e < kPrepFloats / 4; e += kLeafThreads)
-        cp_async16(S + 4 * e, prep + 4 * e);                // L' and D, in flight
-    // b': the leaf's rows (left) or columns (right) of B, coalesced
+    // Every warp loads what it alone reads, so none waits for a CTA-wide
+    // load phase: its row of L' blocks ((q, 0) .. (q, q), contiguous), its 16
+    // reciprocals, and rows [16q, 16q + 16) of its lane's two vectors.
+    {
+        const int b = lblock(q, 0), nchunk = (q + 1) * kBlk * kBlk / 4;
+        for (int k = lane; k < nchunk; k += 32) cp_async16(S + b + 4 * k, prep + b + 4 * k);
+        if (lane < kBlk / 4) cp_async16(D + q * kBlk + 4 * lane, prep + kSFloats + q * kBlk + 4 * lane);
+    }
+    const int i0 = q * kBlk;                          // leaf rows i0 .. i0 + 15
+    const int nv = s - i0 < kBlk ? s - i0 : kBlk;     // of which valid
+    const int b0 = rev ? s - i0 - kBlk : i0;          // stored rows b0 .. b0 + 15 (reversed when rev)
+    const bool full = nv == kBlk;
+    const bool bvec = LEFT && full && !(reinterpret_cast<uintptr_t>(B) & 15) && ldb % 4 == 0 &&
+                      (r0 + b0) % 4 == 0;
+    float x[kVecsPerLane][kBlk];                      // x[h][r]: leaf row i0 + r of vector lane + 32h
     if (LEFT) {
 #pragma unroll
-        for (int g = 0; g < kVecs / kLeafWarps; ++g) {
-            const int v = warp + kLeafWarps * g;
-            float t[kTLeaf / 32];
+        for (int h = 0; h < kVecsPerLane; ++h) {
+            const int64_t v = v0 + lane + 32 * h;
+            const float *bp = B + r0 + v * ldb;
+            if (v >= nvec) {
 #pragma unroll
-            for (int k = 0; k < kTLeaf / 32; ++k) {
-                const int i = lane + 32 * k;
-                const int row = rev ? s - 1 - i : i;
-                t[k] = (i < s && v0 + v < nvec) ? B[r0 + row + (v0 + v) * ldb] : 0.f;
+                for (int r = 0; r < kBlk; ++r) x[h][r] = 0.f;
+            } else if (bvec) {
+                float t[kBlk];
+#pragma unroll
+                for (int g = 0; g < kBlk / 4; ++g) {
+                    const float4 f = *reinterpret_cast<const float4 *>(bp + b0 + 4 * g);
+                    t[4 * g] = f.x; t[4 * g + 1] = f.y; t[4 * g + 2] = f.z; t[4 * g + 3] = f.w;
+                }
+#pragma unroll
+                for (int r = 0; r < kBlk; ++r) x[h][r] = rev ? t[kBlk - 1 - r] : t[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < kBlk; ++r)
+                    x[h][r] = r < nv ? bp[rev ? s - 1 - (i0 + r) : i0 + r] : 0.f;
             }
-#pragma unroll
-            for (int k = 0; k < kTLeaf / 32; ++k) X[v * kXS + lane + 32 * k] = t[k];
         }
     } else {
+        const float *bb = B + (v0 + lane) + r0 * ldb;
+        const int64_t vl = nvec - (v0 + lane);        // vector lane + 32h exists iff 32h < vl
 #pragma unroll
-        for (int g = 0; g < kTLeaf / kLeafWarps; g += 2) {
-            float t[2][kVecsPerLane];
+        for (int r = 0; r < kBlk; ++r) {
+            const int col = rev ? s - 1 - (i0 + r) : i0 + r;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int i = warp + kLeafWarps * (g + k);
-                const int col = rev ? s - 1 - i : i;
-#pragma unroll
-                for (int h = 0; h < kVecsPerLane; ++h) {
-                    const int64_t v = v0 + lane + 32 * h;
-                    t[k][h] = (i < s && v < nvec) ? B[v + (r0 + col) * ldb] : 0.f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int h = 0; h < kVecsPerLane; ++h)
-                    X[(lane + 32 * h) * kXS + warp + kLeafWarps * (g + k)] = t[k][h];
+            for (int h = 0; h < kVecsPerLane; ++h)
+                x[h][r] = (r < nv && 32 * h < vl) ? bb[32 * h + col * ldb] : 0.f;
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+    __syncwarp();
 
-    const int nblk = (s + kBlk - 1) / kBlk;
-    const int q = warp;
-    if (q < nblk) {                       // warp-uniform: every lane reaches each barrier
-        // xx[h][r]: rows (16q + 2r, 16q + 2r + 1) of vector lane + 32h, as
-        // one FP32 pair; each pair of rows takes one paired FMA per term
-        unsigned long long xx[kVecsPerLane][kBlk / 2];
+    // xx[h][r]: rows (2r, 2r + 1) of x[h] as one FP32 pair; each pair of rows
+    // takes one paired FMA per term
+    unsigned long long xx[kVecsPerLane][kBlk / 2];
 #pragma unroll
-        for (int h = 0; h < kVecsPerLane; ++h) {
-            const ulonglong2 *xq = reinterpret_cast<const ulonglong2 *>(X + (lane + 32 * h) * kXS + q * kBlk);
+    for (int h = 0; h < kVecsPerLane; ++h)
 #pragma unroll
-            for (int g = 0; g < kBlk / 4; ++g) {
-                const ulonglong2 f = xq[g];
-                xx[h][2 * g] = f.x; xx[h][2 * g + 1] = f.y;
-            }
-        }
+        for (int r = 0; r < kBlk / 2; ++r) xx[h][r] = pack2(x[h][2 * r], x[h][2 * r + 1]);
 #pragma unroll 1
-        for (int p = 0; p < q; ++p) {
-            named_bar_sync(1 + p, 32 * (nblk - p));       // block p solved
-            float y[kVecsPerLane][kBlk];
+    for (int p = 0; p < q; ++p) {
+        named_bar_sync(1 + p, 32 * (nblk - p));       // block p solved
+        const float *sp = S + lblock(q, p);           // block (q, p), column-major
 #pragma unroll
-            for (int h = 0; h < kVecsPerLane; ++h) {
-                const float4 *xp = reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + p * kBlk);
+        for (int cg = 0; cg < kBlk / 4; ++cg) {
+            float4 yv[kVecsPerLane];                  // x'_j of columns 4cg .. 4cg + 3 of block p
 #pragma unroll
-                for (int g = 0; g < kBlk / 4; ++g) {
-                    const float4 f = xp[g];
-                    y[h][4 * g] = f.x; y[h][4 * g + 1] = f.y; y[h][4 * g + 2] = f.z; y[h][4 * g + 3] = f.w;
-                }
-            }
-            const float *sp = S + lblock(q, p);           // block (q, p), column-major
+            for (int h = 0; h < kVecsPerLane; ++h)
+                yv[h] = *reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + p * kBlk + 4 * cg);
 #pragma unroll
-            for (int c = 0; c < kBlk; ++c) {
-                const ulonglong2 *lc = reinterpret_cast<const ulonglong2 *>(sp + c * kBlk);
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const ulonglong2 *lc = reinterpret_cast<const ulonglong2 *>(sp + (4 * cg + c4) * kBlk);
                 unsigned long long yy[kVecsPerLane];
 #pragma unroll
-                for (int h = 0; h < kVecsPerLane; ++h) yy[h] = pack2(y[h][c], y[h][c]);
+                for (int h = 0; h < kVecsPerLane; ++h) {
+                    const float y = c4 == 0 ? yv[h].x : c4 == 1 ? yv[h].y : c4 == 2 ? yv[h].z : yv[h].w;
+                    yy[h] = pack2(y, y);
+                }
 #pragma unroll
                 for (int g = 0; g < kBlk / 4; ++g) {
-                    const ulonglong2 l = lc[g];            // -L' of rows 4g .. 4g + 3, column c
+                    const ulonglong2 l = lc[g];            // -L' of rows 4g .. 4g + 3
 #pragma unroll
                     for (int h = 0; h < kVecsPerLane; ++h) {
                         ffma2(xx[h][2 * g], l.x, yy[h]);
@@ -332,11 +336,12 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                 }
             }
         }
-        float x[kVecsPerLane][kBlk];
+    }
 #pragma unroll
-        for (int h = 0; h < kVecsPerLane; ++h)
+    for (int h = 0; h < kVecsPerLane; ++h)
 #pragma unroll
-            for (int r = 0; r < kBlk / 2; ++r) unpack2(xx[h][r], x[h][2 * r], x[h][2 * r + 1]);
+        for (int r = 0; r < kBlk / 2; ++r) unpack2(xx[h][r], x[h][2 * r], x[h][2 * r + 1]);
+    {
         float d[kBlk];
         const float4 *dq = reinterpret_cast<const float4 *>(D + q * kBlk);
 #pragma unroll
@@ -362,6 +367,8 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                             x[h][4 * g + e] = fmaf(lv[e], x[h][j], x[h][4 * g + e]);
             }
         }
+    }
+    if (q + 1 < nblk) {                               // the later warps read this block
 #pragma unroll
         for (int h = 0; h < kVecsPerLane; ++h) {
             float4 *xo = reinterpret_cast<float4 *>(X + (lane + 32 * h) * kXS + q * kBlk);
@@ -369,49 +376,84 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
             for (int g = 0; g < kBlk / 4; ++g)
                 xo[g] = make_float4(x[h][4 * g], x[h][4 * g + 1], x[h][4 * g + 2], x[h][4 * g + 3]);
         }
-        if (q + 1 < nblk) named_bar_arrive(1 + q, 32 * (nblk - q));
+        named_bar_arrive(1 + q, 32 * (nblk - q));
     }
-    __syncthreads();
+
+    // The solved rows go out while the later warps are still solving.
     if (LEFT) {
-#pragma unroll
-        for (int g = 0; g < kVecs / kLeafWarps; ++g) {
-            const int v = warp + kLeafWarps * g;
-            if (v0 + v >= nvec) continue;
-#pragma unroll
-            for (int k = 0; k < kTLeaf / 32; ++k) {
-                const int i = lane + 32 * k;
-                const int row = rev ? s - 1 - i : i;
-                if (i < s) B[r0 + row + (v0 + v) * ldb] = X[v * kXS + i];
-            }
-        }
-    } else {
 #pragma unroll
         for (int h = 0; h < kVecsPerLane; ++h) {
             const int64_t v = v0 + lane + 32 * h;
-            if (v >= nvec) break;
-#pragma unroll 4
-            for (int i = warp; i < s; i += kLeafWarps) {
-                const int col = rev ? s - 1 - i : i;
-                B[v + (r0 + col) * ldb] = X[(lane + 32 * h) * kXS + i];
+            if (v >= nvec) continue;
+            float *bp = B + r0 + v * ldb;
+            if (bvec) {
+#pragma unroll
+                for (int g = 0; g < kBlk / 4; ++g) {
+                    float t[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        t[e] = rev ? x[h][kBlk - 1 - (4 * g + e)] : x[h][4 * g + e];
+                    *reinterpret_cast<float4 *>(bp + b0 + 4 * g) = make_float4(t[0], t[1], t[2], t[3]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kBlk; ++r)
+                    if (r < nv) bp[rev ? s - 1 - (i0 + r) : i0 + r] = x[h][r];
             }
+        }
+    } else {
+        float *bb = B + (v0 + lane) + r0 * ldb;
+        const int64_t vl = nvec - (v0 + lane);
+#pragma unroll
+        for (int r = 0; r < kBlk; ++r) {
+            if (r >= nv) break;
+            const int col = rev ? s - 1 - (i0 + r) : i0 + r;
+#pragma unroll
+            for (int h = 0; h < kVecsPerLane; ++h)
+                if (32 * h < vl) bb[32 * h + col * ldb] = x[h][r];
         }
     }
     if (xp) {
-        // one vector per warp at a time, consecutive lanes on consecutive
-        // rows (or columns) of the leaf: contiguous in the packed copy
-#pragma unroll 1
-        for (int v = warp; v < kVecs; v += kLeafWarps) {
-            if (v0 + v >= nvec) break;
-            __nv_bfloat16 *xv = xp + (v0 + v) * xkpad + r0;
+        const bool xvec = full && !(reinterpret_cast<uintptr_t>(xp) & 15) && xkpad % 8 == 0 &&
+                          xps % 8 == 0 && (r0 + b0) % 8 == 0;
 #pragma unroll
-            for (int k = 0; k < kTLeaf / 32; ++k) {
-                const int i = lane + 32 * k;
-                if (i >= s) break;
-                const int pos = rev ? s - 1 - i : i;
+        for (int h = 0; h < kVecsPerLane; ++h) {
+            const int64_t v = v0 + lane + 32 * h;
+            if (v >= nvec) continue;
+            __nv_bfloat16 *xv = xp + v * xkpad + r0;
+            unsigned short tb[3][kBlk];                   // terms' bits, leaf row order
+#pragma unroll
+            for (int r = 0; r < kBlk; ++r) {
                 __nv_bfloat16 t[3];
-                split_bf16<3>(X[v * kXS + i], t);
+                split_bf16<3>(x[h][r], t);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) xv[p * xps + pos] = t[p];
+                for (int p = 0; p < 3; ++p) tb[p][r] = __bfloat16_as_ushort(t[p]);
+            }
+            if (xvec) {
+                // positions b0 .. b0 + 15, two 16-byte stores per term
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        unsigned w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int t0 = 8 * half + 2 * k, t1 = t0 + 1;
+                            const unsigned lo = rev ? tb[p][kBlk - 1 - t0] : tb[p][t0];
+                            const unsigned hi = rev ? tb[p][kBlk - 1 - t1] : tb[p][t1];
+                            w[k] = lo | (hi << 16);
+                        }
+                        *reinterpret_cast<uint4 *>(xv + p * xps + b0 + 8 * half) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kBlk; ++r) {
+                    if (r >= nv) break;
+                    const int pos = rev ? s - 1 - (i0 + r) : i0 + r;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) xv[p * xps + pos] = __ushort_as_bfloat16(tb[p][r]);
+                }
             }
         }
     }
@@ -420,7 +462,7 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
 // ------------------------------------------------------------------- host
 
 // Shared memory of a leaf CTA: L' (kSFloats), the diagonal reciprocals
-// (256) and the 64 vectors (kXS floats each): 206,848 bytes.
+// (256) and the 64 vectors' solved rows (kXS floats each): 206,848 bytes.
 size_t leaf_smem_bytes() {
     return (size_t)(kSFloats + kTLeaf + kVecs * kXS) * sizeof(float);
 }
