@@ -263,26 +263,28 @@ trsm_leaf_kernel(int s, int64_t nvec, int64_t r0, int tlower, const float *__res
                       (r0 + b0) % 4 == 0;
     float x[kVecsPerLane][kBlk];                      // x[h][r]: leaf row i0 + r of vector lane + 32h
     if (LEFT) {
+        // coalesced: half a warp per vector (16 rows = 64 contiguous bytes),
+        // staged through this warp's own rows of X, which nothing else
+        // touches before this warp has solved them
+        const int r = lane & (kBlk - 1);
+        const int64_t brow = r0 + (rev ? s - 1 - (i0 + r) : i0 + r);
+        float *xs = X + i0 + r;
+        float t[kVecs / 2];
+#pragma unroll
+        for (int k = 0; k < kVecs / 2; ++k) {
+            const int64_t v = v0 + 2 * k + (lane >> 4);
+            t[k] = (r < nv && v < nvec) ? B[brow + v * ldb] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kVecs / 2; ++k) xs[(2 * k + (lane >> 4)) * kXS] = t[k];
+        __syncwarp();
 #pragma unroll
         for (int h = 0; h < kVecsPerLane; ++h) {
-            const int64_t v = v0 + lane + 32 * h;
-            const float *bp = B + r0 + v * ldb;
-            if (v >= nvec) {
+            const float4 *xq = reinterpret_cast<const float4 *>(X + (lane + 32 * h) * kXS + i0);
 #pragma unroll
-                for (int r = 0; r < kBlk; ++r) x[h][r] = 0.f;
-            } else if (bvec) {
-                float t[kBlk];
-#pragma unroll
-                for (int g = 0; g < kBlk / 4; ++g) {
-                    const float4 f = *reinterpret_cast<const float4 *>(bp + b0 + 4 * g);
-                    t[4 * g] = f.x; t[4 * g + 1] = f.y; t[4 * g + 2] = f.z; t[4 * g + 3] = f.w;
-                }
-#pragma unroll
-                for (int r = 0; r < kBlk; ++r) x[h][r] = rev ? t[kBlk - 1 - r] : t[r];
-            } else {
-#pragma unroll
-                for (int r = 0; r < kBlk; ++r)
-                    x[h][r] = r < nv ? bp[rev ? s - 1 - (i0 + r) : i0 + r] : 0.f;
+            for (int g = 0; g < kBlk / 4; ++g) {
+                const float4 f = xq[g];
+                x[h][4 * g] = f.x; x[h][4 * g + 1] = f.y; x[h][4 * g + 2] = f.z; x[h][4 * g + 3] = f.w;
             }
         }
     } else {
