@@ -27,7 +27,6 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8;
 constexpr int NT = 256;
 constexpr int LDS = BM + 4;   // padded shared row (floats); conflict-free transposed stores
-constexpr int LDSB = 2 * BN + 8;   // B panel row: every value stored twice (see below)
 
 // Loads this thread's four elements of a 128 x 8 panel of op(X), where op(X)
 // is (rows x K) and the panel starts at (r0, k0). KC: the stored matrix is
@@ -108,37 +107,6 @@ __device__ __forceinline__ void store_panel(float *__restrict__ S, int t, const 
     }
 }
 
-// store_panel for the op(B)^T panel, each value written twice (adjacent):
-// a 16-byte load then yields two (b_j, b_j) pairs, the operand that
-// multiplies a pair of rows of op(A) in ffma2.
-template <bool KC, bool VEC>
-__device__ __forceinline__ void store_panel_dup(float *__restrict__ S, int t, const float v[4]) {
-    if (!KC) {
-        const int p = t >> 5;
-        if (VEC) {
-            float *d = S + p * LDSB + 2 * ((t & 31) * 4);
-            *reinterpret_cast<float4 *>(d) = make_float4(v[0], v[0], v[1], v[1]);
-            *reinterpret_cast<float4 *>(d + 4) = make_float4(v[2], v[2], v[3], v[3]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                *reinterpret_cast<float2 *>(S + p * LDSB + 2 * ((t & 31) + 32 * e)) = make_float2(v[e], v[e]);
-        }
-    } else {
-        if (VEC) {
-            const int r = t >> 1, p = (t & 1) * 4;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                *reinterpret_cast<float2 *>(S + (p + e) * LDSB + 2 * r) = make_float2(v[e], v[e]);
-        } else {
-            const int p = t & 7;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                *reinterpret_cast<float2 *>(S + p * LDSB + 2 * ((t >> 3) + 32 * e)) = make_float2(v[e], v[e]);
-        }
-    }
-}
-
 template <bool TA, bool TB, bool VA, bool VB, bool VC>
 __global__ void __launch_bounds__(NT, 2)
 simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
@@ -151,7 +119,7 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
     constexpr bool AKC = TA;
     constexpr bool BKC = !TB;
     __shared__ __align__(16) float As[2][BK * LDS];
-    __shared__ __align__(16) float Bs[2][BK * LDSB];
+    __shared__ __align__(16) float Bs[2][BK * LDS];
 
     const int t = threadIdx.x;
     const int tx = t & 15, ty = t >> 4;
@@ -172,7 +140,7 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         load_panel<AKC, VA>(A, lda, M, K, m0, 0, t, ra);
         load_panel<BKC, VB>(B, ldb, N, K, n0, 0, t, rb);
         store_panel<AKC, VA>(As[0], t, ra);
-        store_panel_dup<BKC, VB>(Bs[0], t, rb);
+        store_panel<BKC, VB>(Bs[0], t, rb);
     }
     __syncthreads();
 
@@ -187,17 +155,16 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         const float *bs = Bs[cur];
 #pragma unroll
         for (int p = 0; p < BK; ++p) {
-            // a pairs straight from two 16-byte loads; b as (b_j, b_j) pairs
-            // from the duplicated panel (four 16-byte loads)
+            // a pairs straight from two 16-byte loads; b from two 16-byte
+            // loads, each value made a (b_j, b_j) pair in registers
             const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(as + p * LDS + tx * 4);
             const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(as + p * LDS + 64 + tx * 4);
-            const float *bp = bs + p * LDSB;
-            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (ty * 4));
-            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (ty * 4) + 4);
-            const ulonglong2 b2 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (64 + ty * 4));
-            const ulonglong2 b3 = *reinterpret_cast<const ulonglong2 *>(bp + 2 * (64 + ty * 4) + 4);
+            const float4 bl = *reinterpret_cast<const float4 *>(bs + p * LDS + ty * 4);
+            const float4 bh = *reinterpret_cast<const float4 *>(bs + p * LDS + 64 + ty * 4);
             const unsigned long long a[4] = {a0.x, a0.y, a1.x, a1.y};
-            const unsigned long long b[8] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y, b3.x, b3.y};
+            const unsigned long long b[8] = {pack2(bl.x, bl.x), pack2(bl.y, bl.y), pack2(bl.z, bl.z),
+                                             pack2(bl.w, bl.w), pack2(bh.x, bh.x), pack2(bh.y, bh.y),
+                                             pack2(bh.z, bh.z), pack2(bh.w, bh.w)};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -205,7 +172,7 @@ simt_sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, float beta,
         }
         if (more) {
             store_panel<AKC, VA>(As[cur ^ 1], t, ra);
-            store_panel_dup<BKC, VB>(Bs[cur ^ 1], t, rb);
+            store_panel<BKC, VB>(Bs[cur ^ 1], t, rb);
         }
         __syncthreads();
         cur ^= 1;
